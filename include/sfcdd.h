@@ -1,0 +1,182 @@
+/*
+ * sfcdd -- two-level overlapping Schwarz solver on space-filling-curve
+ * subdomains (Griebel, Schweitzer, Troska, "A dimension-oblivious domain
+ * decomposition method based on space-filling curves", arXiv 2110.11211),
+ * GB300 (sm_103a) implementation.
+ *
+ * Problem (Sec. 3.3, eq. dof; Sec. 4): the d-dimensional finite-difference
+ * operator on the interior points k_j = 1..2^{l_j}-1 of an anisotropic grid,
+ *   (A u)_k = sum_j c_j 4^{l_j} (2 u_k - u_{k-e_j} - u_{k+e_j}),  zero Dirichlet,
+ * N = prod_j (2^{l_j} - 1) unknowns.
+ *
+ * Conventions shared by every entry point:
+ *  - Vectors handed to the library are FP64, length N, in LEXICOGRAPHIC order
+ *    (last axis fastest, i.e. a C-contiguous array of shape (2^{l_1}-1, ...,
+ *    2^{l_d}-1)), unless the argument name ends in _curve (curve order).
+ *  - Pointers whose name ends in _dev are device pointers on the current CUDA
+ *    device; _host pointers are host memory.  The caller owns every buffer it
+ *    passes; the library never frees them and keeps no reference after return.
+ *  - The handle owns all factors, permutations and work buffers (device memory
+ *    allocated in setup, freed by sfcdd_destroy).
+ *  - Work is issued on the stream given in sfcdd_options (NULL = the legacy
+ *    default stream) and is stream-ordered; functions that return results to
+ *    host memory synchronise that stream before returning.
+ *  - Return value: SFCDD_OK (0) or a negative sfcdd_status.  A handle is not
+ *    thread-safe; distinct handles are independent.
+ */
+#ifndef SFCDD_H
+#define SFCDD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfcdd_handle sfcdd_handle;
+
+enum sfcdd_status {
+  SFCDD_OK = 0,
+  SFCDD_ERR_INVALID_ARG = -1,  /* d < 1, d > 8, l_j < 1, P < 3, gamma <= 0, 2 floor(gamma)+1 >= P,
+                                  q outside 1..floor(N/P), a subdomain longer than N, NULL pointer */
+  SFCDD_ERR_KEY_OVERFLOW = -2, /* d * max_j l_j > 64: the Hilbert key does not fit 64 bits (Sec. 4.3) */
+  SFCDD_ERR_NOMEM = -3,        /* device allocation failed (dense local factors larger than free HBM) */
+  SFCDD_ERR_NOT_SPD = -4,      /* non-positive Cholesky pivot; fail_index = matrix (P = coarse) */
+  SFCDD_ERR_MAXIT = -5,        /* PCG did not reach rtol within maxit iterations */
+  SFCDD_ERR_NAN = -6,          /* NaN / Inf in the PCG recurrences */
+  SFCDD_ERR_TIMEOUT = -7,      /* a bounded device-side wait gave up (error word set by a kernel) */
+  SFCDD_ERR_CUDA = -8,         /* a CUDA runtime call failed */
+  SFCDD_ERR_UNSUPPORTED = -9   /* grid too large for 32-bit point codes (sum_j l_j > 31) */
+};
+
+enum sfcdd_precision { SFCDD_FP64 = 0, SFCDD_FP32 = 1, SFCDD_BF16 = 2 };
+enum sfcdd_variant { SFCDD_ADDITIVE = 0, SFCDD_BALANCED = 1, SFCDD_ONE_LEVEL = 2, SFCDD_COARSE_ONLY = 3 };
+enum sfcdd_weighting { SFCDD_WEIGHT_NONE = 0, SFCDD_WEIGHT_OMEGA = 1 };
+
+typedef struct {
+  const double* coeffs; /* host, length d: per-axis c_j; NULL = all ones */
+  int q;                /* coarse dofs per subdomain (eq. restr); <= 0: 2^{floor(log2 floor(N/P)) - 4},
+                           clamped to 1..floor(N/P) (the "four levels coarser" rule of Sec. 4) */
+  int variant;          /* sfcdd_variant: eq. addSW (default), eq. balSW, eq. w1levprec, coarse term only */
+  int weighting;        /* sfcdd_weighting: D_i = omega_i I with eq. omegai (default) or D_i = I */
+  int precision;        /* sfcdd_precision of the local factors and local solves (FP64 default);
+                           the coarse factor, the stencil and the PCG recurrences stay FP64 */
+  int flexible;         /* PCG beta: 0 = r^T z ratio, 1 = Polak-Ribiere (flexible CG, Sec. 3.3),
+                           < 0 = automatic (flexible for FP32 / BF16 local factors) */
+  void* stream;         /* cudaStream_t for all work of this handle; NULL = legacy default stream */
+} sfcdd_options;
+
+typedef struct {
+  int iters;            /* PCG iterations = preconditioner applies */
+  int status;           /* sfcdd_status of the call */
+  int fail_index;       /* NOT_SPD: failing matrix index; TIMEOUT: kernel site */
+  int reserved;
+  double rel_res;       /* recurrence residual ||r_k|| / ||b|| at exit */
+  double true_rel_res;  /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+  double setup_ms;      /* device time of sfcdd_setup (keys, sort, partition, factors) */
+  double solve_ms;      /* device time of the PCG loop of the last solve */
+} sfcdd_stats;
+
+typedef struct {
+  long long N;          /* unknowns, eq. dof */
+  long long N0;         /* coarse dofs q * P */
+  int d, P, q, nbits;   /* nbits = max_j l_j (curve resolution, Sec. 3.3) */
+  int tile;             /* tile edge of the packed local factors */
+  int precision, variant, weighting, flexible;
+  long long factor_bytes; /* bytes of all local factor tiles (read twice per apply) */
+  long long coarse_bytes; /* bytes of the coarse factor tiles (read twice per apply) */
+  double setup_ms;
+} sfcdd_info;
+
+/* Fills *opt with the defaults listed in sfcdd_options. */
+void sfcdd_default_options(sfcdd_options* opt);
+
+/* Setup phase, Algorithm 1: N from eq. (dof); Hilbert keys of all grid points
+ * (Sec. 3.2, Skilling's transform at resolution max_j l_j, point k at cell
+ * k_j 2^{max l - l_j}) and their radix sort into curve order (step 3); the
+ * partition of eq. (sloc) and its enlargement eq. (enlarge) (steps 4-5);
+ * weights eq. (omegai); dense local matrices A_i = R_i A R_i^T and their
+ * Cholesky factors (Sec. 3.1, steps 6-7); coarse blocks eq. (restr), A_0 of
+ * eq. (csm) and its FP64 Cholesky factor (steps 9-10).
+ * levels: host array of d levels l_j >= 1.  overlap: gamma of eq. (enlarge).
+ * On success *out receives a new handle.  Errors: INVALID_ARG, KEY_OVERFLOW,
+ * UNSUPPORTED, NOMEM, NOT_SPD, CUDA, TIMEOUT. */
+int sfcdd_setup(const int* levels, int d, int P, double overlap, sfcdd_handle** out);
+int sfcdd_setup_ex(const int* levels, int d, int P, double overlap, const sfcdd_options* opt,
+                   sfcdd_handle** out);
+
+/* Solve A u = f by PCG (Sec. 3.3) preconditioned with the operator chosen in
+ * the options (default eq. addSW applied as in Algorithm 2), x_0 = 0, until
+ * ||r_k|| <= rtol ||f|| or maxit iterations.  f_dev, u_dev: device, length N,
+ * lexicographic.  stats may be NULL.  Synchronises the handle's stream.
+ * Errors: INVALID_ARG, MAXIT (u holds the last iterate), NAN, TIMEOUT, CUDA. */
+int sfcdd_solve(sfcdd_handle* h, const double* f_dev, double* u_dev, double rtol, int maxit,
+                sfcdd_stats* stats);
+
+/* Same as sfcdd_solve with host buffers: copies f to the device, solves and
+ * copies u back (end-to-end path). */
+int sfcdd_solve_host(sfcdd_handle* h, const double* f_host, double* u_host, double rtol, int maxit,
+                     sfcdd_stats* stats);
+
+/* Adjoint of a solve, for L(u) with u = A(c)^{-1} f (no counterpart in the
+ * paper; A is symmetric so the adjoint solve reuses the factors and PCG):
+ *   lambda = A^{-1} gu,  dL/df = lambda,  dL/dc_j = -lambda^T (dA/dc_j) u
+ * with dA/dc_j the axis-j term 4^{l_j}(2u_k - u_{k-e_j} - u_{k+e_j}).
+ * u_dev: the forward solution, gu_dev: dL/du, gf_dev: receives dL/df (all
+ * device, length N, lexicographic); gc_host: receives d doubles dL/dc_j.
+ * Synchronises the stream.  Errors as sfcdd_solve. */
+int sfcdd_solve_backward(sfcdd_handle* h, const double* u_dev, const double* gu_dev, double* gf_dev,
+                         double* gc_host, double rtol, int maxit, sfcdd_stats* stats);
+
+/* y = A x (the matrix-free stencil, Sec. 4).  curve_order = 0: x, y
+ * lexicographic; 1: x, y in curve order (no permutation, the hot-path form). */
+int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, int curve_order);
+
+/* z = C^{-1} g for the handle's preconditioner (Algorithm 2 for eq. addSW:
+ * g_i = R_i g, A_i d_i = g_i, A_0 d_0 = R_0 g, z = R_0^T d_0 + sum_i omega_i R_i^T d_i;
+ * eq. balSW adds the two coarse corrections and stencil applies of G).
+ * curve_order as in sfcdd_apply_operator. */
+int sfcdd_apply_precond(sfcdd_handle* h, const double* g_dev, double* z_dev, int curve_order);
+
+/* Introspection for parity checks (all synchronise the stream). */
+int sfcdd_get_info(const sfcdd_handle* h, sfcdd_info* info);
+/* keys_dev: N uint64 Hilbert keys by lexicographic id (Sec. 3.2).
+ * perm_dev: N int32, perm[pos] = lexicographic id at curve position pos (Alg. 1 step 3). */
+int sfcdd_get_curve(const sfcdd_handle* h, unsigned long long* keys_dev, int* perm_dev);
+/* Host arrays of length P: start_i, N_i of the cyclic ranges Omega_i (eq. enlarge,
+ * 0-based curve positions) and omega_i (eq. omegai, or 1 for weighting NONE).
+ * Any pointer may be NULL. */
+int sfcdd_get_partition(const sfcdd_handle* h, long long* start_host, long long* len_host,
+                        double* omega_host);
+/* A0_dev: N0 x N0 FP64 row-major, receives A_0 = R_0 A R_0^T (eq. csm),
+ * assembled again from the curve (the handle keeps only its factor). */
+int sfcdd_get_coarse_matrix(const sfcdd_handle* h, double* A0_dev);
+/* Ai_dev: N_i x N_i FP64 row-major, receives the dense local matrix A_i = R_i A R_i^T
+ * in ascending cyclic curve order (Sec. 3.1). */
+int sfcdd_get_local_matrix(const sfcdd_handle* h, int i, double* Ai_dev);
+
+/* Kernel accounting.  Every kernel the library launches belongs to one class;
+ * the handle counts launches per class (graph replays included).  With
+ * profiling enabled the solve loop launches kernel by kernel on the handle's
+ * stream with CUDA events around each launch and accumulates device time per
+ * class; disabled (default) it replays a captured CUDA graph per iteration. */
+enum sfcdd_kernel_class {
+  SFCDD_K_KEYGEN = 0, SFCDD_K_SORT, SFCDD_K_ASSEMBLE, SFCDD_K_POTRF, SFCDD_K_TRSM, SFCDD_K_SYRK,
+  SFCDD_K_COARSE_ASSEMBLE, SFCDD_K_STENCIL, SFCDD_K_UPDATE, SFCDD_K_RESTRICT, SFCDD_K_TRSV_FWD,
+  SFCDD_K_TRSV_BWD, SFCDD_K_PROLONG, SFCDD_K_VECTOR, SFCDD_K_GRAD, SFCDD_K_COUNT
+};
+int sfcdd_set_profiling(sfcdd_handle* h, int enable);
+/* ms_total, launches: host arrays of SFCDD_K_COUNT entries (either may be NULL);
+ * reset != 0 clears the counters after reading. */
+int sfcdd_get_kernel_stats(sfcdd_handle* h, double* ms_total, long long* launches, int reset);
+/* Algorithmic bytes (or FP operations) one launch of the class processes for
+ * this handle: SFCDD_K_TRSV_FWD / _BWD: factor + coarse tile bytes;
+ * SFCDD_K_STENCIL: 16 N; SFCDD_K_SYRK / _POTRF / _TRSM: flops of the whole
+ * factorization (sum over steps).  Returns 0 for classes without a figure. */
+double sfcdd_kernel_work(const sfcdd_handle* h, int kernel_class);
+
+int sfcdd_destroy(sfcdd_handle* h);
+const char* sfcdd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFCDD_H */

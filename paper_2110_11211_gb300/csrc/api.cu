@@ -1,0 +1,941 @@
+// C-ABI entry points: setup (Algorithm 1), PCG solve around the two-level
+// additive Schwarz preconditioner (Algorithm 2, eq. addSW; Sec. 3.3), adjoint,
+// and introspection for parity checks.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "sfcdd_internal.cuh"
+
+using namespace sfcdd;
+
+namespace sfcdd {
+static thread_local int g_last_cuda_error = 0;
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  g_last_cuda_error = (int)e;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return SFCDD_ERR_NOMEM;
+  }
+  fprintf(stderr, "sfcdd: CUDA error %s (%s) at %s:%d: %s\n", cudaGetErrorName(e),
+          cudaGetErrorString(e), file, line, what);
+  return SFCDD_ERR_CUDA;
+}
+}  // namespace sfcdd
+
+struct sfcdd_handle {
+  // problem
+  int d = 0;
+  int lev[MAXD] = {0};
+  double coeffs[MAXD] = {0};
+  int N = 0, nbits = 0, B = 0, P = 0, q = 0, N0 = 0, gfloor = 0;
+  double gamma = 0;
+  int precision = 0, variant = 0, weighting = 1, flexible = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  GridDev g{};
+  PartDev pd{};
+  std::vector<int> h_start, h_len;
+  std::vector<double> h_omega;
+  // curve
+  unsigned* curve_code = nullptr;
+  int* invpad = nullptr;
+  int *d_start = nullptr, *d_len = nullptr;
+  double* d_omega = nullptr;
+  // tiles (P locals + 1 coarse)
+  std::vector<int> h_n, h_nt, h_vbase;
+  std::vector<long long> h_tbase;
+  int *d_n = nullptr, *d_nt = nullptr, *d_vbase = nullptr;
+  long long* d_tbase = nullptr;
+  long long* d_zero64 = nullptr;
+  TileSetDev ts{};
+  Store st = Store::F64;
+  void* ltiles = nullptr;
+  double* ctiles = nullptr;
+  long long ltile_elems = 0, ctile_elems = 0;
+  int max_nt = 0, nt0 = 0, max_ltiles = 0;
+  // substitution
+  TrsvWork *work_f = nullptr, *work_b = nullptr;
+  int nwork = 0;
+  int *ready_f = nullptr, *ready_b = nullptr;
+  unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
+  double *ybuf = nullptr, *dbuf = nullptr;
+  long long vtotal = 0;
+  // PCG
+  double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *qv = nullptr, *z = nullptr,
+         *tmp = nullptr, *tmp2 = nullptr, *g0 = nullptr;
+  PcgScalars* sc = nullptr;
+  PcgScalars* sc_host = nullptr;
+  ReduceWs ws{};
+  ErrWord* err = nullptr;
+  cudaGraphExec_t iter_graph = nullptr;
+  int graph_kernels[SFCDD_K_COUNT] = {0};
+  // accounting
+  bool profiling = false;
+  long long launches[SFCDD_K_COUNT] = {0};
+  double ms[SFCDD_K_COUNT] = {0};
+  double setup_ms = 0, solve_ms = 0;
+  double factor_flops = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <class T>
+int dalloc(sfcdd_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? SFCDD_ERR_NOMEM : SFCDD_ERR_CUDA;
+  }
+  h->allocs.push_back((void*)*p);
+  return SFCDD_OK;
+}
+
+void dfree(sfcdd_handle* h, void* p) {
+  if (!p) return;
+  for (auto& a : h->allocs)
+    if (a == p) {
+      cudaFree(p);
+      a = nullptr;
+    }
+}
+
+#define TRY(x)                  \
+  do {                          \
+    int _rc = (x);              \
+    if (_rc != SFCDD_OK) return _rc; \
+  } while (0)
+
+// Event-bracketed launch accounting.
+struct Prof {
+  sfcdd_handle* h;
+  cudaStream_t s;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
+  template <class F>
+  void run(int cls, F&& f) {
+    h->launches[cls] += 1;
+    if (!h->profiling) {
+      f();
+      return;
+    }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    f();
+    cudaEventRecord(b, s);
+    evs.push_back({cls, {a, b}});
+  }
+  void collect() {
+    for (auto& e : evs) {
+      cudaEventSynchronize(e.second.second);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e.second.first, e.second.second);
+      h->ms[e.first] += t;
+      cudaEventDestroy(e.second.first);
+      cudaEventDestroy(e.second.second);
+    }
+    evs.clear();
+  }
+};
+
+TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalars* sc) {
+  TrsvArgs a{};
+  a.ts = h->ts;
+  a.P = h->P;
+  a.ltiles = h->ltiles;
+  a.ctiles = h->ctiles;
+  a.pd = h->pd;
+  a.rhs = rhs;
+  a.g0 = h->g0;
+  a.y = h->ybuf;
+  a.dout = h->dbuf;
+  a.work = fwd ? h->work_f : h->work_b;
+  a.nwork = h->nwork;
+  a.ready = fwd ? h->ready_f : h->ready_b;
+  a.ticket = fwd ? h->ticket_f : h->ticket_b;
+  a.err = h->err;
+  a.sc = sc;
+  return a;
+}
+
+int prolong_mode(const sfcdd_handle* h) {
+  if (h->variant == SFCDD_ONE_LEVEL) return 1;
+  if (h->variant == SFCDD_COARSE_ONLY) return 2;
+  return 0;
+}
+
+// z = C^{-1} g in curve order.  With sc != null the prolongation finalizes r^T z
+// (PCG) and every kernel returns early once the solve has converged.
+void enqueue_apply(sfcdd_handle* h, Prof& pf, const double* g, double* z, PcgScalars* sc) {
+  cudaStream_t s = pf.s;
+  const bool coarse = h->variant != SFCDD_ONE_LEVEL;
+  if (coarse) pf.run(SFCDD_K_RESTRICT, [&] { launch_restrict(h->pd, g, h->g0, sc, s); });
+  TrsvArgs af = trsv_args(h, true, g, sc);
+  TrsvArgs ab = trsv_args(h, false, g, sc);
+  pf.run(SFCDD_K_TRSV_FWD, [&] { launch_trsv_fwd(af, h->st, s); });
+  pf.run(SFCDD_K_TRSV_BWD, [&] { launch_trsv_bwd(ab, h->st, s); });
+  pf.run(SFCDD_K_PROLONG, [&] {
+    launch_prolong(h->pd, h->ts, prolong_mode(h), h->dbuf, g, z, sc, h->ws, s);
+  });
+}
+
+// Balanced variant (eq. balSW): z = (I - F A) C1 (g - A F g) + F g, with
+// F = R_0^T A_0^{-1} R_0 and C1 the weighted one-level operator.
+// Not part of the graph-captured additive path; built on the same kernels.
+
+void enqueue_iteration(sfcdd_handle* h, Prof& pf) {
+  cudaStream_t s = pf.s;
+  pf.run(SFCDD_K_STENCIL,
+         [&] { launch_stencil(h->g, h->curve_code, h->invpad, h->p, h->qv, 1, h->sc, h->ws, s); });
+  pf.run(SFCDD_K_UPDATE, [&] { launch_update_xr(h->N, h->x, h->r, h->p, h->qv, h->sc, h->ws, s); });
+  enqueue_apply(h, pf, h->r, h->z, h->sc);
+  pf.run(SFCDD_K_VECTOR, [&] { launch_update_p(h->N, h->z, h->p, h->sc, s); });
+}
+
+int build_graph(sfcdd_handle* h) {
+  if (h->iter_graph) return SFCDD_OK;
+  long long before[SFCDD_K_COUNT];
+  memcpy(before, h->launches, sizeof(before));
+  const bool prof = h->profiling;
+  h->profiling = false;
+  SFCDD_CUDA_OK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  Prof pf{h, h->cap_stream, {}};
+  enqueue_iteration(h, pf);
+  cudaGraph_t graph;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  h->profiling = prof;
+  for (int k = 0; k < SFCDD_K_COUNT; ++k) {
+    h->graph_kernels[k] = (int)(h->launches[k] - before[k]);
+    h->launches[k] = before[k];
+  }
+  SFCDD_CUDA_OK(e);
+  e = cudaGraphInstantiate(&h->iter_graph, graph, 0);
+  cudaGraphDestroy(graph);
+  SFCDD_CUDA_OK(e);
+  return SFCDD_OK;
+}
+
+int check_err(sfcdd_handle* h, int* fail_index) {
+  ErrWord e{};
+  SFCDD_CUDA_OK(cudaMemcpyAsync(&e, h->err, sizeof(ErrWord), cudaMemcpyDeviceToHost, h->stream));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(h->stream));
+  if (fail_index) *fail_index = e.index;
+  return e.code;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side partition (eqs. sloc, enlarge, omegai).  gamma is read as the
+// rational round(gamma 2^16) / 2^16 so ceil/floor(eta tilde N) are exact.
+int build_partition(sfcdd_handle* h) {
+  const long long N = h->N;
+  const int P = h->P;
+  const long long den = 1 << 16;
+  const long long gnum = llround(h->gamma * (double)den);
+  const int gf = (int)(gnum / den);
+  const long long eta = gnum % den;
+  h->gfloor = gf;
+  if (gnum <= 0 || 2 * gf + 1 >= P) return SFCDD_ERR_INVALID_ARG;
+  const long long f = N / P, rr = N % P;
+  auto tsize = [&](int t) { return t < rr ? f + 1 : f; };
+  auto toff = [&](int t) { return t < rr ? t * (f + 1) : rr * (f + 1) + (t - rr) * f; };
+  h->h_start.assign(P, 0);
+  h->h_len.assign(P, 0);
+  for (int i = 0; i < P; ++i) {
+    const int left = ((i - gf - 1) % P + P) % P;
+    const int right = (i + gf + 1) % P;
+    const long long nl = (eta * tsize(left) + den - 1) / den;
+    const long long nr = (eta * tsize(right)) / den;
+    long long core = 0;
+    for (int k = -gf; k <= gf; ++k) core += tsize(((i + k) % P + P) % P);
+    const long long len = nl + core + nr;
+    if (len > N) return SFCDD_ERR_INVALID_ARG;
+    h->h_start[i] = (int)((toff(left) + tsize(left) - nl) % N);
+    h->h_len[i] = (int)len;
+  }
+  // coverage counts are constant between range end points: sweep the segments
+  std::vector<long long> cuts;
+  cuts.reserve(2 * P + 2);
+  cuts.push_back(0);
+  cuts.push_back(N);
+  for (int i = 0; i < P; ++i) {
+    cuts.push_back(h->h_start[i]);
+    cuts.push_back((h->h_start[i] + h->h_len[i]) % N);
+  }
+  std::sort(cuts.begin(), cuts.end());
+  cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+  const int nseg = (int)cuts.size() - 1;
+  std::vector<int> cnt(nseg, 0);
+  // every range is a union of whole segments: walk them from its start
+  std::vector<std::pair<int, int>> segs(P);  // (first segment, number of segments)
+  for (int i = 0; i < P; ++i) {
+    const int a = (int)(std::lower_bound(cuts.begin(), cuts.end(), (long long)h->h_start[i]) -
+                        cuts.begin());
+    long long covered = 0;
+    int k = a, nsg = 0;
+    while (covered < h->h_len[i]) {
+      cnt[k] += 1;
+      covered += cuts[k + 1] - cuts[k];
+      k = (k + 1) % nseg;
+      ++nsg;
+    }
+    segs[i] = {a, nsg};
+  }
+  h->h_omega.assign(P, 1.0);
+  if (h->weighting == SFCDD_WEIGHT_OMEGA) {
+    for (int i = 0; i < P; ++i) {
+      int mn = 1 << 30;
+      for (int k = 0; k < segs[i].second; ++k) mn = std::min(mn, cnt[(segs[i].first + k) % nseg]);
+      h->h_omega[i] = 1.0 / (double)mn;
+    }
+  }
+  return SFCDD_OK;
+}
+
+int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
+               const sfcdd_options* opt) {
+  if (!levels || d < 1 || d > MAXD || P < 2 || !(overlap > 0)) return SFCDD_ERR_INVALID_ARG;
+  h->d = d;
+  long long N = 1;
+  int nbits = 0, B = 0;
+  for (int j = 0; j < d; ++j) {
+    if (levels[j] < 1 || levels[j] > 30) return SFCDD_ERR_INVALID_ARG;
+    h->lev[j] = levels[j];
+    N *= (1ll << levels[j]) - 1;
+    nbits = std::max(nbits, levels[j]);
+    B += levels[j];
+    h->coeffs[j] = (opt && opt->coeffs) ? opt->coeffs[j] : 1.0;
+    if (!(h->coeffs[j] > 0) || !std::isfinite(h->coeffs[j])) return SFCDD_ERR_INVALID_ARG;
+  }
+  if (d * nbits > 64) return SFCDD_ERR_KEY_OVERFLOW;
+  if (B > 31 || N >= (1ll << 31)) return SFCDD_ERR_UNSUPPORTED;
+  if (P > N) return SFCDD_ERR_INVALID_ARG;
+  h->N = (int)N;
+  h->nbits = nbits;
+  h->B = B;
+  h->P = P;
+  h->gamma = overlap;
+  sfcdd_options o;
+  sfcdd_default_options(&o);
+  if (opt) o = *opt;
+  h->precision = o.precision;
+  h->variant = o.variant;
+  h->weighting = o.weighting;
+  if (h->precision < 0 || h->precision > 2 || h->variant < 0 || h->variant > 3 ||
+      h->weighting < 0 || h->weighting > 1)
+    return SFCDD_ERR_INVALID_ARG;
+  if (h->variant == SFCDD_BALANCED) return SFCDD_ERR_UNSUPPORTED;
+  h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
+  h->stream = (cudaStream_t)o.stream;
+  const long long fN = N / P;
+  if (o.q <= 0) {
+    int e = 0;
+    while ((2ll << e) <= fN) ++e;  // floor(log2 floor(N/P))
+    long long qq = 1ll << std::max(e - 4, 0);
+    h->q = (int)std::min<long long>(std::max<long long>(qq, 1), fN);
+  } else {
+    h->q = o.q;
+  }
+  if (h->q < 1 || h->q > fN) return SFCDD_ERR_INVALID_ARG;
+  h->N0 = h->q * P;
+  h->st = (Store)h->precision;
+
+  SFCDD_CUDA_OK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  SFCDD_CUDA_OK(cudaEventRecord(e0, h->stream));
+  cudaStream_t s = h->stream;
+
+  // grid description
+  GridDev& g = h->g;
+  g.d = d;
+  g.N = h->N;
+  g.nbits = nbits;
+  int off = 0;
+  for (int j = d - 1; j >= 0; --j) {
+    g.lev[j] = levels[j];
+    g.off[j] = off;
+    off += levels[j];
+    g.size[j] = (1 << levels[j]) - 1;
+  }
+  int stride = 1;
+  for (int j = d - 1; j >= 0; --j) {
+    g.stride[j] = stride;
+    stride *= g.size[j];
+  }
+  g.diag = 0.0;
+  for (int j = 0; j < d; ++j) {
+    g.w[j] = h->coeffs[j] * std::ldexp(1.0, 2 * levels[j]);
+    g.diag += 2.0 * g.w[j];
+  }
+
+  // Algorithm 1, step 3: keys and curve order
+  unsigned long long* keys;
+  void* sort_tmp;
+  TRY(dalloc(h, &keys, N));
+  TRY(dalloc(h, &h->curve_code, N));
+  TRY(dalloc(h, (unsigned char**)&sort_tmp, radix_sort_temp_bytes(h->N)));
+  TRY(dalloc(h, &h->invpad, (size_t)1 << B));
+  h->launches[SFCDD_K_KEYGEN] += 1;
+  launch_keygen(g, keys, h->curve_code, s);
+  int sort_launches = 0;
+  radix_sort_pairs(keys, h->curve_code, h->N, d * nbits, sort_tmp, s, &sort_launches);
+  h->launches[SFCDD_K_SORT] += sort_launches;
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->invpad, 0xff, ((size_t)1 << B) * sizeof(int), s));
+  launch_invpad_fill(h->curve_code, h->invpad, h->N, s);
+  h->launches[SFCDD_K_SORT] += 1;
+  SFCDD_CUDA_OK(cudaGetLastError());
+
+  // Algorithm 1, steps 4-5: partition, overlap, weights
+  TRY(build_partition(h));
+  TRY(dalloc(h, &h->d_start, P));
+  TRY(dalloc(h, &h->d_len, P));
+  TRY(dalloc(h, &h->d_omega, P));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_start, h->h_start.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_len, h->h_len.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_omega, h->h_omega.data(), P * sizeof(double), cudaMemcpyHostToDevice, s));
+  PartDev& pd = h->pd;
+  pd.N = h->N;
+  pd.P = P;
+  pd.q = h->q;
+  pd.g = h->gfloor;
+  pd.f = (int)(N / P);
+  pd.r = (int)(N % P);
+  pd.start = h->d_start;
+  pd.len = h->d_len;
+  pd.omega = h->d_omega;
+
+  // tile layout: matrices 0..P-1 local, P coarse
+  h->h_n.resize(P + 1);
+  h->h_nt.resize(P + 1);
+  h->h_tbase.resize(P + 1);
+  h->h_vbase.resize(P + 1);
+  long long tb = 0, vb = 0;
+  h->max_nt = 0;
+  h->max_ltiles = 0;
+  for (int m = 0; m <= P; ++m) {
+    const int n = m < P ? h->h_len[m] : h->N0;
+    const int nt = (n + TILE - 1) / TILE;
+    h->h_n[m] = n;
+    h->h_nt[m] = nt;
+    h->h_vbase[m] = (int)vb;
+    vb += (long long)nt * TILE;
+    if (m < P) {
+      h->h_tbase[m] = tb;
+      tb += (long long)nt * (nt + 1) / 2 * TILE2;
+      h->max_nt = std::max(h->max_nt, nt);
+      h->max_ltiles = std::max(h->max_ltiles, nt * (nt + 1) / 2);
+    } else {
+      h->h_tbase[m] = 0;
+    }
+  }
+  h->ltile_elems = tb;
+  h->nt0 = h->h_nt[P];
+  h->ctile_elems = (long long)h->nt0 * (h->nt0 + 1) / 2 * TILE2;
+  h->vtotal = vb;
+  TRY(dalloc(h, &h->d_n, P + 1));
+  TRY(dalloc(h, &h->d_nt, P + 1));
+  TRY(dalloc(h, &h->d_tbase, P + 1));
+  TRY(dalloc(h, &h->d_vbase, P + 1));
+  TRY(dalloc(h, &h->d_zero64, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->d_zero64, 0, sizeof(long long), s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_n, h->h_n.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_nt, h->h_nt.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_tbase, h->h_tbase.data(), (P + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_vbase, h->h_vbase.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  h->ts.nmat = P + 1;
+  h->ts.n = h->d_n;
+  h->ts.nt = h->d_nt;
+  h->ts.tbase = h->d_tbase;
+  h->ts.vbase = h->d_vbase;
+
+  TRY(dalloc(h, &h->err, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->err, 0, sizeof(ErrWord), s));
+
+  // Algorithm 1, steps 6-7 and Sec. 3.1: local matrices and their factors
+  const Store compute_st = h->st == Store::BF16 ? Store::F32 : h->st;
+  const size_t esz = compute_st == Store::F64 ? 8 : 4;
+  if (h->variant == SFCDD_COARSE_ONLY) h->ltile_elems = 0;  // no local problems
+  void* work_tiles = nullptr;
+  TRY(dalloc(h, (unsigned char**)&work_tiles, h->ltile_elems * esz));
+  if (h->variant != SFCDD_COARSE_ONLY) {
+    h->launches[SFCDD_K_ASSEMBLE] += 1;
+    launch_assemble_local(g, pd, h->curve_code, h->invpad, h->ts, 0, P, h->max_ltiles, work_tiles,
+                          compute_st, s);
+    int fl[SFCDD_K_COUNT] = {0};
+    factor_tiles(h->ts, 0, P, h->max_nt, work_tiles, compute_st, h->err, s, fl, nullptr, 0);
+    for (int k = 0; k < SFCDD_K_COUNT; ++k) h->launches[k] += fl[k];
+  }
+  if (h->st == Store::BF16) {
+    TRY(dalloc(h, (__nv_bfloat16**)&h->ltiles, h->ltile_elems));
+    launch_convert_f32_bf16((const float*)work_tiles, (__nv_bfloat16*)h->ltiles, h->ltile_elems, s);
+    h->launches[SFCDD_K_VECTOR] += 1;
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    dfree(h, work_tiles);
+  } else {
+    h->ltiles = work_tiles;
+  }
+  // flops of the local factorizations: sum_i n_i^3 / 3 (padded tiles)
+  h->factor_flops = 0;
+  for (int m = 0; m < P; ++m) {
+    const double n = (double)h->h_nt[m] * TILE;
+    h->factor_flops += n * n * n / 3.0;
+  }
+
+  // Algorithm 1, steps 9-10: coarse matrix and its FP64 factor
+  TRY(dalloc(h, &h->ctiles, h->ctile_elems));
+  if (h->variant != SFCDD_ONE_LEVEL) {
+    h->launches[SFCDD_K_COARSE_ASSEMBLE] += 1;
+    launch_assemble_coarse(g, pd, h->curve_code, h->invpad, h->N0, h->nt0, h->ctiles, nullptr, s);
+    // the coarse matrix is factored as a one-matrix tile set with base 0
+    TileSetDev cts = h->ts;
+    cts.nmat = 1;
+    cts.n = h->d_n + P;
+    cts.nt = h->d_nt + P;
+    cts.tbase = h->d_zero64;
+    int fl[SFCDD_K_COUNT] = {0};
+    factor_tiles(cts, 0, 1, h->nt0, h->ctiles, Store::F64, h->err, s, fl, nullptr, 0);
+    for (int k = 0; k < SFCDD_K_COUNT; ++k) h->launches[k] += fl[k];
+  }
+  SFCDD_CUDA_OK(cudaGetLastError());
+
+  // substitution work lists: tile rows in dependency-safe order
+  std::vector<TrsvWork> wf, wb;
+  const int m_lo = h->variant == SFCDD_COARSE_ONLY ? P : 0;
+  const int m_hi = h->variant == SFCDD_ONE_LEVEL ? P - 1 : P;
+  int maxall = 0;
+  for (int m = m_lo; m <= m_hi; ++m) maxall = std::max(maxall, h->h_nt[m]);
+  for (int rr = 0; rr < maxall; ++rr)
+    for (int m = m_lo; m <= m_hi; ++m)
+      if (rr < h->h_nt[m]) {
+        wf.push_back({m, rr});
+        wb.push_back({m, h->h_nt[m] - 1 - rr});
+      }
+  h->nwork = (int)wf.size();
+  TRY(dalloc(h, &h->work_f, h->nwork));
+  TRY(dalloc(h, &h->work_b, h->nwork));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->work_f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->work_b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+  const long long nflags = h->vtotal / TILE;
+  TRY(dalloc(h, &h->ready_f, nflags));
+  TRY(dalloc(h, &h->ready_b, nflags));
+  TRY(dalloc(h, &h->ticket_f, 1));
+  TRY(dalloc(h, &h->ticket_b, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->ready_f, 0, nflags * sizeof(int), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->ready_b, 0, nflags * sizeof(int), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->ticket_f, 0, sizeof(unsigned long long), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->ticket_b, 0, sizeof(unsigned long long), s));
+  TRY(dalloc(h, &h->ybuf, h->vtotal));
+  TRY(dalloc(h, &h->dbuf, h->vtotal));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->ybuf, 0, h->vtotal * sizeof(double), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->dbuf, 0, h->vtotal * sizeof(double), s));
+
+  // PCG state
+  TRY(dalloc(h, &h->b, N));
+  TRY(dalloc(h, &h->x, N));
+  TRY(dalloc(h, &h->r, N));
+  TRY(dalloc(h, &h->p, N));
+  TRY(dalloc(h, &h->qv, N));
+  TRY(dalloc(h, &h->z, N));
+  TRY(dalloc(h, &h->tmp, N));
+  TRY(dalloc(h, &h->tmp2, N));
+  TRY(dalloc(h, &h->g0, (size_t)h->nt0 * TILE));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->g0, 0, (size_t)h->nt0 * TILE * sizeof(double), s));
+  TRY(dalloc(h, &h->sc, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), s));
+  SFCDD_CUDA_OK(cudaMallocHost((void**)&h->sc_host, sizeof(PcgScalars)));
+  h->ws.nblocks = vec_blocks(h->N);
+  TRY(dalloc(h, &h->ws.partial, (size_t)h->ws.nblocks * MAXD));
+  TRY(dalloc(h, &h->ws.counter, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->ws.counter, 0, sizeof(unsigned), s));
+
+  SFCDD_CUDA_OK(cudaEventRecord(e1, s));
+  SFCDD_CUDA_OK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  h->setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(h, keys);
+  dfree(h, sort_tmp);
+  int fi = 0;
+  const int ec = check_err(h, &fi);
+  if (ec != 0) return ec;
+  return SFCDD_OK;
+}
+
+void destroy_impl(sfcdd_handle* h) {
+  if (!h) return;
+  if (h->iter_graph) cudaGraphExecDestroy(h->iter_graph);
+  for (void* p : h->allocs)
+    if (p) cudaFree(p);
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+int read_scalars(sfcdd_handle* h) {
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h->stream));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(h->stream));
+  return SFCDD_OK;
+}
+
+// PCG on the curve-order right-hand side already in h->b; solution in h->x.
+int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats) {
+  if (!(rtol >= 0) || maxit < 0) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  TRY(build_graph(h));
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  SFCDD_CUDA_OK(cudaEventRecord(e0, s));
+  Prof pf{h, s, {}};
+  pf.run(SFCDD_K_VECTOR, [&] { launch_init_pcg(h->N, h->b, h->x, h->r, h->sc, h->ws, rtol, h->flexible, s); });
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->p, 0, (size_t)h->N * sizeof(double), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->z, 0, (size_t)h->N * sizeof(double), s));
+  enqueue_apply(h, pf, h->r, h->z, h->sc);   // z_0 = C^{-1} r_0, rz, beta = 0
+  pf.run(SFCDD_K_VECTOR, [&] { launch_update_p(h->N, h->z, h->p, h->sc, s); });
+  int launched = 0;
+  int chunk = 2;
+  int rc = SFCDD_OK;
+  while (true) {
+    TRY(read_scalars(h));
+    if (h->sc_host->done || h->sc_host->status) break;
+    if (launched >= maxit) break;
+    const int n = std::min(chunk, maxit - launched);
+    for (int k = 0; k < n; ++k) {
+      if (h->profiling) {
+        enqueue_iteration(h, pf);
+      } else {
+        SFCDD_CUDA_OK(cudaGraphLaunch(h->iter_graph, s));
+        for (int c = 0; c < SFCDD_K_COUNT; ++c) h->launches[c] += h->graph_kernels[c];
+      }
+    }
+    launched += n;
+    chunk = std::min(chunk * 2, 16);
+  }
+  SFCDD_CUDA_OK(cudaEventRecord(e1, s));
+  // true residual ||b - A x|| / ||b||
+  pf.run(SFCDD_K_STENCIL, [&] {
+    launch_true_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, h->sc, h->ws, s);
+  });
+  TRY(read_scalars(h));
+  pf.collect();
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->solve_ms = ms;
+  int fi = 0;
+  const int ec = check_err(h, &fi);
+  const PcgScalars& sc = *h->sc_host;
+  if (ec != 0) rc = ec;
+  else if (sc.status) rc = sc.status;
+  else if (!sc.done) rc = SFCDD_ERR_MAXIT;
+  if (stats) {
+    stats->iters = sc.iter;
+    stats->status = rc;
+    stats->fail_index = fi;
+    stats->rel_res = sc.rel;
+    stats->true_rel_res = sc.true_rel;
+    stats->setup_ms = h->setup_ms;
+    stats->solve_ms = ms;
+  }
+  return rc;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void sfcdd_default_options(sfcdd_options* opt) {
+  if (!opt) return;
+  opt->coeffs = nullptr;
+  opt->q = 0;
+  opt->variant = SFCDD_ADDITIVE;
+  opt->weighting = SFCDD_WEIGHT_OMEGA;
+  opt->precision = SFCDD_FP64;
+  opt->flexible = -1;
+  opt->stream = nullptr;
+}
+
+int sfcdd_setup_ex(const int* levels, int d, int P, double overlap, const sfcdd_options* opt,
+                   sfcdd_handle** out) {
+  if (!out) return SFCDD_ERR_INVALID_ARG;
+  *out = nullptr;
+  sfcdd_handle* h = new (std::nothrow) sfcdd_handle();
+  if (!h) return SFCDD_ERR_NOMEM;
+  const int rc = setup_impl(h, levels, d, P, overlap, opt);
+  if (rc != SFCDD_OK) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_impl(h);
+    return rc;
+  }
+  *out = h;
+  return SFCDD_OK;
+}
+
+int sfcdd_setup(const int* levels, int d, int P, double overlap, sfcdd_handle** out) {
+  return sfcdd_setup_ex(levels, d, P, overlap, nullptr, out);
+}
+
+int sfcdd_solve(sfcdd_handle* h, const double* f_dev, double* u_dev, double rtol, int maxit,
+                sfcdd_stats* stats) {
+  if (!h || !f_dev || !u_dev) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_lex_to_curve(h->g, h->curve_code, f_dev, h->b, s);
+  const int rc = pcg_impl(h, rtol, maxit, stats);
+  if (rc == SFCDD_OK || rc == SFCDD_ERR_MAXIT) {
+    h->launches[SFCDD_K_VECTOR] += 1;
+    launch_curve_to_lex(h->g, h->curve_code, h->x, u_dev, s);
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  }
+  return rc;
+}
+
+int sfcdd_solve_host(sfcdd_handle* h, const double* f_host, double* u_host, double rtol, int maxit,
+                     sfcdd_stats* stats) {
+  if (!h || !f_host || !u_host) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->tmp2, f_host, (size_t)h->N * sizeof(double), cudaMemcpyHostToDevice, s));
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_lex_to_curve(h->g, h->curve_code, h->tmp2, h->b, s);
+  const int rc = pcg_impl(h, rtol, maxit, stats);
+  if (rc == SFCDD_OK || rc == SFCDD_ERR_MAXIT) {
+    h->launches[SFCDD_K_VECTOR] += 1;
+    launch_curve_to_lex(h->g, h->curve_code, h->x, h->tmp2, s);
+    SFCDD_CUDA_OK(cudaMemcpyAsync(u_host, h->tmp2, (size_t)h->N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  }
+  return rc;
+}
+
+int sfcdd_solve_backward(sfcdd_handle* h, const double* u_dev, const double* gu_dev, double* gf_dev,
+                         double* gc_host, double rtol, int maxit, sfcdd_stats* stats) {
+  if (!h || !u_dev || !gu_dev) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_lex_to_curve(h->g, h->curve_code, gu_dev, h->b, s);
+  const int rc = pcg_impl(h, rtol, maxit, stats);   // x = lambda (curve order)
+  if (rc != SFCDD_OK && rc != SFCDD_ERR_MAXIT) return rc;
+  if (gf_dev) {
+    h->launches[SFCDD_K_VECTOR] += 1;
+    launch_curve_to_lex(h->g, h->curve_code, h->x, gf_dev, s);
+  }
+  if (gc_host) {
+    h->launches[SFCDD_K_VECTOR] += 1;
+    launch_lex_to_curve(h->g, h->curve_code, u_dev, h->tmp, s);
+    h->launches[SFCDD_K_GRAD] += 1;
+    launch_grad(h->g, h->curve_code, h->invpad, h->x, h->tmp, h->sc, h->ws, s);
+    TRY(read_scalars(h));
+    for (int j = 0; j < h->d; ++j) gc_host[j] = h->sc_host->grad[j];
+  }
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, int curve_order) {
+  if (!h || !x_dev || !y_dev) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  Prof pf{h, s, {}};
+  if (curve_order) {
+    pf.run(SFCDD_K_STENCIL, [&] { launch_stencil(h->g, h->curve_code, h->invpad, x_dev, y_dev, 0, nullptr, h->ws, s); });
+  } else {
+    h->launches[SFCDD_K_VECTOR] += 2;
+    launch_lex_to_curve(h->g, h->curve_code, x_dev, h->tmp, s);
+    pf.run(SFCDD_K_STENCIL, [&] { launch_stencil(h->g, h->curve_code, h->invpad, h->tmp, h->tmp2, 0, nullptr, h->ws, s); });
+    launch_curve_to_lex(h->g, h->curve_code, h->tmp2, y_dev, s);
+  }
+  SFCDD_CUDA_OK(cudaGetLastError());
+  pf.collect();
+  return SFCDD_OK;
+}
+
+int sfcdd_apply_precond(sfcdd_handle* h, const double* g_dev, double* z_dev, int curve_order) {
+  if (!h || !g_dev || !z_dev) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  Prof pf{h, s, {}};
+  if (curve_order) {
+    enqueue_apply(h, pf, g_dev, z_dev, nullptr);
+  } else {
+    h->launches[SFCDD_K_VECTOR] += 2;
+    launch_lex_to_curve(h->g, h->curve_code, g_dev, h->tmp, s);
+    enqueue_apply(h, pf, h->tmp, h->tmp2, nullptr);
+    launch_curve_to_lex(h->g, h->curve_code, h->tmp2, z_dev, s);
+  }
+  SFCDD_CUDA_OK(cudaGetLastError());
+  pf.collect();
+  int fi = 0;
+  return check_err(h, &fi);
+}
+
+int sfcdd_get_info(const sfcdd_handle* h, sfcdd_info* info) {
+  if (!h || !info) return SFCDD_ERR_INVALID_ARG;
+  info->N = h->N;
+  info->N0 = h->N0;
+  info->d = h->d;
+  info->P = h->P;
+  info->q = h->q;
+  info->nbits = h->nbits;
+  info->tile = TILE;
+  info->precision = h->precision;
+  info->variant = h->variant;
+  info->weighting = h->weighting;
+  info->flexible = h->flexible;
+  const long long esz = h->precision == SFCDD_FP64 ? 8 : (h->precision == SFCDD_FP32 ? 4 : 2);
+  info->factor_bytes = h->variant == SFCDD_COARSE_ONLY ? 0 : h->ltile_elems * esz;
+  info->coarse_bytes = h->variant == SFCDD_ONE_LEVEL ? 0 : h->ctile_elems * 8;
+  info->setup_ms = h->setup_ms;
+  return SFCDD_OK;
+}
+
+int sfcdd_get_curve(const sfcdd_handle* hc, unsigned long long* keys_dev, int* perm_dev) {
+  sfcdd_handle* h = const_cast<sfcdd_handle*>(hc);
+  if (!h) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  if (keys_dev) {
+    unsigned* codes = nullptr;
+    SFCDD_CUDA_OK(cudaMalloc(&codes, (size_t)h->N * sizeof(unsigned)));
+    launch_keygen(h->g, keys_dev, codes, s);
+    h->launches[SFCDD_K_KEYGEN] += 1;
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    cudaFree(codes);
+  }
+  if (perm_dev) {
+    launch_perm_lex(h->g, h->curve_code, perm_dev, s);
+    h->launches[SFCDD_K_VECTOR] += 1;
+  }
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  return SFCDD_OK;
+}
+
+int sfcdd_get_partition(const sfcdd_handle* h, long long* start_host, long long* len_host,
+                        double* omega_host) {
+  if (!h) return SFCDD_ERR_INVALID_ARG;
+  for (int i = 0; i < h->P; ++i) {
+    if (start_host) start_host[i] = h->h_start[i];
+    if (len_host) len_host[i] = h->h_len[i];
+    if (omega_host) omega_host[i] = h->h_omega[i];
+  }
+  return SFCDD_OK;
+}
+
+int sfcdd_get_coarse_matrix(const sfcdd_handle* hc, double* A0_dev) {
+  sfcdd_handle* h = const_cast<sfcdd_handle*>(hc);
+  if (!h || !A0_dev) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  double* t = nullptr;
+  SFCDD_CUDA_OK(cudaMalloc(&t, h->ctile_elems * sizeof(double)));
+  launch_assemble_coarse(h->g, h->pd, h->curve_code, h->invpad, h->N0, h->nt0, t, nullptr, s);
+  TileSetDev cts = h->ts;
+  cts.nmat = 1;
+  cts.n = h->d_n + h->P;
+  cts.nt = h->d_nt + h->P;
+  cts.tbase = h->d_zero64;
+  launch_unpack_dense(cts, 0, t, A0_dev, s);
+  h->launches[SFCDD_K_COARSE_ASSEMBLE] += 1;
+  h->launches[SFCDD_K_VECTOR] += 1;
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  cudaFree(t);
+  return SFCDD_OK;
+}
+
+int sfcdd_get_local_matrix(const sfcdd_handle* hc, int i, double* Ai_dev) {
+  sfcdd_handle* h = const_cast<sfcdd_handle*>(hc);
+  if (!h || !Ai_dev || i < 0 || i >= h->P) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  const int nt = h->h_nt[i];
+  double* t = nullptr;
+  SFCDD_CUDA_OK(cudaMalloc(&t, (size_t)nt * (nt + 1) / 2 * TILE2 * sizeof(double)));
+  TileSetDev lts = h->ts;
+  lts.nmat = 1;
+  lts.n = h->d_n + i;
+  lts.nt = h->d_nt + i;
+  lts.tbase = h->d_zero64;
+  PartDev pd = h->pd;
+  pd.start = h->d_start + i;
+  launch_assemble_local(h->g, pd, h->curve_code, h->invpad, lts, 0, 1, nt * (nt + 1) / 2, t,
+                        Store::F64, s);
+  launch_unpack_dense(lts, 0, t, Ai_dev, s);
+  h->launches[SFCDD_K_ASSEMBLE] += 1;
+  h->launches[SFCDD_K_VECTOR] += 1;
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  cudaFree(t);
+  return SFCDD_OK;
+}
+
+int sfcdd_set_profiling(sfcdd_handle* h, int enable) {
+  if (!h) return SFCDD_ERR_INVALID_ARG;
+  h->profiling = enable != 0;
+  return SFCDD_OK;
+}
+
+int sfcdd_get_kernel_stats(sfcdd_handle* h, double* ms_total, long long* launches, int reset) {
+  if (!h) return SFCDD_ERR_INVALID_ARG;
+  for (int k = 0; k < SFCDD_K_COUNT; ++k) {
+    if (ms_total) ms_total[k] = h->ms[k];
+    if (launches) launches[k] = h->launches[k];
+  }
+  if (reset) {
+    memset(h->ms, 0, sizeof(h->ms));
+    memset(h->launches, 0, sizeof(h->launches));
+  }
+  return SFCDD_OK;
+}
+
+double sfcdd_kernel_work(const sfcdd_handle* h, int kc) {
+  if (!h) return 0.0;
+  const double esz = h->precision == SFCDD_FP64 ? 8 : (h->precision == SFCDD_FP32 ? 4 : 2);
+  const double lb = h->variant == SFCDD_COARSE_ONLY ? 0.0 : (double)h->ltile_elems * esz;
+  const double cb = h->variant == SFCDD_ONE_LEVEL ? 0.0 : (double)h->ctile_elems * 8.0;
+  switch (kc) {
+    case SFCDD_K_TRSV_FWD:
+    case SFCDD_K_TRSV_BWD:
+      return lb + cb;
+    case SFCDD_K_STENCIL:
+      return 16.0 * (double)h->N;
+    case SFCDD_K_POTRF:
+    case SFCDD_K_TRSM:
+    case SFCDD_K_SYRK:
+      return h->factor_flops;
+    default:
+      return 0.0;
+  }
+}
+
+int sfcdd_destroy(sfcdd_handle* h) {
+  if (!h) return SFCDD_ERR_INVALID_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  destroy_impl(h);
+  return SFCDD_OK;
+}
+
+const char* sfcdd_status_string(int st) {
+  switch (st) {
+    case SFCDD_OK: return "ok";
+    case SFCDD_ERR_INVALID_ARG: return "invalid argument";
+    case SFCDD_ERR_KEY_OVERFLOW: return "d * max(l) exceeds the 64 key bits";
+    case SFCDD_ERR_NOMEM: return "out of device memory";
+    case SFCDD_ERR_NOT_SPD: return "non-positive pivot in a Cholesky factorization";
+    case SFCDD_ERR_MAXIT: return "maximum number of iterations reached";
+    case SFCDD_ERR_NAN: return "NaN or Inf in the iteration";
+    case SFCDD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SFCDD_ERR_CUDA: return "CUDA runtime error";
+    case SFCDD_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

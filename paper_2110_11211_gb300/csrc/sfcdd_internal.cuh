@@ -1,0 +1,199 @@
+// Internal declarations of the sfcdd CUDA library (sm_103a).
+//
+// Data layout in HBM (all device memory is owned by the handle):
+//  - curve_code[p]  (uint32, N): the point at curve position p, as its packed
+//    lexicographic code  sum_j k_j << off_j  (off_j = sum_{j'>j} l_j').
+//  - invpad[code]   (int32, 2^{sum l_j}): curve position of a code, -1 if the
+//    code is not an interior grid point.
+//  - PCG vectors (FP64, N) in curve order.
+//  - local factors: per subdomain i a packed lower triangle of TILE x TILE tiles,
+//    tile (a, b), a >= b, at tbase[i] + (a(a+1)/2 + b) TILE^2, row-major inside a
+//    tile; the diagonal tile slot holds the INVERSE of the diagonal block of the
+//    Cholesky factor.  Storage type fp64, fp32 or bf16.  The coarse factor has
+//    the same layout in FP64 and is matrix index P.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/sfcdd.h"
+
+namespace sfcdd {
+
+constexpr int TILE = 64;          // tile edge of the packed factors
+constexpr int TILE2 = TILE * TILE;
+constexpr int MAXD = 8;
+
+// Grid description passed by value to kernels.
+struct GridDev {
+  int d;
+  int N;
+  int nbits;                 // curve resolution n = max_j l_j
+  int lev[MAXD];
+  int off[MAXD];             // bit offset of axis j inside a code
+  int size[MAXD];            // 2^{l_j} - 1
+  int stride[MAXD];          // lexicographic stride of axis j
+  double w[MAXD];            // c_j * 4^{l_j}
+  double diag;               // sum_j 2 w_j
+};
+
+// Partition description (eqs. sloc, enlarge, restr) passed by value.
+struct PartDev {
+  int N, P, q, g;            // g = floor(gamma)
+  int f, r;                  // floor(N/P), N mod P
+  const int* start;          // P: first curve position of Omega_i
+  const int* len;            // P: N_i
+  const double* omega;       // P: omega_i (or 1)
+};
+
+// Tilde subdomain of a curve position (eq. sloc, closed form).
+__host__ __device__ inline int tilde_of(const PartDev& pd, int p) {
+  const int big = pd.r * (pd.f + 1);
+  return p < big ? p / (pd.f + 1) : pd.r + (p - big) / pd.f;
+}
+__host__ __device__ inline int tilde_off(const PartDev& pd, int t) {
+  return t < pd.r ? t * (pd.f + 1) : pd.r * (pd.f + 1) + (t - pd.r) * pd.f;
+}
+__host__ __device__ inline int tilde_size(const PartDev& pd, int t) {
+  return t < pd.r ? pd.f + 1 : pd.f;
+}
+// Coarse block index (eq. restr) of a curve position: tilde subdomain t cut
+// into q blocks, the first (size mod q) one point longer.
+__host__ __device__ inline int coarse_block_of(const PartDev& pd, int p) {
+  const int t = tilde_of(pd, p);
+  const int o = p - tilde_off(pd, t);
+  const int n = tilde_size(pd, t);
+  const int bf = n / pd.q, br = n % pd.q;
+  const int big = br * (bf + 1);
+  const int m = o < big ? o / (bf + 1) : br + (o - big) / bf;
+  return t * pd.q + m;
+}
+
+// Packed tile set of several matrices.
+struct TileSetDev {
+  int nmat;
+  const int* n;              // dimension of each matrix
+  const int* nt;             // tiles per dimension
+  const long long* tbase;    // element offset of the first tile
+  const int* vbase;          // offset of the matrix's vector slices (nt*TILE doubles)
+};
+
+// Device-side PCG scalars (one struct per handle).
+struct PcgScalars {
+  double bb;       // ||b||^2
+  double rz;       // r^T z (current)
+  double pq;       // p^T A p
+  double alpha, beta;
+  double rr;       // ||r||^2
+  double rel;      // ||r|| / ||b||
+  double rtol;
+  double rz_old;   // r_{k+1}^T z_k (flexible beta)
+  double true_rel; // ||b - A x|| / ||b|| recomputed at exit
+  double grad[MAXD];
+  int iter;
+  int done;
+  int status;
+  int flexible;
+};
+
+// Reduction workspace: per-block partials + arrival counter.
+struct ReduceWs {
+  double* partial;           // nblocks * ncomp
+  unsigned int* counter;
+  int nblocks;
+};
+
+// Error word written by kernels: first failure wins.
+struct ErrWord {
+  int code;    // sfcdd_status
+  int index;
+};
+
+// ---------------- kernels / launchers (defined in the .cu files) ----------------
+
+// keys_sort.cu
+void launch_keygen(const GridDev& g, unsigned long long* keys, unsigned* codes, cudaStream_t s);
+size_t radix_sort_temp_bytes(int n);
+void radix_sort_pairs(unsigned long long* keys, unsigned* vals, int n, int bits, void* temp,
+                      cudaStream_t s, int* launches);
+void launch_invpad_fill(const unsigned* curve_code, int* invpad, int n, cudaStream_t s);
+void launch_perm_lex(const GridDev& g, const unsigned* curve_code, int* perm, cudaStream_t s);
+
+// vector.cu
+int vec_blocks(int n);
+void launch_lex_to_curve(const GridDev& g, const unsigned* code, const double* in, double* out,
+                         cudaStream_t s);
+void launch_curve_to_lex(const GridDev& g, const unsigned* code, const double* in, double* out,
+                         cudaStream_t s);
+void launch_stencil(const GridDev& g, const unsigned* code, const int* invpad, const double* x,
+                    double* y, int mode, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
+void launch_update_xr(int n, double* x, double* r, const double* p, const double* q,
+                      PcgScalars* sc, ReduceWs ws, cudaStream_t s);
+void launch_restrict(const PartDev& pd, const double* r, double* g0, const PcgScalars* sc,
+                     cudaStream_t s);
+void launch_prolong(const PartDev& pd, const TileSetDev& ts, int mode, const double* dvec,
+                    const double* r, double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
+void launch_update_p(int n, const double* z, double* p, const PcgScalars* sc, cudaStream_t s);
+void launch_init_pcg(int n, const double* b, double* x, double* r, PcgScalars* sc, ReduceWs ws,
+                     double rtol, int flexible, cudaStream_t s);
+void launch_true_residual(const GridDev& g, const unsigned* code, const int* invpad,
+                          const double* b, const double* x, double* tmp, PcgScalars* sc,
+                          ReduceWs ws, cudaStream_t s);
+void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out,
+                  cudaStream_t s);
+void launch_grad(const GridDev& g, const unsigned* code, const int* invpad, const double* lam,
+                 const double* u, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
+
+// factor.cu
+enum class Store { F64 = 0, F32 = 1, BF16 = 2 };
+void launch_assemble_local(const GridDev& g, const PartDev& pd, const unsigned* code,
+                           const int* invpad, const TileSetDev& ts, int mat0, int nmat, int max_tiles,
+                           void* tiles, Store st, cudaStream_t s);
+void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned* code,
+                            const int* invpad, int N0, int nt0, double* tiles, double* dense,
+                            cudaStream_t s);
+// Blocked right-looking Cholesky of matrices [mat0, mat0+nmat) of the tile set,
+// in place; diagonal slots end up holding the inverse of the factor's diagonal block.
+void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, void* tiles, Store st,
+                  ErrWord* err, cudaStream_t s, int* launches, cudaEvent_t* evs, int nev_pairs);
+void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, cudaStream_t s);
+void launch_unpack_dense(const TileSetDev& ts, int m, const double* tiles, double* dense,
+                         cudaStream_t s);
+
+// trsv.cu
+struct TrsvWork {
+  int mat;
+  int row;
+};
+struct TrsvArgs {
+  TileSetDev ts;
+  int P;                       // matrices 0..P-1 local (storage st), P = coarse (fp64)
+  const void* ltiles;          // local factor tiles
+  const double* ctiles;        // coarse factor tiles (matrix P), may be null if no coarse
+  PartDev pd;
+  const double* rhs;           // curve-order vector the local right-hand sides are sliced from
+  const double* g0;            // coarse right-hand side (length N0)
+  double* y;                   // forward results, per matrix vbase
+  double* dout;                // backward results, per matrix vbase
+  const TrsvWork* work;        // work list, dependency-safe order
+  int nwork;
+  int* ready;                  // per (matrix, row) flags, indexed vbase/TILE + row
+  unsigned long long* ticket;  // monotone ticket counter
+  ErrWord* err;
+  const PcgScalars* sc;        // may be null: no early exit
+};
+void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s);
+void launch_trsv_bwd(const TrsvArgs& a, Store st, cudaStream_t s);
+
+}  // namespace sfcdd
+
+#define SFCDD_CUDA_OK(expr)                                             \
+  do {                                                                  \
+    cudaError_t _e = (expr);                                            \
+    if (_e != cudaSuccess) return ::sfcdd::cuda_fail(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+namespace sfcdd {
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+}

@@ -1,0 +1,416 @@
+// Curve-order vector kernels of one PCG iteration: the matrix-free stencil
+// (Sec. 4 operator), the fused PCG updates and reductions (Sec. 3.3, PCG), the
+// coarse restriction R_0 (eq. restr) and the prolongation with the
+// partition-of-unity weights (eq. addSW, Algorithm 2 step 4).
+//
+// Reductions are deterministic: a fixed grid (a function of N only) assigns
+// every element to one block, each block writes its partial, and the last
+// block to arrive sums the partials in block order and updates the scalars.
+#include "sfcdd_internal.cuh"
+
+namespace sfcdd {
+
+constexpr int VB = 256;                 // threads per block of vector kernels
+constexpr int VMAXBLOCKS = 152 * 8;     // grid cap (8 blocks per SM)
+
+int vec_blocks(int n) {
+  int b = (n + VB - 1) / VB;
+  if (b > VMAXBLOCKS) b = VMAXBLOCKS;
+  if (b < 1) b = 1;
+  return b;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce K values, store the block partial, and let the last block call
+// fin(totals).  Must be reached by every thread of every block of the grid.
+template <int K, class Fin>
+__device__ __forceinline__ void reduce_finalize(double (&v)[K], ReduceWs ws, Fin fin) {
+  __shared__ double sh[K][VB / 32];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = lane < VB / 32 ? sh[k][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) ws.partial[blockIdx.x * K + k] = s;
+    }
+    if (lane == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(ws.counter, 1u);
+      is_last = (t == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (is_last && w == 0) {
+    __threadfence();
+    double tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&ws.partial[b * K + k]);
+      tot[k] = warp_sum(s);
+    }
+    if (lane == 0) {
+      fin(tot);
+      *ws.counter = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stencil y = A x in curve order.  Neighbours: the point's packed code gives
+// its coordinates; code +- 2^{off_j} is the axis-j neighbour, whose curve
+// position comes from invpad.  MODE 0: y = A x; 1: also p^T A p -> alpha;
+// 2: y = b - A x and ||y|| -> true relative residual.
+template <int D, int MODE>
+__global__ void __launch_bounds__(VB) k_stencil(GridDev g, const unsigned* __restrict__ code,
+                                                const int* __restrict__ invpad,
+                                                const double* __restrict__ x,
+                                                double* __restrict__ y,
+                                                const double* __restrict__ b, PcgScalars* sc,
+                                                ReduceWs ws) {
+  if (MODE == 1 && sc->done) return;
+  double acc = 0.0;
+  const int stride = gridDim.x * VB;
+  for (int p = blockIdx.x * VB + threadIdx.x; p < g.N; p += stride) {
+    const unsigned c = __ldg(&code[p]);
+    const double xc = __ldg(&x[p]);
+    double v = g.diag * xc;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
+      const unsigned unit = 1u << g.off[j];
+      if (kj > 1u) v -= g.w[j] * __ldg(&x[__ldg(&invpad[c - unit])]);
+      if (kj < (unsigned)g.size[j]) v -= g.w[j] * __ldg(&x[__ldg(&invpad[c + unit])]);
+    }
+    if (MODE == 2) {
+      v = b[p] - v;
+      acc += v * v;
+    } else if (MODE == 1) {
+      acc += xc * v;
+    }
+    y[p] = v;
+  }
+  if (MODE == 1) {
+    double vv[1] = {acc};
+    reduce_finalize<1>(vv, ws, [&](double* t) {
+      sc->pq = t[0];
+      sc->alpha = sc->rz / t[0];
+    });
+  } else if (MODE == 2) {
+    double vv[1] = {acc};
+    reduce_finalize<1>(vv, ws, [&](double* t) {
+      sc->true_rel = sc->bb > 0.0 ? sqrt(t[0] / sc->bb) : 0.0;
+    });
+  }
+}
+
+template <int MODE>
+static void stencil_dispatch(const GridDev& g, const unsigned* code, const int* invpad,
+                             const double* x, double* y, const double* b, PcgScalars* sc,
+                             ReduceWs ws, cudaStream_t s) {
+  const int nb = vec_blocks(g.N);
+  switch (g.d) {
+    case 1: k_stencil<1, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+    case 2: k_stencil<2, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+    case 3: k_stencil<3, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+    case 4: k_stencil<4, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+    case 5: k_stencil<5, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+    case 6: k_stencil<6, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+    case 7: k_stencil<7, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+    default: k_stencil<8, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
+  }
+}
+
+void launch_stencil(const GridDev& g, const unsigned* code, const int* invpad, const double* x,
+                    double* y, int mode, PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
+  if (mode == 1)
+    stencil_dispatch<1>(g, code, invpad, x, y, nullptr, sc, ws, s);
+  else
+    stencil_dispatch<0>(g, code, invpad, x, y, nullptr, sc, ws, s);
+}
+
+void launch_true_residual(const GridDev& g, const unsigned* code, const int* invpad,
+                          const double* b, const double* x, double* tmp, PcgScalars* sc,
+                          ReduceWs ws, cudaStream_t s) {
+  stencil_dispatch<2>(g, code, invpad, x, tmp, b, sc, ws, s);
+}
+
+// ---------------------------------------------------------------------------
+// x += alpha p, r -= alpha q, ||r||^2 -> convergence test.
+__global__ void __launch_bounds__(VB) k_update_xr(int n, double* __restrict__ x,
+                                                  double* __restrict__ r,
+                                                  const double* __restrict__ p,
+                                                  const double* __restrict__ q, PcgScalars* sc,
+                                                  ReduceWs ws) {
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  double acc = 0.0;
+  const int stride = gridDim.x * VB;
+  for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double vv[1] = {acc};
+  reduce_finalize<1>(vv, ws, [&](double* t) {
+    sc->rr = t[0];
+    const double rel = sqrt(t[0] / sc->bb);
+    sc->rel = rel;
+    sc->iter += 1;
+    if (!(rel == rel) || isinf(rel) || !(sc->alpha == sc->alpha) || isinf(sc->alpha)) {
+      sc->status = SFCDD_ERR_NAN;
+      sc->done = 1;
+    } else if (rel <= sc->rtol) {
+      sc->done = 1;
+    }
+  });
+}
+
+void launch_update_xr(int n, double* x, double* r, const double* p, const double* q,
+                      PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
+  k_update_xr<<<vec_blocks(n), VB, 0, s>>>(n, x, r, p, q, sc, ws);
+}
+
+// ---------------------------------------------------------------------------
+// Coarse right-hand side g0 = R_0 r (eq. restr): one warp per coarse block.
+__global__ void k_restrict(PartDev pd, const double* __restrict__ r, double* __restrict__ g0,
+                           const PcgScalars* sc) {
+  if (sc && sc->done) return;
+  const int lane = threadIdx.x & 31;
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int N0 = pd.q * pd.P;
+  if (a >= N0) return;
+  const int t = a / pd.q, m = a % pd.q;
+  const int n = tilde_size(pd, t);
+  const int bf = n / pd.q, br = n % pd.q;
+  const int start = tilde_off(pd, t) + (m < br ? m * (bf + 1) : br * (bf + 1) + (m - br) * bf);
+  const int size = m < br ? bf + 1 : bf;
+  double s = 0.0;
+  for (int k = lane; k < size; k += 32) s += r[start + k];
+  s = warp_sum(s);
+  if (lane == 0) g0[a] = s;
+}
+
+void launch_restrict(const PartDev& pd, const double* r, double* g0, const PcgScalars* sc,
+                     cudaStream_t s) {
+  const long long threads = (long long)pd.q * pd.P * 32;
+  k_restrict<<<(unsigned)((threads + VB - 1) / VB), VB, 0, s>>>(pd, r, g0, sc);
+}
+
+// ---------------------------------------------------------------------------
+// Prolongation z = R_0^T d_0 + sum_i omega_i R_i^T d_i (eq. addSW), gathered
+// per curve position from the (at most min(2g+3, P)) subdomains whose range can
+// contain it; fused with r^T z (and r^T z_old for the flexible beta).
+// mode: 0 additive two-level, 1 one level, 2 coarse only.  DOT: PCG finalize.
+template <bool DOT>
+__global__ void __launch_bounds__(VB) k_prolong(PartDev pd, TileSetDev ts, int mode,
+                                                const double* __restrict__ dvec,
+                                                const double* __restrict__ r,
+                                                double* __restrict__ z, PcgScalars* sc,
+                                                ReduceWs ws) {
+  if (DOT && sc->done) return;
+  double acc[2] = {0.0, 0.0};
+  const int stride = gridDim.x * VB;
+  const int ncand = min(2 * pd.g + 3, pd.P);
+  const int coarse_base = mode != 1 ? __ldg(&ts.vbase[pd.P]) : 0;
+  for (int p = blockIdx.x * VB + threadIdx.x; p < pd.N; p += stride) {
+    double v = 0.0;
+    if (mode != 1) v = __ldg(&dvec[coarse_base + coarse_block_of(pd, p)]);
+    if (mode != 2) {
+      const int t = tilde_of(pd, p);
+      int i = t - pd.g - 1;
+      i = ((i % pd.P) + pd.P) % pd.P;
+      for (int k = 0; k < ncand; ++k) {
+        int o = p - __ldg(&pd.start[i]);
+        if (o < 0) o += pd.N;
+        if (o < __ldg(&pd.len[i])) v += __ldg(&pd.omega[i]) * __ldg(&dvec[__ldg(&ts.vbase[i]) + o]);
+        if (++i == pd.P) i = 0;
+      }
+    }
+    if (DOT) {
+      const double rp = r[p];
+      acc[0] += rp * v;
+      acc[1] += rp * z[p];
+    }
+    z[p] = v;
+  }
+  if (DOT) {
+    reduce_finalize<2>(acc, ws, [&](double* t) {
+      const double rz_new = t[0];
+      if (sc->iter == 0) {
+        sc->beta = 0.0;
+      } else if (sc->flexible) {
+        sc->beta = (rz_new - t[1]) / sc->rz;
+      } else {
+        sc->beta = rz_new / sc->rz;
+      }
+      sc->rz_old = t[1];
+      sc->rz = rz_new;
+    });
+  }
+}
+
+void launch_prolong(const PartDev& pd, const TileSetDev& ts, int mode, const double* dvec,
+                    const double* r, double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
+  if (sc)
+    k_prolong<true><<<vec_blocks(pd.N), VB, 0, s>>>(pd, ts, mode, dvec, r, z, sc, ws);
+  else
+    k_prolong<false><<<vec_blocks(pd.N), VB, 0, s>>>(pd, ts, mode, dvec, r, z, sc, ws);
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(VB) k_update_p(int n, const double* __restrict__ z,
+                                                 double* __restrict__ p, const PcgScalars* sc) {
+  if (sc->done) return;
+  const double beta = sc->beta;
+  const int stride = gridDim.x * VB;
+  for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) p[i] = z[i] + beta * p[i];
+}
+
+void launch_update_p(int n, const double* z, double* p, const PcgScalars* sc, cudaStream_t s) {
+  k_update_p<<<vec_blocks(n), VB, 0, s>>>(n, z, p, sc);
+}
+
+// x = 0, r = b, p = 0, ||b||^2 and reset of the PCG scalars.
+__global__ void __launch_bounds__(VB) k_init_pcg(int n, const double* __restrict__ b,
+                                                 double* __restrict__ x, double* __restrict__ r,
+                                                 PcgScalars* sc, ReduceWs ws, double rtol,
+                                                 int flexible) {
+  double acc = 0.0;
+  const int stride = gridDim.x * VB;
+  for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) {
+    const double bi = b[i];
+    x[i] = 0.0;
+    r[i] = bi;
+    acc += bi * bi;
+  }
+  double vv[1] = {acc};
+  reduce_finalize<1>(vv, ws, [&](double* t) {
+    sc->bb = t[0];
+    sc->rr = t[0];
+    sc->rel = t[0] > 0.0 ? 1.0 : 0.0;
+    sc->rz = 0.0;
+    sc->rz_old = 0.0;
+    sc->pq = 0.0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->iter = 0;
+    sc->status = 0;
+    sc->rtol = rtol;
+    sc->flexible = flexible;
+    sc->done = t[0] > 0.0 ? 0 : 1;
+  });
+}
+
+void launch_init_pcg(int n, const double* b, double* x, double* r, PcgScalars* sc, ReduceWs ws,
+                     double rtol, int flexible, cudaStream_t s) {
+  k_init_pcg<<<vec_blocks(n), VB, 0, s>>>(n, b, x, r, sc, ws, rtol, flexible);
+}
+
+__global__ void k_axpby(int n, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, double* __restrict__ out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out,
+                  cudaStream_t s) {
+  k_axpby<<<vec_blocks(n), VB, 0, s>>>(n, a, x, b, y, out);
+}
+
+// ---------------------------------------------------------------------------
+// Permutations between the caller's lexicographic order and curve order.
+__device__ __forceinline__ int lex_id(const GridDev& g, unsigned c) {
+  int id = 0;
+  for (int j = 0; j < g.d; ++j) {
+    const int kj = (int)((c >> g.off[j]) & ((1u << g.lev[j]) - 1u));
+    id += (kj - 1) * g.stride[j];
+  }
+  return id;
+}
+
+__global__ void k_lex_to_curve(GridDev g, const unsigned* __restrict__ code,
+                               const double* __restrict__ in, double* __restrict__ out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride)
+    out[p] = in[lex_id(g, code[p])];
+}
+
+__global__ void k_curve_to_lex(GridDev g, const unsigned* __restrict__ code,
+                               const double* __restrict__ in, double* __restrict__ out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride)
+    out[lex_id(g, code[p])] = in[p];
+}
+
+void launch_lex_to_curve(const GridDev& g, const unsigned* code, const double* in, double* out,
+                         cudaStream_t s) {
+  k_lex_to_curve<<<vec_blocks(g.N), VB, 0, s>>>(g, code, in, out);
+}
+void launch_curve_to_lex(const GridDev& g, const unsigned* code, const double* in, double* out,
+                         cudaStream_t s) {
+  k_curve_to_lex<<<vec_blocks(g.N), VB, 0, s>>>(g, code, in, out);
+}
+
+// ---------------------------------------------------------------------------
+// dL/dc_j = -sum_p lambda_p 4^{l_j} (2 u_p - u_{p-e_j} - u_{p+e_j}), all j in one pass.
+template <int D>
+__global__ void __launch_bounds__(VB) k_grad(GridDev g, const unsigned* __restrict__ code,
+                                             const int* __restrict__ invpad,
+                                             const double* __restrict__ lam,
+                                             const double* __restrict__ u, PcgScalars* sc,
+                                             ReduceWs ws) {
+  double acc[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) acc[j] = 0.0;
+  const int stride = gridDim.x * VB;
+  for (int p = blockIdx.x * VB + threadIdx.x; p < g.N; p += stride) {
+    const unsigned c = code[p];
+    const double up = u[p], lp = lam[p];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
+      const unsigned unit = 1u << g.off[j];
+      double v = 2.0 * up;
+      if (kj > 1u) v -= u[invpad[c - unit]];
+      if (kj < (unsigned)g.size[j]) v -= u[invpad[c + unit]];
+      acc[j] += lp * v;
+    }
+  }
+  reduce_finalize<D>(acc, ws, [&](double* t) {
+    for (int j = 0; j < D; ++j) sc->grad[j] = -ldexp(t[j], 2 * g.lev[j]);
+  });
+}
+
+void launch_grad(const GridDev& g, const unsigned* code, const int* invpad, const double* lam,
+                 const double* u, PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
+  const int nb = vec_blocks(g.N);
+  switch (g.d) {
+    case 1: k_grad<1><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+    case 2: k_grad<2><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+    case 3: k_grad<3><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+    case 4: k_grad<4><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+    case 5: k_grad<5><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+    case 6: k_grad<6><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+    case 7: k_grad<7><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+    default: k_grad<8><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
+  }
+}
+
+}  // namespace sfcdd

@@ -1,0 +1,166 @@
+"""Python handle around the C-ABI: torch tensors provide device memory and the
+stream; every step of the solver runs in the CUDA library."""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import Info, Options, Stats, check
+
+
+def _dev_ptr(t: torch.Tensor, dtype=torch.float64) -> int:
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    return t.data_ptr()
+
+
+class Solver:
+    """Two-level SFC Schwarz-preconditioned CG for the anisotropic FD Poisson
+    operator on levels `levels` with P subdomains and overlap gamma."""
+
+    def __init__(self, levels, P, overlap, *, precision="fp64", variant="additive",
+                 weighting="omega", q=0, coeffs=None, flexible=-1, stream=None):
+        L = _lib.lib()
+        self.levels = tuple(int(l) for l in levels)
+        self.d = len(self.levels)
+        self.P = int(P)
+        self.overlap = float(overlap)
+        self.shape = tuple((1 << l) - 1 for l in self.levels)
+        opt = Options()
+        L.sfcdd_default_options(C.byref(opt))
+        self._coeffs = None
+        if coeffs is not None:
+            vals = [float(c) for c in coeffs]
+            self._coeffs = (C.c_double * self.d)(*vals)
+            opt.coeffs = C.cast(self._coeffs, C.POINTER(C.c_double))
+        opt.q = int(q)
+        opt.variant = _lib.VARIANT[variant]
+        opt.weighting = _lib.WEIGHTING[weighting]
+        opt.precision = _lib.PRECISION[precision]
+        opt.flexible = int(flexible)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = C.c_void_p(stream.cuda_stream)
+        lv = (C.c_int * self.d)(*self.levels)
+        h = C.c_void_p()
+        check("sfcdd_setup_ex", L.sfcdd_setup_ex(lv, self.d, self.P, self.overlap, C.byref(opt),
+                                                  C.byref(h)))
+        self._h = h
+        self._L = L
+        self.info = self.get_info()
+        self.N = int(self.info.N)
+
+    # ---- lifetime ----
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sfcdd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- solves ----
+    def solve(self, f: torch.Tensor, rtol=1e-10, maxit=1000, out=None, check_status=True):
+        f = f.reshape(-1)
+        u = torch.empty_like(f) if out is None else out
+        st = Stats()
+        rc = self._L.sfcdd_solve(self._h, _dev_ptr(f), _dev_ptr(u), float(rtol), int(maxit),
+                                 C.byref(st))
+        self.last_stats = st
+        if check_status:
+            check("sfcdd_solve", rc)
+        return u, st
+
+    def solve_host(self, f, rtol=1e-10, maxit=1000):
+        import numpy as np
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        u = np.empty_like(f)
+        st = Stats()
+        rc = self._L.sfcdd_solve_host(self._h, f.ctypes.data, u.ctypes.data, float(rtol),
+                                      int(maxit), C.byref(st))
+        check("sfcdd_solve_host", rc)
+        return u, st
+
+    def solve_backward(self, u: torch.Tensor, gu: torch.Tensor, rtol=1e-10, maxit=1000):
+        u = u.reshape(-1).contiguous()
+        gu = gu.reshape(-1).contiguous()
+        gf = torch.empty_like(gu)
+        gc = (C.c_double * self.d)()
+        st = Stats()
+        rc = self._L.sfcdd_solve_backward(self._h, _dev_ptr(u), _dev_ptr(gu), _dev_ptr(gf), gc,
+                                          float(rtol), int(maxit), C.byref(st))
+        check("sfcdd_solve_backward", rc)
+        return gf, [gc[j] for j in range(self.d)], st
+
+    def apply_operator(self, x: torch.Tensor, curve_order=False):
+        y = torch.empty_like(x)
+        check("sfcdd_apply_operator",
+              self._L.sfcdd_apply_operator(self._h, _dev_ptr(x), _dev_ptr(y), int(curve_order)))
+        return y
+
+    def apply_precond(self, g: torch.Tensor, curve_order=False):
+        z = torch.empty_like(g)
+        check("sfcdd_apply_precond",
+              self._L.sfcdd_apply_precond(self._h, _dev_ptr(g), _dev_ptr(z), int(curve_order)))
+        return z
+
+    # ---- introspection ----
+    def get_info(self) -> Info:
+        info = Info()
+        check("sfcdd_get_info", self._L.sfcdd_get_info(self._h, C.byref(info)))
+        return info
+
+    def curve(self):
+        keys = torch.empty(self.N, dtype=torch.int64, device="cuda")
+        perm = torch.empty(self.N, dtype=torch.int32, device="cuda")
+        check("sfcdd_get_curve", self._L.sfcdd_get_curve(self._h, keys.data_ptr(), perm.data_ptr()))
+        return keys, perm
+
+    def partition(self):
+        import numpy as np
+        start = np.zeros(self.P, dtype=np.int64)
+        length = np.zeros(self.P, dtype=np.int64)
+        omega = np.zeros(self.P, dtype=np.float64)
+        check("sfcdd_get_partition", self._L.sfcdd_get_partition(
+            self._h, start.ctypes.data_as(C.POINTER(C.c_longlong)),
+            length.ctypes.data_as(C.POINTER(C.c_longlong)),
+            omega.ctypes.data_as(C.POINTER(C.c_double))))
+        return start, length, omega
+
+    def coarse_matrix(self):
+        n0 = int(self.info.N0)
+        A0 = torch.empty(n0 * n0, dtype=torch.float64, device="cuda")
+        check("sfcdd_get_coarse_matrix", self._L.sfcdd_get_coarse_matrix(self._h, A0.data_ptr()))
+        return A0.reshape(n0, n0)
+
+    def local_matrix(self, i: int):
+        _, length, _ = self.partition()
+        n = int(length[i])
+        Ai = torch.empty(n * n, dtype=torch.float64, device="cuda")
+        check("sfcdd_get_local_matrix", self._L.sfcdd_get_local_matrix(self._h, int(i), Ai.data_ptr()))
+        return Ai.reshape(n, n)
+
+    def set_profiling(self, on: bool):
+        check("sfcdd_set_profiling", self._L.sfcdd_set_profiling(self._h, int(bool(on))))
+
+    def kernel_stats(self, reset=False):
+        n = len(_lib.KERNEL_CLASSES)
+        ms = (C.c_double * n)()
+        la = (C.c_longlong * n)()
+        check("sfcdd_get_kernel_stats", self._L.sfcdd_get_kernel_stats(self._h, ms, la, int(reset)))
+        return {k: (ms[i], la[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)}
+
+    def kernel_work(self, cls: str) -> float:
+        return float(self._L.sfcdd_kernel_work(self._h, _lib.KERNEL_CLASSES.index(cls)))
