@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark: time to relative residual 1e-10 of the two-level SFC Schwarz PCG
+solve (setup + solve), on seeded synthetic inputs, through the C-ABI library.
+
+A step is one pass of the whole path over one right-hand side: Hilbert keys,
+radix sort, partition, local and coarse assembly + Cholesky, then PCG to
+rtol = 1e-10 (stencil, restriction, batched substitutions, prolongation,
+fused reductions).  Default workload: the 1023 x 31 x 7 anisotropic grid
+(levels 10,5,3; N = 221,991), P = 128, gamma = 1, FP64 local factors.
+
+`--impl reference` times the oracle (plain FP64 CPU implementation) on the
+host cores instead, on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank solves its own replica (independent problems,
+no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2110_11211_gb300 import inputs  # noqa: E402
+
+METRIC = "time to rel. residual 1e-10 (ms) & precond applies/s; FP64 vs mixed/batched"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="aniso3d_l10x5x3_P128", choices=list(inputs.WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "bf16"])
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP32/BF16 comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=4, help="local subdomains the oracle factors")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# FP64 and FP32 CUDA-core peaks from unit counts and clocks: 152 SMs x 2070 MHz
+# x 2 flops per FMA x (FP64: 1.25e12 nominal GPU total; FP32: 128 lanes per SM).
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        load = [r for r in rows if (num(r[4]) or 0) >= 50] or rows
+        sm = [num(r[1]) for r in load if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max((num(r[2]) or 0) for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_args(name, precision):
+    w = inputs.WORKLOADS[name]
+    if w["levels"] is None:
+        raise SystemExit(f"{name} is a batched set, not a single-solve workload")
+    return dict(levels=w["levels"], P=w["P"], gamma=w["gamma"],
+                precision=precision or w["precision"], coeffs=inputs.coefficients(name))
+
+
+def cpu_baseline(name, wl, iters, sample):
+    """The oracle as it stands, on a bounded sample: full grid operator, curve and
+    partition, the FP64 coarse factorization, `sample` of the P local Cholesky
+    factorizations and solves; scaled to all P subdomains and the GPU's iteration
+    count (time = setup + iters * (local solves + coarse solve + operator))."""
+    import numpy as np
+    from oracle import schwarz
+    levels, P, gamma = wl["levels"], wl["P"], wl["gamma"]
+    t0 = time.perf_counter()
+    S = schwarz.Schwarz(levels, P, gamma, coeffs=wl["coeffs"], cache_factors=False)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    S.coarse_factor()
+    t_coarse_fac = time.perf_counter() - t0
+    f = inputs.rhs(name)
+    idx = np.linspace(0, P - 1, sample).round().astype(int)
+    t_fac = t_sol = 0.0
+    for i in idx:
+        t0 = time.perf_counter()
+        fac = S.local_factor(i)
+        t_fac += time.perf_counter() - t0
+        ids = S.local_ids(i)
+        t0 = time.perf_counter()
+        import scipy.linalg as sla
+        sla.cho_solve(fac, f[ids], check_finite=False)
+        t_sol += time.perf_counter() - t0
+    t0 = time.perf_counter()
+    S.coarse_correction(f)
+    y = S.A @ f
+    t_iter_other = time.perf_counter() - t0
+    setup = t_build + t_coarse_fac + t_fac / len(idx) * P
+    per_it = t_sol / len(idx) * P + t_iter_other
+    total_ms = 1e3 * (setup + iters * per_it)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    del y
+    return {"value": round(total_ms, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle setup (operator, curve, partition, coarse FP64 Cholesky) in full; "
+                       f"{len(idx)} of {P} local Cholesky factorizations and solves, scaled to "
+                       f"{P}; {iters} iterations (the GPU run's count) of local solves + coarse "
+                       f"solve + operator"),
+            "measured_s": round(t_build + t_coarse_fac + t_fac + t_sol + t_iter_other, 2)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload_args(args.workload, args.precision)
+    # the oracle's own PCG iteration count for this workload (full oracle run,
+    # written by tests/golden/make_oracle_pcg.py)
+    gpath = os.path.join(ROOT, "tests", "golden", f"oracle_pcg_{args.workload}.json")
+    if not os.path.exists(gpath):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no oracle iteration count stored for {args.workload}"}), flush=True)
+        return
+    with open(gpath) as fh:
+        iters = int(json.load(fh)["iters"])
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.workload, wl, iters, max(1, min(args.cpu_sample, 2)))
+        if k >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    cb["value"] = round(v, 1)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "levels": list(wl["levels"]), "P": wl["P"],
+                       "gamma": wl["gamma"], "rtol": args.rtol},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2110_11211_gb300.solver import Solver
+
+    world, rank, local = dist_setup()
+    wl = workload_args(args.workload, args.precision)
+    levels, P, gamma, prec, coeffs = wl["levels"], wl["P"], wl["gamma"], wl["precision"], wl["coeffs"]
+    f_np = inputs.rhs(args.workload)
+    N = f_np.size
+    f = torch.tensor(f_np, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(profile):
+        s = Solver(levels, P, gamma, precision=prec, coeffs=coeffs, profile=profile)
+        u, st = s.solve(f, rtol=args.rtol)
+        ks = s.kernel_stats()
+        work = {k: s.kernel_work(k) for k in ("trsv_fwd", "trsv_bwd", "stencil", "potrf", "trsm",
+                                              "syrk", "coarse_factor")}
+        info = s.get_info()
+        s.close()
+        return u, st, ks, work, info
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    iters, setup_ms, solve_ms = [], [], []
+    agg = {}
+    for _ in range(args.steps):
+        u, st, ks, work, info = step(True)
+        iters.append(st.iters)
+        setup_ms.append(st.setup_ms)
+        solve_ms.append(st.solve_ms)
+        for k, (ms, n) in ks.items():
+            a = agg.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = max_over_ranks(world, ms_step)
+    u64 = u.detach()
+
+    # end to end through the public C-ABI with host buffers (pinned), same metric
+    f_pin = torch.tensor(f_np).pin_memory()
+    e2e_ms = []
+    for k in range(1 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = Solver(levels, P, gamma, precision=prec, coeffs=coeffs)
+        uh, st_h = s.solve_host(f_pin.numpy(), rtol=args.rtol)
+        s.close()
+        t1 = time.perf_counter()
+        if k >= 1:
+            e2e_ms.append(1e3 * (t1 - t0))
+    e2e = max_over_ranks(world, statistics.mean(e2e_ms))
+
+    # mixed-precision variants of the same workload
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for vp in ("fp32", "bf16"):
+            if vp == prec:
+                continue
+            times = []
+            for k in range(3):
+                torch.cuda.synchronize()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                s = Solver(levels, P, gamma, precision=vp, coeffs=coeffs)
+                uv, stv = s.solve(f, rtol=args.rtol)
+                s.close()
+                a1.record(stream)
+                torch.cuda.synchronize()
+                if k >= 1:
+                    times.append(a0.elapsed_time(a1))
+            err = float(torch.linalg.norm(uv - u64) / torch.linalg.norm(u64))
+            variants[vp] = {"ms": round(statistics.mean(times), 2), "iters": stv.iters,
+                            "setup_ms": round(stv.setup_ms, 2), "solve_ms": round(stv.solve_ms, 2),
+                            "applies_per_s": round(stv.iters / (stv.solve_ms / 1e3), 1),
+                            "rel_diff_vs_fp64_solution": err, "true_rel_res": stv.true_rel_res}
+
+    hbm_peak, bf16_peak, peak_src = load_peaks()
+    steps = args.steps
+    kernels = {}
+    for k, (ms, n) in agg.items():
+        if n == 0:
+            continue
+        kernels[k] = {"ms_per_step": round(ms / steps, 3), "launches_per_step": n / steps}
+    # roofline of the dominant kernel class (largest device time in the timed region)
+    timed = {k: v for k, v in agg.items() if v[0] > 0}
+    dom = max(timed, key=lambda k: timed[k][0])
+    dom_ms, dom_n = timed[dom]
+    if dom in ("trsv_fwd", "trsv_bwd"):
+        per_launch = work[dom]
+        achieved = per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+        roof = {"bound": "hbm", "peak": hbm_peak, "unit": "GB/s"}
+    elif dom == "stencil":
+        per_launch = work[dom]
+        achieved = per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+        roof = {"bound": "hbm", "peak": hbm_peak, "unit": "GB/s"}
+    else:
+        # factorization classes: operations per setup / device time per setup
+        launches_per_setup = dom_n / steps
+        per_launch = work.get(dom, 0.0) / launches_per_setup
+        achieved = per_launch / (dom_ms / dom_n * 1e-3) / 1e12
+        fp64 = prec == "fp64" or dom == "coarse_factor"
+        roof = {"bound": "alu", "peak": FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s"}
+    roof.update({"kernel": dom, "achieved": round(achieved, 3),
+                 "frac": round(achieved / roof["peak"], 4), "traffic": None,
+                 "work_per_launch": per_launch, "avg_launch_ms": round(dom_ms / dom_n, 4),
+                 "peak_source": peak_src if roof["bound"] == "hbm" else "nominal (unit counts x clock)"})
+    # substitution roofline (the per-iteration dominant kernel)
+    trsv = {}
+    for k in ("trsv_fwd", "trsv_bwd"):
+        if k in timed:
+            ms, n = timed[k]
+            gbs = work[k] / (ms / n * 1e-3) / 1e9
+            trsv[k] = {"GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
+                       "bytes_per_launch": work[k], "avg_launch_ms": round(ms / n, 4)}
+    if "stencil" in timed:
+        ms, n = timed["stencil"]
+        trsv["stencil"] = {"GB/s_algorithmic": round(work["stencil"] / (ms / n * 1e-3) / 1e9, 1),
+                           "avg_launch_ms": round(ms / n, 4)}
+    launches = sum(n for (_, n) in agg.values()) / steps
+    it = statistics.mean(iters)
+    sol = statistics.mean(solve_ms)
+    line = {
+        "metric": METRIC, "value": round(ms_step, 2), "unit": "ms", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 2),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[prec],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "levels": list(levels), "N": N, "P": P,
+                   "gamma": gamma, "q": int(info.q), "N0": int(info.N0), "precision": prec,
+                   "rtol": args.rtol, "rhs": inputs.WORKLOADS[args.workload]["rhs"],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": (f"working set > L2: {info.factor_bytes / 1e9:.1f} GB of factors "
+                          "re-streamed every apply; every step re-assembles and re-factors")},
+        "iters": it, "setup_ms": round(statistics.mean(setup_ms), 2), "solve_ms": round(sol, 2),
+        "applies_per_s": round(it / (sol / 1e3), 1),
+        "clocks": clk,
+        "e2e": {"value": round(e2e, 2), "unit": "ms", "h2d_bytes_per_step": 8 * N,
+                "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": int(round(launches)),
+        "roofline": roof,
+        "kernels": kernels,
+        "hot_loop": trsv,
+        "variants": variants,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, wl, int(round(it)), args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -62,6 +62,8 @@ typedef struct {
   int flexible;         /* PCG beta: 0 = r^T z ratio, 1 = Polak-Ribiere (flexible CG, Sec. 3.3),
                            < 0 = automatic (flexible for FP32 / BF16 local factors) */
   void* stream;         /* cudaStream_t for all work of this handle; NULL = legacy default stream */
+  int profile;          /* != 0: time every kernel launch of setup and solves with CUDA events
+                           (see sfcdd_set_profiling); 0 (default): no events */
 } sfcdd_options;
 
 typedef struct {
@@ -161,7 +163,8 @@ int sfcdd_get_local_matrix(const sfcdd_handle* h, int i, double* Ai_dev);
 enum sfcdd_kernel_class {
   SFCDD_K_KEYGEN = 0, SFCDD_K_SORT, SFCDD_K_ASSEMBLE, SFCDD_K_POTRF, SFCDD_K_TRSM, SFCDD_K_SYRK,
   SFCDD_K_COARSE_ASSEMBLE, SFCDD_K_STENCIL, SFCDD_K_UPDATE, SFCDD_K_RESTRICT, SFCDD_K_TRSV_FWD,
-  SFCDD_K_TRSV_BWD, SFCDD_K_PROLONG, SFCDD_K_VECTOR, SFCDD_K_GRAD, SFCDD_K_COUNT
+  SFCDD_K_TRSV_BWD, SFCDD_K_PROLONG, SFCDD_K_VECTOR, SFCDD_K_GRAD, SFCDD_K_COARSE_FACTOR,
+  SFCDD_K_COUNT
 };
 int sfcdd_set_profiling(sfcdd_handle* h, int enable);
 /* ms_total, launches: host arrays of SFCDD_K_COUNT entries (either may be NULL);
@@ -169,8 +172,10 @@ int sfcdd_set_profiling(sfcdd_handle* h, int enable);
 int sfcdd_get_kernel_stats(sfcdd_handle* h, double* ms_total, long long* launches, int reset);
 /* Algorithmic bytes (or FP operations) one launch of the class processes for
  * this handle: SFCDD_K_TRSV_FWD / _BWD: factor + coarse tile bytes;
- * SFCDD_K_STENCIL: 16 N; SFCDD_K_SYRK / _POTRF / _TRSM: flops of the whole
- * factorization (sum over steps).  Returns 0 for classes without a figure. */
+ * SFCDD_K_STENCIL: 16 N; SFCDD_K_POTRF / _TRSM / _SYRK: floating-point
+ * operations of that part of the local factorizations summed over all launches
+ * of one setup; SFCDD_K_COARSE_FACTOR: all operations of the coarse
+ * factorization.  Returns 0 for classes without a figure. */
 double sfcdd_kernel_work(const sfcdd_handle* h, int kernel_class);
 
 int sfcdd_destroy(sfcdd_handle* h);

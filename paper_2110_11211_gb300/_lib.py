@@ -21,7 +21,7 @@ VARIANT = {"additive": 0, "balanced": 1, "one_level": 2, "coarse_only": 3}
 WEIGHTING = {"none": 0, "omega": 1}
 KERNEL_CLASSES = ["keygen", "sort", "assemble", "potrf", "trsm", "syrk", "coarse_assemble",
                   "stencil", "update", "restrict", "trsv_fwd", "trsv_bwd", "prolong", "vector",
-                  "grad"]
+                  "grad", "coarse_factor"]
 
 # Every exported function the header declares (checked by a CPU test).
 EXPORTS = [
@@ -36,7 +36,7 @@ EXPORTS = [
 class Options(C.Structure):
     _fields_ = [("coeffs", C.POINTER(C.c_double)), ("q", C.c_int), ("variant", C.c_int),
                 ("weighting", C.c_int), ("precision", C.c_int), ("flexible", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("profile", C.c_int)]
 
 
 class Stats(C.Structure):

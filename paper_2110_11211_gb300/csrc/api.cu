@@ -80,6 +80,7 @@ struct sfcdd_handle {
   double ms[SFCDD_K_COUNT] = {0};
   double setup_ms = 0, solve_ms = 0;
   double factor_flops = 0;
+  double work_potrf = 0, work_trsm = 0, work_syrk = 0, work_coarse = 0;
   std::vector<void*> allocs;
 };
 
@@ -114,25 +115,35 @@ void dfree(sfcdd_handle* h, void* p) {
     if (_rc != SFCDD_OK) return _rc; \
   } while (0)
 
-// Event-bracketed launch accounting.
-struct Prof {
+// Launch accounting: counts launches per class and, when profiling, brackets
+// each launch with CUDA events on the launching stream.
+struct Prof : LaunchHook {
   sfcdd_handle* h;
   cudaStream_t s;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> evs;
+  cudaEvent_t pending = nullptr;
+  Prof(sfcdd_handle* h_, cudaStream_t s_) : h(h_), s(s_) {}
+  void before(int cls) override {
+    h->launches[cls] += 1;
+    if (h->profiling) {
+      cudaEventCreate(&pending);
+      cudaEventRecord(pending, s);
+    }
+  }
+  void after(int cls) override {
+    if (h->profiling && pending) {
+      cudaEvent_t b;
+      cudaEventCreate(&b);
+      cudaEventRecord(b, s);
+      evs.push_back({cls, {pending, b}});
+      pending = nullptr;
+    }
+  }
   template <class F>
   void run(int cls, F&& f) {
-    h->launches[cls] += 1;
-    if (!h->profiling) {
-      f();
-      return;
-    }
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, s);
+    before(cls);
     f();
-    cudaEventRecord(b, s);
-    evs.push_back({cls, {a, b}});
+    after(cls);
   }
   void collect() {
     for (auto& e : evs) {
@@ -145,6 +156,15 @@ struct Prof {
     }
     evs.clear();
   }
+  ~Prof() override { collect(); }
+};
+
+// Routes every factorization class of the coarse matrix to one class.
+struct CoarseHook : LaunchHook {
+  Prof& p;
+  explicit CoarseHook(Prof& p_) : p(p_) {}
+  void before(int) override { p.before(SFCDD_K_COARSE_FACTOR); }
+  void after(int) override { p.after(SFCDD_K_COARSE_FACTOR); }
 };
 
 TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalars* sc) {
@@ -208,7 +228,7 @@ int build_graph(sfcdd_handle* h) {
   const bool prof = h->profiling;
   h->profiling = false;
   SFCDD_CUDA_OK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  Prof pf{h, h->cap_stream, {}};
+  Prof pf(h, h->cap_stream);
   enqueue_iteration(h, pf);
   cudaGraph_t graph;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -335,6 +355,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   if (h->variant == SFCDD_BALANCED) return SFCDD_ERR_UNSUPPORTED;
   h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
   h->stream = (cudaStream_t)o.stream;
+  h->profiling = o.profile != 0;
   const long long fN = N / P;
   if (o.q <= 0) {
     int e = 0;
@@ -385,14 +406,15 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   TRY(dalloc(h, &h->curve_code, N));
   TRY(dalloc(h, (unsigned char**)&sort_tmp, radix_sort_temp_bytes(h->N)));
   TRY(dalloc(h, &h->invpad, (size_t)1 << B));
-  h->launches[SFCDD_K_KEYGEN] += 1;
-  launch_keygen(g, keys, h->curve_code, s);
+  Prof pf(h, s);
+  pf.run(SFCDD_K_KEYGEN, [&] { launch_keygen(g, keys, h->curve_code, s); });
   int sort_launches = 0;
-  radix_sort_pairs(keys, h->curve_code, h->N, d * nbits, sort_tmp, s, &sort_launches);
+  pf.run(SFCDD_K_SORT, [&] {
+    radix_sort_pairs(keys, h->curve_code, h->N, d * nbits, sort_tmp, s, &sort_launches);
+    cudaMemsetAsync(h->invpad, 0xff, ((size_t)1 << B) * sizeof(int), s);
+    launch_invpad_fill(h->curve_code, h->invpad, h->N, s);
+  });
   h->launches[SFCDD_K_SORT] += sort_launches;
-  SFCDD_CUDA_OK(cudaMemsetAsync(h->invpad, 0xff, ((size_t)1 << B) * sizeof(int), s));
-  launch_invpad_fill(h->curve_code, h->invpad, h->N, s);
-  h->launches[SFCDD_K_SORT] += 1;
   SFCDD_CUDA_OK(cudaGetLastError());
 
   // Algorithm 1, steps 4-5: partition, overlap, weights
@@ -468,43 +490,58 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   void* work_tiles = nullptr;
   TRY(dalloc(h, (unsigned char**)&work_tiles, h->ltile_elems * esz));
   if (h->variant != SFCDD_COARSE_ONLY) {
-    h->launches[SFCDD_K_ASSEMBLE] += 1;
-    launch_assemble_local(g, pd, h->curve_code, h->invpad, h->ts, 0, P, h->max_ltiles, work_tiles,
-                          compute_st, s);
-    int fl[SFCDD_K_COUNT] = {0};
-    factor_tiles(h->ts, 0, P, h->max_nt, work_tiles, compute_st, h->err, s, fl, nullptr, 0);
-    for (int k = 0; k < SFCDD_K_COUNT; ++k) h->launches[k] += fl[k];
+    pf.run(SFCDD_K_ASSEMBLE, [&] {
+      launch_assemble_local(g, pd, h->curve_code, h->invpad, h->ts, 0, P, h->max_ltiles,
+                            work_tiles, compute_st, s);
+    });
+    factor_tiles(h->ts, 0, P, h->max_nt, work_tiles, compute_st, h->err, s, &pf);
   }
   if (h->st == Store::BF16) {
     TRY(dalloc(h, (__nv_bfloat16**)&h->ltiles, h->ltile_elems));
-    launch_convert_f32_bf16((const float*)work_tiles, (__nv_bfloat16*)h->ltiles, h->ltile_elems, s);
-    h->launches[SFCDD_K_VECTOR] += 1;
+    pf.run(SFCDD_K_VECTOR, [&] {
+      launch_convert_f32_bf16((const float*)work_tiles, (__nv_bfloat16*)h->ltiles, h->ltile_elems, s);
+    });
     SFCDD_CUDA_OK(cudaStreamSynchronize(s));
     dfree(h, work_tiles);
   } else {
     h->ltiles = work_tiles;
   }
-  // flops of the local factorizations: sum_i n_i^3 / 3 (padded tiles)
+  // operation counts of the tiled factorization as executed (padded tiles):
+  // per step k, the diagonal Cholesky + inverse (2 TILE^3 / 3), the panel
+  // (rows * 2 TILE^3) and the trailing update (rows (rows+1)/2 * 2 TILE^3)
+  auto count_factor = [&](int nt, double& po, double& tr, double& sy) {
+    const double t3 = (double)TILE * TILE * TILE;
+    for (int k = 0; k < nt; ++k) {
+      const double rows = nt - k - 1;
+      po += 2.0 * t3 / 3.0;
+      tr += rows * 2.0 * t3;
+      sy += rows * (rows + 1) / 2.0 * 2.0 * t3;
+    }
+  };
   h->factor_flops = 0;
-  for (int m = 0; m < P; ++m) {
-    const double n = (double)h->h_nt[m] * TILE;
-    h->factor_flops += n * n * n / 3.0;
+  if (h->variant != SFCDD_COARSE_ONLY)
+    for (int m = 0; m < P; ++m) count_factor(h->h_nt[m], h->work_potrf, h->work_trsm, h->work_syrk);
+  h->factor_flops = h->work_potrf + h->work_trsm + h->work_syrk;
+  if (h->variant != SFCDD_ONE_LEVEL) {
+    double a = 0, b2 = 0, c = 0;
+    count_factor(h->nt0, a, b2, c);
+    h->work_coarse = a + b2 + c;
   }
 
   // Algorithm 1, steps 9-10: coarse matrix and its FP64 factor
   TRY(dalloc(h, &h->ctiles, h->ctile_elems));
   if (h->variant != SFCDD_ONE_LEVEL) {
-    h->launches[SFCDD_K_COARSE_ASSEMBLE] += 1;
-    launch_assemble_coarse(g, pd, h->curve_code, h->invpad, h->N0, h->nt0, h->ctiles, nullptr, s);
+    pf.run(SFCDD_K_COARSE_ASSEMBLE, [&] {
+      launch_assemble_coarse(g, pd, h->curve_code, h->invpad, h->N0, h->nt0, h->ctiles, nullptr, s);
+    });
     // the coarse matrix is factored as a one-matrix tile set with base 0
     TileSetDev cts = h->ts;
     cts.nmat = 1;
     cts.n = h->d_n + P;
     cts.nt = h->d_nt + P;
     cts.tbase = h->d_zero64;
-    int fl[SFCDD_K_COUNT] = {0};
-    factor_tiles(cts, 0, 1, h->nt0, h->ctiles, Store::F64, h->err, s, fl, nullptr, 0);
-    for (int k = 0; k < SFCDD_K_COUNT; ++k) h->launches[k] += fl[k];
+    CoarseHook ch(pf);
+    factor_tiles(cts, 0, 1, h->nt0, h->ctiles, Store::F64, h->err, s, &ch);
   }
   SFCDD_CUDA_OK(cudaGetLastError());
 
@@ -560,6 +597,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
 
   SFCDD_CUDA_OK(cudaEventRecord(e1, s));
   SFCDD_CUDA_OK(cudaEventSynchronize(e1));
+  pf.collect();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   h->setup_ms = ms;
@@ -598,7 +636,7 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats) {
   SFCDD_CUDA_OK(cudaEventCreate(&e0));
   SFCDD_CUDA_OK(cudaEventCreate(&e1));
   SFCDD_CUDA_OK(cudaEventRecord(e0, s));
-  Prof pf{h, s, {}};
+  Prof pf(h, s);
   pf.run(SFCDD_K_VECTOR, [&] { launch_init_pcg(h->N, h->b, h->x, h->r, h->sc, h->ws, rtol, h->flexible, s); });
   SFCDD_CUDA_OK(cudaMemsetAsync(h->p, 0, (size_t)h->N * sizeof(double), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->z, 0, (size_t)h->N * sizeof(double), s));
@@ -667,6 +705,7 @@ void sfcdd_default_options(sfcdd_options* opt) {
   opt->precision = SFCDD_FP64;
   opt->flexible = -1;
   opt->stream = nullptr;
+  opt->profile = 0;
 }
 
 int sfcdd_setup_ex(const int* levels, int d, int P, double overlap, const sfcdd_options* opt,
@@ -748,7 +787,7 @@ int sfcdd_solve_backward(sfcdd_handle* h, const double* u_dev, const double* gu_
 int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, int curve_order) {
   if (!h || !x_dev || !y_dev) return SFCDD_ERR_INVALID_ARG;
   cudaStream_t s = h->stream;
-  Prof pf{h, s, {}};
+  Prof pf(h, s);
   if (curve_order) {
     pf.run(SFCDD_K_STENCIL, [&] { launch_stencil(h->g, h->curve_code, h->invpad, x_dev, y_dev, 0, nullptr, h->ws, s); });
   } else {
@@ -765,7 +804,7 @@ int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, in
 int sfcdd_apply_precond(sfcdd_handle* h, const double* g_dev, double* z_dev, int curve_order) {
   if (!h || !g_dev || !z_dev) return SFCDD_ERR_INVALID_ARG;
   cudaStream_t s = h->stream;
-  Prof pf{h, s, {}};
+  Prof pf(h, s);
   if (curve_order) {
     enqueue_apply(h, pf, g_dev, z_dev, nullptr);
   } else {
@@ -906,9 +945,13 @@ double sfcdd_kernel_work(const sfcdd_handle* h, int kc) {
     case SFCDD_K_STENCIL:
       return 16.0 * (double)h->N;
     case SFCDD_K_POTRF:
+      return h->work_potrf;
     case SFCDD_K_TRSM:
+      return h->work_trsm;
     case SFCDD_K_SYRK:
-      return h->factor_flops;
+      return h->work_syrk;
+    case SFCDD_K_COARSE_FACTOR:
+      return h->work_coarse;
     default:
       return 0.0;
   }

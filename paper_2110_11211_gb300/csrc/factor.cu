@@ -318,35 +318,34 @@ __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* 
 
 template <class T>
 static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt, T* tiles,
-                           ErrWord* err, cudaStream_t s, int* launches) {
+                           ErrWord* err, cudaStream_t s, LaunchHook* hook) {
   const int sm_potrf = (2 * TILE + 1) * (TILE + 1) * (int)sizeof(T);
   const int sm_gemm = 2 * TILE * (TILE + 4) * (int)sizeof(T);
   cudaFuncSetAttribute(k_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_potrf);
   cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_gemm);
   cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_gemm);
   for (int k = 0; k < max_nt; ++k) {
+    hook->before(SFCDD_K_POTRF);
     k_potrf<T><<<nmat, FB, sm_potrf, s>>>(ts, mat0, k, tiles, err);
+    hook->after(SFCDD_K_POTRF);
     const int rows = max_nt - k - 1;
     if (rows > 0) {
+      hook->before(SFCDD_K_TRSM);
       k_trsm<T><<<dim3(rows, nmat), FB, sm_gemm, s>>>(ts, mat0, k, tiles);
+      hook->after(SFCDD_K_TRSM);
+      hook->before(SFCDD_K_SYRK);
       k_syrk<T><<<dim3(rows * (rows + 1) / 2, nmat), FB, sm_gemm, s>>>(ts, mat0, k, tiles);
-      if (launches) {
-        launches[SFCDD_K_TRSM] += 1;
-        launches[SFCDD_K_SYRK] += 1;
-      }
+      hook->after(SFCDD_K_SYRK);
     }
-    if (launches) launches[SFCDD_K_POTRF] += 1;
   }
 }
 
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, void* tiles, Store st,
-                  ErrWord* err, cudaStream_t s, int* launches, cudaEvent_t* evs, int nev_pairs) {
-  (void)evs;
-  (void)nev_pairs;
+                  ErrWord* err, cudaStream_t s, LaunchHook* hook) {
   if (st == Store::F64)
-    factor_tiles_t<double>(ts, mat0, nmat, max_nt, (double*)tiles, err, s, launches);
+    factor_tiles_t<double>(ts, mat0, nmat, max_nt, (double*)tiles, err, s, hook);
   else
-    factor_tiles_t<float>(ts, mat0, nmat, max_nt, (float*)tiles, err, s, launches);
+    factor_tiles_t<float>(ts, mat0, nmat, max_nt, (float*)tiles, err, s, hook);
 }
 
 __global__ void k_convert_f32_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,

@@ -145,6 +145,14 @@ void launch_axpby(int n, double a, const double* x, double b, const double* y, d
 void launch_grad(const GridDev& g, const unsigned* code, const int* invpad, const double* lam,
                  const double* u, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
 
+// Launch accounting hook (implemented by the API layer): counts launches per
+// kernel class and, when profiling, brackets them with CUDA events.
+struct LaunchHook {
+  virtual void before(int cls) = 0;
+  virtual void after(int cls) = 0;
+  virtual ~LaunchHook() {}
+};
+
 // factor.cu
 enum class Store { F64 = 0, F32 = 1, BF16 = 2 };
 void launch_assemble_local(const GridDev& g, const PartDev& pd, const unsigned* code,
@@ -156,7 +164,7 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 // Blocked right-looking Cholesky of matrices [mat0, mat0+nmat) of the tile set,
 // in place; diagonal slots end up holding the inverse of the factor's diagonal block.
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, void* tiles, Store st,
-                  ErrWord* err, cudaStream_t s, int* launches, cudaEvent_t* evs, int nev_pairs);
+                  ErrWord* err, cudaStream_t s, LaunchHook* hook);
 void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, cudaStream_t s);
 void launch_unpack_dense(const TileSetDev& ts, int m, const double* tiles, double* dense,
                          cudaStream_t s);

@@ -21,7 +21,8 @@ class Solver:
     operator on levels `levels` with P subdomains and overlap gamma."""
 
     def __init__(self, levels, P, overlap, *, precision="fp64", variant="additive",
-                 weighting="omega", q=0, coeffs=None, flexible=-1, stream=None):
+                 weighting="omega", q=0, coeffs=None, flexible=-1, stream=None,
+                 profile=False):
         L = _lib.lib()
         self.levels = tuple(int(l) for l in levels)
         self.d = len(self.levels)
@@ -40,6 +41,7 @@ class Solver:
         opt.weighting = _lib.WEIGHTING[weighting]
         opt.precision = _lib.PRECISION[precision]
         opt.flexible = int(flexible)
+        opt.profile = int(bool(profile))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
