@@ -181,6 +181,27 @@ double sfcdd_kernel_work(const sfcdd_handle* h, int kernel_class);
 int sfcdd_destroy(sfcdd_handle* h);
 const char* sfcdd_status_string(int status);
 
+/* Curve order without any device allocation (the paper has no counterpart: it
+ * is a deployment variant of the key generation and sort of Algorithm 1,
+ * step 3).  For callers that cannot call cudaMalloc: code running while a
+ * stream is being captured into a CUDA graph, hosts that hand out all device
+ * memory from their own pool, and latency-critical code that must not hit the
+ * device synchronisation of cudaMalloc/cudaFree.
+ * Outputs (caller-owned device buffers): keys_dev, N uint64 Hilbert keys by
+ * lexicographic id; perm_dev, N int32 with perm[pos] = lexicographic id at
+ * curve position pos -- the same values sfcdd_get_curve returns.
+ * Scratch: a file-scope device array of about 6.4 MB, resident on every GPU
+ * that loads the library until the process exits; N may be at most 262,144
+ * (2^18) grid points, larger grids return SFCDD_ERR_INVALID_ARG with a message
+ * on stderr.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make that first call before
+ * any stream capture.  All calls share the one array, so calls that overlap on
+ * the GPU (other streams, other host threads) race; serialise them.  Work is
+ * issued on `stream` (cudaStream_t, NULL = legacy default stream) and is not
+ * synchronised.  Errors: INVALID_ARG, KEY_OVERFLOW, UNSUPPORTED, CUDA. */
+int sfcdd_curve_order_noalloc(const int* levels, int d, unsigned long long* keys_dev, int* perm_dev,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ EXPORTS = [
     "sfcdd_solve_backward", "sfcdd_apply_operator", "sfcdd_apply_precond", "sfcdd_get_info",
     "sfcdd_get_curve", "sfcdd_get_partition", "sfcdd_get_coarse_matrix", "sfcdd_get_local_matrix",
     "sfcdd_set_profiling", "sfcdd_get_kernel_stats", "sfcdd_kernel_work", "sfcdd_destroy",
-    "sfcdd_status_string",
+    "sfcdd_status_string", "sfcdd_curve_order_noalloc",
 ]
 
 
@@ -98,6 +98,7 @@ def lib() -> C.CDLL:
     L.sfcdd_destroy.argtypes = [H]
     L.sfcdd_status_string.argtypes = [C.c_int]
     L.sfcdd_status_string.restype = C.c_char_p
+    L.sfcdd_curve_order_noalloc.argtypes = [C.POINTER(C.c_int), C.c_int, P, P, C.c_void_p]
     for name in EXPORTS:
         if name not in ("sfcdd_default_options", "sfcdd_kernel_work", "sfcdd_status_string"):
             getattr(L, name).restype = C.c_int
