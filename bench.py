@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP32/BF16 comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4, help="local subdomains the oracle factors")
+    ap.add_argument("--levels", default=None, help="custom grid levels, e.g. 8,5,3 (profiling runs)")
+    ap.add_argument("--P", type=int, default=None, help="custom subdomain count")
+    ap.add_argument("--gamma", type=float, default=None, help="custom overlap")
     return ap.parse_args()
 
 
@@ -146,12 +149,20 @@ def max_over_ranks(world, v):
     return float(t.item())
 
 
-def workload_args(name, precision):
+def workload_args(name, precision, args=None):
     w = inputs.WORKLOADS[name]
     if w["levels"] is None:
         raise SystemExit(f"{name} is a batched set, not a single-solve workload")
-    return dict(levels=w["levels"], P=w["P"], gamma=w["gamma"],
-                precision=precision or w["precision"], coeffs=inputs.coefficients(name))
+    out = dict(levels=w["levels"], P=w["P"], gamma=w["gamma"],
+               precision=precision or w["precision"], coeffs=inputs.coefficients(name))
+    if args is not None and args.levels:
+        out["levels"] = tuple(int(v) for v in args.levels.split(","))
+        out["coeffs"] = None
+    if args is not None and args.P:
+        out["P"] = args.P
+    if args is not None and args.gamma:
+        out["gamma"] = args.gamma
+    return out
 
 
 def cpu_baseline(name, wl, iters, sample):
@@ -168,7 +179,7 @@ def cpu_baseline(name, wl, iters, sample):
     t0 = time.perf_counter()
     S.coarse_factor()
     t_coarse_fac = time.perf_counter() - t0
-    f = inputs.rhs(name)
+    f = inputs.rhs(name, levels)
     idx = np.linspace(0, P - 1, sample).round().astype(int)
     t_fac = t_sol = 0.0
     for i in idx:
@@ -237,9 +248,9 @@ def run_ours(args):
     from paper_2110_11211_gb300.solver import Solver
 
     world, rank, local = dist_setup()
-    wl = workload_args(args.workload, args.precision)
+    wl = workload_args(args.workload, args.precision, args)
     levels, P, gamma, prec, coeffs = wl["levels"], wl["P"], wl["gamma"], wl["precision"], wl["coeffs"]
-    f_np = inputs.rhs(args.workload)
+    f_np = inputs.rhs(args.workload, levels)
     N = f_np.size
     f = torch.tensor(f_np, device="cuda")
     stream = torch.cuda.current_stream()
@@ -374,7 +385,8 @@ def run_ours(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[prec],
         "data": "synthetic",
-        "config": {"workload": args.workload, "levels": list(levels), "N": N, "P": P,
+        "config": {"workload": args.workload if not args.levels else "custom",
+                   "levels": list(levels), "N": N, "P": P,
                    "gamma": gamma, "q": int(info.q), "N0": int(info.N0), "precision": prec,
                    "rtol": args.rtol, "rhs": inputs.WORKLOADS[args.workload]["rhs"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -103,8 +103,12 @@ __device__ void fwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
     wait_flag(a.ready + fb + c, ep, a.err, 1);
     const double2 yv = __ldcg(reinterpret_cast<const double2*>(a.y + vb + c * TILE + 2 * lane));
     const A y0 = A(yv.x), y1 = A(yv.y);
+    // one fused multiply-add per factor element (FP64 FMA issue rate bounds this loop)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) part[i] += cur[i][0] * y0 + cur[i][1] * y1;
+    for (int i = 0; i < 8; ++i) {
+      part[i] = fma(cur[i][0], y0, part[i]);
+      part[i] = fma(cur[i][1], y1, part[i]);
+    }
     if (c + 1 < r) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -143,7 +147,7 @@ __device__ void fwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
   for (int i = 0; i < 8; ++i) {
     A l0, l1;
     ld_pair(dt + (8 * w + i) * TILE + 2 * lane, l0, l1);
-    q[i] = l0 * x0 + l1 * x1;
+    q[i] = fma(l1, x1, l0 * x0);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) q[i] = warp_allsum(q[i]);
