@@ -52,6 +52,8 @@ struct sfcdd_handle {
   int *d_n = nullptr, *d_nt = nullptr, *d_vbase = nullptr;
   long long* d_tbase = nullptr;
   long long* d_zero64 = nullptr;
+  int *d_kmin = nullptr, *d_rowoff = nullptr, *d_colptr = nullptr, *d_colidx = nullptr;
+  std::vector<int> h_kmin, h_rowoff, stored, col_max_local, col_max_coarse;
   TileSetDev ts{};
   Store st = Store::F64;
   void* ltiles = nullptr;
@@ -185,6 +187,26 @@ TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalar
   a.err = h->err;
   a.sc = sc;
   return a;
+}
+
+// One-matrix views (tile base 0) of the coarse matrix and of local matrix i.
+TileSetDev coarse_view(const sfcdd_handle* h) {
+  TileSetDev v = h->ts;
+  v.nmat = 1;
+  v.n = h->d_n + h->P;
+  v.nt = h->d_nt + h->P;
+  v.vbase = h->d_vbase + h->P;
+  v.tbase = h->d_zero64;
+  return v;
+}
+TileSetDev local_view(const sfcdd_handle* h, int i) {
+  TileSetDev v = h->ts;
+  v.nmat = 1;
+  v.n = h->d_n + i;
+  v.nt = h->d_nt + i;
+  v.vbase = h->d_vbase + i;
+  v.tbase = h->d_zero64;
+  return v;
 }
 
 int prolong_mode(const sfcdd_handle* h) {
@@ -441,9 +463,9 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->h_nt.resize(P + 1);
   h->h_tbase.resize(P + 1);
   h->h_vbase.resize(P + 1);
-  long long tb = 0, vb = 0;
+  long long vb = 0;
   h->max_nt = 0;
-  h->max_ltiles = 0;
+  int max_nlocal = 0;
   for (int m = 0; m <= P; ++m) {
     const int n = m < P ? h->h_len[m] : h->N0;
     const int nt = (n + TILE - 1) / TILE;
@@ -452,33 +474,120 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     h->h_vbase[m] = (int)vb;
     vb += (long long)nt * TILE;
     if (m < P) {
-      h->h_tbase[m] = tb;
-      tb += (long long)nt * (nt + 1) / 2 * TILE2;
       h->max_nt = std::max(h->max_nt, nt);
-      h->max_ltiles = std::max(h->max_ltiles, nt * (nt + 1) / 2);
-    } else {
-      h->h_tbase[m] = 0;
+      max_nlocal = std::max(max_nlocal, n);
     }
   }
-  h->ltile_elems = tb;
   h->nt0 = h->h_nt[P];
-  h->ctile_elems = (long long)h->nt0 * (h->nt0 + 1) / 2 * TILE2;
   h->vtotal = vb;
+  const int nrows = (int)(vb / TILE);  // tile rows over all matrices
   TRY(dalloc(h, &h->d_n, P + 1));
   TRY(dalloc(h, &h->d_nt, P + 1));
   TRY(dalloc(h, &h->d_tbase, P + 1));
   TRY(dalloc(h, &h->d_vbase, P + 1));
   TRY(dalloc(h, &h->d_zero64, 1));
+  TRY(dalloc(h, &h->d_kmin, nrows));
+  TRY(dalloc(h, &h->d_rowoff, nrows));
+  TRY(dalloc(h, &h->d_colptr, nrows + 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->d_zero64, 0, sizeof(long long), s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_n, h->h_n.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_nt, h->h_nt.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_tbase, h->h_tbase.data(), (P + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_vbase, h->h_vbase.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   h->ts.nmat = P + 1;
   h->ts.n = h->d_n;
   h->ts.nt = h->d_nt;
   h->ts.tbase = h->d_tbase;
   h->ts.vbase = h->d_vbase;
+
+  // Cholesky envelopes of every local matrix and of the coarse matrix: the
+  // first column with a nonzero in each tile row (the factor keeps that profile)
+  {
+    const int max_nt_all = std::max(h->max_nt, h->nt0);
+    int* tfirst = nullptr;
+    TRY(dalloc(h, &tfirst, nrows));
+    pf.run(SFCDD_K_ASSEMBLE, [&] {
+      launch_envelope_init(h->ts, P + 1, max_nt_all, tfirst, s);
+      if (h->variant != SFCDD_COARSE_ONLY)
+        launch_envelope_local(g, pd, h->curve_code, h->invpad, h->ts, P, max_nlocal, tfirst, s);
+      if (h->variant != SFCDD_ONE_LEVEL)
+        launch_envelope_coarse(g, pd, h->curve_code, h->invpad, h->h_vbase[P] / TILE, tfirst, s);
+    });
+    std::vector<int> tf(nrows);
+    SFCDD_CUDA_OK(cudaMemcpyAsync(tf.data(), tfirst, nrows * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    dfree(h, tfirst);
+    h->h_kmin.assign(nrows, 0);
+    h->h_rowoff.assign(nrows, 0);
+    for (int r = 0; r < nrows; ++r) h->h_kmin[r] = tf[r] / TILE;
+  }
+  // skyline offsets, per-matrix tile counts, column lists and step sizes
+  std::vector<int> colcnt(nrows, 0);
+  h->stored.assign(P + 1, 0);
+  h->max_ltiles = 0;
+  long long tb = 0;
+  for (int m = 0; m <= P; ++m) {
+    const int fb = h->h_vbase[m] / TILE, nt = h->h_nt[m];
+    int off = 0;
+    for (int I = 0; I < nt; ++I) {
+      h->h_rowoff[fb + I] = off;
+      off += I - h->h_kmin[fb + I] + 1;
+      for (int K = h->h_kmin[fb + I]; K < I; ++K) colcnt[fb + K] += 1;
+    }
+    h->stored[m] = off;
+    if (m < P) {
+      h->h_tbase[m] = tb;
+      tb += (long long)off * TILE2;
+      h->max_ltiles = std::max(h->max_ltiles, off);
+    } else {
+      h->h_tbase[m] = 0;
+    }
+  }
+  h->ltile_elems = tb;
+  h->ctile_elems = (long long)h->stored[P] * TILE2;
+  std::vector<int> colptr(nrows + 1, 0);
+  for (int r = 0; r < nrows; ++r) colptr[r + 1] = colptr[r] + colcnt[r];
+  std::vector<int> colidx(std::max(colptr[nrows], 1));
+  {
+    std::vector<int> pos(colptr.begin(), colptr.end() - 1);
+    for (int m = 0; m <= P; ++m) {
+      const int fb = h->h_vbase[m] / TILE, nt = h->h_nt[m];
+      for (int I = 0; I < nt; ++I)
+        for (int K = h->h_kmin[fb + I]; K < I; ++K) colidx[pos[fb + K]++] = I;
+    }
+  }
+  h->col_max_local.assign(std::max(h->max_nt, 1), 0);
+  h->col_max_coarse.assign(std::max(h->nt0, 1), 0);
+  const double t3 = (double)TILE * TILE * TILE;
+  for (int m = 0; m <= P; ++m) {
+    const int fb = h->h_vbase[m] / TILE, nt = h->h_nt[m];
+    for (int K = 0; K < nt; ++K) {
+      const int c = colcnt[fb + K];
+      const double po = 2.0 * t3 / 3.0, tr = c * 2.0 * t3, sy = c * (c + 1) / 2.0 * 2.0 * t3;
+      if (m < P) {
+        h->col_max_local[K] = std::max(h->col_max_local[K], c);
+        if (h->variant != SFCDD_COARSE_ONLY) {
+          h->work_potrf += po;
+          h->work_trsm += tr;
+          h->work_syrk += sy;
+        }
+      } else {
+        h->col_max_coarse[K] = c;
+        if (h->variant != SFCDD_ONE_LEVEL) h->work_coarse += po + tr + sy;
+      }
+    }
+  }
+  h->factor_flops = h->work_potrf + h->work_trsm + h->work_syrk;
+  TRY(dalloc(h, &h->d_colidx, colidx.size()));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_kmin, h->h_kmin.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_rowoff, h->h_rowoff.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_colptr, colptr.data(), (nrows + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_colidx, colidx.data(), colidx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_tbase, h->h_tbase.data(), (P + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+  h->ts.kmin = h->d_kmin;
+  h->ts.rowoff = h->d_rowoff;
+  h->ts.colptr = h->d_colptr;
+  h->ts.colidx = h->d_colidx;
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors above go out of scope
 
   TRY(dalloc(h, &h->err, 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->err, 0, sizeof(ErrWord), s));
@@ -494,7 +603,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
       launch_assemble_local(g, pd, h->curve_code, h->invpad, h->ts, 0, P, h->max_ltiles,
                             work_tiles, compute_st, s);
     });
-    factor_tiles(h->ts, 0, P, h->max_nt, work_tiles, compute_st, h->err, s, &pf);
+    factor_tiles(h->ts, 0, P, h->max_nt, h->col_max_local.data(), work_tiles, compute_st, h->err,
+                 s, &pf);
   }
   if (h->st == Store::BF16) {
     TRY(dalloc(h, (__nv_bfloat16**)&h->ltiles, h->ltile_elems));
@@ -506,42 +616,17 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   } else {
     h->ltiles = work_tiles;
   }
-  // operation counts of the tiled factorization as executed (padded tiles):
-  // per step k, the diagonal Cholesky + inverse (2 TILE^3 / 3), the panel
-  // (rows * 2 TILE^3) and the trailing update (rows (rows+1)/2 * 2 TILE^3)
-  auto count_factor = [&](int nt, double& po, double& tr, double& sy) {
-    const double t3 = (double)TILE * TILE * TILE;
-    for (int k = 0; k < nt; ++k) {
-      const double rows = nt - k - 1;
-      po += 2.0 * t3 / 3.0;
-      tr += rows * 2.0 * t3;
-      sy += rows * (rows + 1) / 2.0 * 2.0 * t3;
-    }
-  };
-  h->factor_flops = 0;
-  if (h->variant != SFCDD_COARSE_ONLY)
-    for (int m = 0; m < P; ++m) count_factor(h->h_nt[m], h->work_potrf, h->work_trsm, h->work_syrk);
-  h->factor_flops = h->work_potrf + h->work_trsm + h->work_syrk;
-  if (h->variant != SFCDD_ONE_LEVEL) {
-    double a = 0, b2 = 0, c = 0;
-    count_factor(h->nt0, a, b2, c);
-    h->work_coarse = a + b2 + c;
-  }
-
   // Algorithm 1, steps 9-10: coarse matrix and its FP64 factor
   TRY(dalloc(h, &h->ctiles, h->ctile_elems));
   if (h->variant != SFCDD_ONE_LEVEL) {
+    // the coarse matrix is a one-matrix tile set with base 0
+    const TileSetDev cts = coarse_view(h);
     pf.run(SFCDD_K_COARSE_ASSEMBLE, [&] {
-      launch_assemble_coarse(g, pd, h->curve_code, h->invpad, h->N0, h->nt0, h->ctiles, nullptr, s);
+      launch_assemble_coarse(g, pd, h->curve_code, h->invpad, cts, h->stored[P], h->ctiles, s);
     });
-    // the coarse matrix is factored as a one-matrix tile set with base 0
-    TileSetDev cts = h->ts;
-    cts.nmat = 1;
-    cts.n = h->d_n + P;
-    cts.nt = h->d_nt + P;
-    cts.tbase = h->d_zero64;
     CoarseHook ch(pf);
-    factor_tiles(cts, 0, 1, h->nt0, h->ctiles, Store::F64, h->err, s, &ch);
+    factor_tiles(cts, 0, 1, h->nt0, h->col_max_coarse.data(), h->ctiles, Store::F64, h->err, s,
+                 &ch);
   }
   SFCDD_CUDA_OK(cudaGetLastError());
 
@@ -875,13 +960,9 @@ int sfcdd_get_coarse_matrix(const sfcdd_handle* hc, double* A0_dev) {
   if (!h || !A0_dev) return SFCDD_ERR_INVALID_ARG;
   cudaStream_t s = h->stream;
   double* t = nullptr;
-  SFCDD_CUDA_OK(cudaMalloc(&t, h->ctile_elems * sizeof(double)));
-  launch_assemble_coarse(h->g, h->pd, h->curve_code, h->invpad, h->N0, h->nt0, t, nullptr, s);
-  TileSetDev cts = h->ts;
-  cts.nmat = 1;
-  cts.n = h->d_n + h->P;
-  cts.nt = h->d_nt + h->P;
-  cts.tbase = h->d_zero64;
+  SFCDD_CUDA_OK(cudaMalloc(&t, std::max<long long>(h->ctile_elems, 1) * sizeof(double)));
+  const TileSetDev cts = coarse_view(h);
+  launch_assemble_coarse(h->g, h->pd, h->curve_code, h->invpad, cts, h->stored[h->P], t, s);
   launch_unpack_dense(cts, 0, t, A0_dev, s);
   h->launches[SFCDD_K_COARSE_ASSEMBLE] += 1;
   h->launches[SFCDD_K_VECTOR] += 1;
@@ -893,18 +974,14 @@ int sfcdd_get_coarse_matrix(const sfcdd_handle* hc, double* A0_dev) {
 int sfcdd_get_local_matrix(const sfcdd_handle* hc, int i, double* Ai_dev) {
   sfcdd_handle* h = const_cast<sfcdd_handle*>(hc);
   if (!h || !Ai_dev || i < 0 || i >= h->P) return SFCDD_ERR_INVALID_ARG;
+  if (h->variant == SFCDD_COARSE_ONLY) return SFCDD_ERR_UNSUPPORTED;
   cudaStream_t s = h->stream;
-  const int nt = h->h_nt[i];
   double* t = nullptr;
-  SFCDD_CUDA_OK(cudaMalloc(&t, (size_t)nt * (nt + 1) / 2 * TILE2 * sizeof(double)));
-  TileSetDev lts = h->ts;
-  lts.nmat = 1;
-  lts.n = h->d_n + i;
-  lts.nt = h->d_nt + i;
-  lts.tbase = h->d_zero64;
+  SFCDD_CUDA_OK(cudaMalloc(&t, (size_t)h->stored[i] * TILE2 * sizeof(double)));
+  const TileSetDev lts = local_view(h, i);
   PartDev pd = h->pd;
   pd.start = h->d_start + i;
-  launch_assemble_local(h->g, pd, h->curve_code, h->invpad, lts, 0, 1, nt * (nt + 1) / 2, t,
+  launch_assemble_local(h->g, pd, h->curve_code, h->invpad, lts, 0, 1, h->stored[i], t,
                         Store::F64, s);
   launch_unpack_dense(lts, 0, t, Ai_dev, s);
   h->launches[SFCDD_K_ASSEMBLE] += 1;

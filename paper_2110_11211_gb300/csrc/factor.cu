@@ -9,22 +9,42 @@
 // assembly exact and deterministic.
 // Factorization (Sec. 3.1: factor once, then only forward/backward solves): a
 // blocked right-looking Cholesky on TILE x TILE tiles, batched over all
-// matrices: per step k one launch factors the diagonal tiles (and inverts the
-// factor's diagonal block in place), one solves the panel, one updates the
-// trailing lower triangle.
+// matrices.  Only tiles inside the Cholesky envelope are stored and updated:
+// row r of the factor is zero left of the first nonzero of row r of A, so the
+// tiles left of a tile row's envelope stay exact zeros and skipping them gives
+// the same factor.  Per step k one launch factors the diagonal tiles (and
+// inverts the factor's diagonal block in place), one solves the panel tiles of
+// column k, one updates the trailing tiles they touch.
 #include "sfcdd_internal.cuh"
 
 namespace sfcdd {
 
 constexpr int FB = 256;
 
-// packed lower-triangular tile index -> (a, b)
+// packed lower-triangular index -> (a, b), a >= b
 __device__ __forceinline__ void tri_decode(int idx, int& a, int& b) {
   int t = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
   while ((t + 1) * (t + 2) / 2 <= idx) ++t;
   while (t * (t + 1) / 2 > idx) --t;
   a = t;
   b = idx - t * (t + 1) / 2;
+}
+
+// stored tile number t of matrix (fb, nt) -> (I, K)
+__device__ __forceinline__ void skyline_decode(const TileSetDev& ts, int fb, int nt, int t, int& I,
+                                               int& K) {
+  int lo = 0, hi = nt - 1;
+  while (lo < hi) {  // last I with rowoff[I] <= t
+    const int mid = (lo + hi + 1) >> 1;
+    if (ts.rowoff[fb + mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  I = lo;
+  K = ts.kmin[fb + I] + (t - ts.rowoff[fb + I]);
+}
+
+__device__ __forceinline__ int stored_tiles(const TileSetDev& ts, int fb, int nt) {
+  return ts.rowoff[fb + nt - 1] + (nt - ts.kmin[fb + nt - 1]);
 }
 
 template <class T>
@@ -35,7 +55,82 @@ __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// Local matrices.  grid = (max tiles per matrix, nmat); one CTA per tile.
+// Envelopes.
+__global__ void k_envelope_init(TileSetDev ts, int* tfirst) {
+  const int m = blockIdx.y;
+  const int nt = ts.nt[m];
+  const int fb = ts.vbase[m] / TILE;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nt; I += gridDim.x * blockDim.x)
+    tfirst[fb + I] = I * TILE;  // the diagonal
+}
+
+void launch_envelope_init(const TileSetDev& ts, int nmat, int max_nt, int* tfirst, cudaStream_t s) {
+  dim3 grid((max_nt + 127) / 128, nmat);
+  k_envelope_init<<<grid, 128, 0, s>>>(ts, tfirst);
+}
+
+// Row r of A_i: smallest local column among its neighbours inside Omega_i.
+__global__ void k_envelope_local(GridDev g, PartDev pd, const unsigned* __restrict__ code,
+                                 const int* __restrict__ invpad, TileSetDev ts, int* tfirst) {
+  const int m = blockIdx.y;
+  const int n = ts.n[m];
+  const int fb = ts.vbase[m] / TILE;
+  const int start = pd.start[m];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    int p = start + r;
+    if (p >= g.N) p -= g.N;
+    const unsigned c = code[p];
+    int first = r;
+    for (int j = 0; j < g.d; ++j) {
+      const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
+      const unsigned unit = 1u << g.off[j];
+      if (kj > 1u) {
+        int cg = invpad[c - unit] - start;
+        if (cg < 0) cg += g.N;
+        if (cg < n && cg < first) first = cg;
+      }
+      if (kj < (unsigned)g.size[j]) {
+        int cg = invpad[c + unit] - start;
+        if (cg < 0) cg += g.N;
+        if (cg < n && cg < first) first = cg;
+      }
+    }
+    if (first < r) atomicMin(&tfirst[fb + r / TILE], first);
+  }
+}
+
+void launch_envelope_local(const GridDev& g, const PartDev& pd, const unsigned* code,
+                           const int* invpad, const TileSetDev& ts, int nmat, int max_n, int* tfirst,
+                           cudaStream_t s) {
+  dim3 grid((max_n + 255) / 256, nmat);
+  k_envelope_local<<<grid, 256, 0, s>>>(g, pd, code, invpad, ts, tfirst);
+}
+
+// Coarse row a: smallest coarse block adjacent to block a.
+__global__ void k_envelope_coarse(GridDev g, PartDev pd, const unsigned* __restrict__ code,
+                                  const int* __restrict__ invpad, int fbc, int* tfirst) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += gridDim.x * blockDim.x) {
+    const int a = coarse_block_of(pd, p);
+    const unsigned c = code[p];
+    int first = a;
+    for (int j = 0; j < g.d; ++j) {
+      const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
+      const unsigned unit = 1u << g.off[j];
+      if (kj > 1u) first = min(first, coarse_block_of(pd, invpad[c - unit]));
+      if (kj < (unsigned)g.size[j]) first = min(first, coarse_block_of(pd, invpad[c + unit]));
+    }
+    if (first < a) atomicMin(&tfirst[fbc + a / TILE], first);
+  }
+}
+
+void launch_envelope_coarse(const GridDev& g, const PartDev& pd, const unsigned* code,
+                            const int* invpad, int fb_coarse, int* tfirst, cudaStream_t s) {
+  const int nb = min((g.N + 255) / 256, 152 * 8);
+  k_envelope_coarse<<<nb, 256, 0, s>>>(g, pd, code, invpad, fb_coarse, tfirst);
+}
+
+// ---------------------------------------------------------------------------
+// Local matrices.  grid = (max stored tiles per matrix, nmat); one CTA per tile.
 template <class T>
 __global__ void __launch_bounds__(FB) k_assemble_local(GridDev g, PartDev pd,
                                                        const unsigned* __restrict__ code,
@@ -44,10 +139,11 @@ __global__ void __launch_bounds__(FB) k_assemble_local(GridDev g, PartDev pd,
   __shared__ double sm[TILE2];
   const int m = mat0 + blockIdx.y;
   const int nt = ts.nt[m];
+  const int fb = ts.vbase[m] / TILE;
   const int idx = blockIdx.x;
-  if (idx >= nt * (nt + 1) / 2) return;
+  if (idx >= stored_tiles(ts, fb, nt)) return;
   int a, b;
-  tri_decode(idx, a, b);
+  skyline_decode(ts, fb, nt, idx, a, b);
   for (int k = threadIdx.x; k < TILE2; k += FB) sm[k] = 0.0;
   __syncthreads();
   const int n = ts.n[m];
@@ -101,20 +197,22 @@ void launch_assemble_local(const GridDev& g, const PartDev& pd, const unsigned* 
 }
 
 // ---------------------------------------------------------------------------
-// Coarse matrix tiles (single matrix, nt0 tile rows).  One CTA per lower tile;
+// Coarse matrix tiles (a one-matrix tile set).  One CTA per stored tile;
 // 4 threads per coarse row walk the points of the row's block.
 __global__ void __launch_bounds__(FB) k_assemble_coarse(GridDev g, PartDev pd,
                                                         const unsigned* __restrict__ code,
-                                                        const int* __restrict__ invpad, int N0,
-                                                        double* __restrict__ tiles) {
+                                                        const int* __restrict__ invpad,
+                                                        TileSetDev cts, double* __restrict__ tiles) {
   extern __shared__ __align__(16) unsigned char dsm_coarse[];
   double* acc = reinterpret_cast<double*>(dsm_coarse);
   int* cnt = reinterpret_cast<int*>(acc + TILE2);
+  const int N0 = cts.n[0];
+  const int nt = cts.nt[0];
+  const int fb = cts.vbase[0] / TILE;
   int R, C;
-  tri_decode(blockIdx.x, R, C);
+  skyline_decode(cts, fb, nt, blockIdx.x, R, C);
   const int tr = threadIdx.x >> 2, sub = threadIdx.x & 3;
   const int arow = R * TILE + tr;
-  // block of coarse row arow
   int bstart = 0, bsize = 0;
   if (arow < N0) {
     const int t = arow / pd.q, mm = arow % pd.q;
@@ -162,18 +260,16 @@ __global__ void __launch_bounds__(FB) k_assemble_coarse(GridDev g, PartDev pd,
       if (cnt[k]) acc[k] -= g.w[j] * (double)cnt[k];
     __syncthreads();
   }
-  double* out = tiles + (long long)blockIdx.x * TILE2;
+  double* out = tiles + cts.tbase[0] + (long long)blockIdx.x * TILE2;
   for (int k = threadIdx.x; k < TILE2; k += FB) out[k] = acc[k];
 }
 
 void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned* code,
-                            const int* invpad, int N0, int nt0, double* tiles, double* dense,
+                            const int* invpad, const TileSetDev& cts, int ntiles, double* tiles,
                             cudaStream_t s) {
-  (void)dense;
-  const int ntiles = nt0 * (nt0 + 1) / 2;
   const int smem = TILE2 * (int)(sizeof(double) + sizeof(int));
   cudaFuncSetAttribute(k_assemble_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_assemble_coarse<<<ntiles, FB, smem, s>>>(g, pd, code, invpad, N0, tiles);
+  k_assemble_coarse<<<ntiles, FB, smem, s>>>(g, pd, code, invpad, cts, tiles);
 }
 
 // ---------------------------------------------------------------------------
@@ -190,7 +286,8 @@ __global__ void __launch_bounds__(FB) k_potrf(TileSetDev ts, int mat0, int k, T*
   T& s_inv = X[TILE][0];
   const int m = mat0 + blockIdx.x;
   if (ts.nt[m] <= k) return;
-  T* tp = tiles + ts.tbase[m] + (long long)(k * (k + 1) / 2 + k) * TILE2;
+  const int fb = ts.vbase[m] / TILE;
+  T* tp = tiles + tile_at(ts, ts.tbase[m], fb, k, k);
   for (int e = threadIdx.x; e < TILE2; e += FB) L[e / TILE][e % TILE] = tp[e];
   __syncthreads();
   for (int j = 0; j < TILE; ++j) {
@@ -254,7 +351,8 @@ __device__ __forceinline__ void mma_4x4(T (&acc)[4][4], T (*Xt)[TILE + 4], T (*Y
   }
 }
 
-// Panel: L_ik = A_ik * Linv_kk^T for every tile row i > k.  grid = (max rows, nmat)
+// Panel: L_ik = A_ik * Linv_kk^T for the stored tiles of column k below the
+// diagonal.  grid = (max panel rows, nmat)
 template <class T>
 __global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int k, T* __restrict__ tiles) {
   extern __shared__ __align__(16) unsigned char dsm_trsm[];
@@ -262,11 +360,14 @@ __global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int k, T* 
   T (*Bt)[TILE + 4] = At + TILE;
   const int m = mat0 + blockIdx.y;
   const int nt = ts.nt[m];
-  const int i = k + 1 + blockIdx.x;
-  if (i >= nt) return;
-  T* base = tiles + ts.tbase[m];
-  T* aik = base + (long long)(i * (i + 1) / 2 + k) * TILE2;
-  const T* lkk = base + (long long)(k * (k + 1) / 2 + k) * TILE2;
+  if (k >= nt) return;
+  const int fb = ts.vbase[m] / TILE;
+  const int c0p = ts.colptr[fb + k];
+  if ((int)blockIdx.x >= ts.colptr[fb + k + 1] - c0p) return;
+  const int i = ts.colidx[c0p + blockIdx.x];
+  const long long tb = ts.tbase[m];
+  T* aik = tiles + tile_at(ts, tb, fb, i, k);
+  const T* lkk = tiles + tile_at(ts, tb, fb, k, k);
   load_transposed<T>(At, aik);
   load_transposed<T>(Bt, lkk);
   __syncthreads();
@@ -283,7 +384,8 @@ __global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int k, T* 
     for (int b = 0; b < 4; ++b) aik[(r0 + a) * TILE + c0 + b] = acc[a][b];
 }
 
-// Trailing update A_ij -= L_ik L_jk^T for k < j <= i.  grid = (pairs, nmat)
+// Trailing update A_ij -= L_ik L_jk^T for the stored panel tiles i >= j of
+// column k.  grid = (max pairs, nmat)
 template <class T>
 __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* __restrict__ tiles) {
   extern __shared__ __align__(16) unsigned char dsm_syrk[];
@@ -291,15 +393,18 @@ __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* 
   T (*Yt)[TILE + 4] = Xt + TILE;
   const int m = mat0 + blockIdx.y;
   const int nt = ts.nt[m];
-  const int rem = nt - k - 1;
-  if ((int)blockIdx.x >= rem * (rem + 1) / 2) return;
+  if (k >= nt) return;
+  const int fb = ts.vbase[m] / TILE;
+  const int c0p = ts.colptr[fb + k];
+  const int cnt = ts.colptr[fb + k + 1] - c0p;
+  if ((int)blockIdx.x >= cnt * (cnt + 1) / 2) return;
   int ii, jj;
   tri_decode(blockIdx.x, ii, jj);
-  const int i = k + 1 + ii, j = k + 1 + jj;
-  T* base = tiles + ts.tbase[m];
-  const T* lik = base + (long long)(i * (i + 1) / 2 + k) * TILE2;
-  const T* ljk = base + (long long)(j * (j + 1) / 2 + k) * TILE2;
-  T* aij = base + (long long)(i * (i + 1) / 2 + j) * TILE2;
+  const int i = ts.colidx[c0p + ii], j = ts.colidx[c0p + jj];
+  const long long tb = ts.tbase[m];
+  const T* lik = tiles + tile_at(ts, tb, fb, i, k);
+  const T* ljk = tiles + tile_at(ts, tb, fb, j, k);
+  T* aij = tiles + tile_at(ts, tb, fb, i, j);
   load_transposed<T>(Xt, lik);
   load_transposed<T>(Yt, ljk);
   __syncthreads();
@@ -317,8 +422,8 @@ __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* 
 }
 
 template <class T>
-static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt, T* tiles,
-                           ErrWord* err, cudaStream_t s, LaunchHook* hook) {
+static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
+                           T* tiles, ErrWord* err, cudaStream_t s, LaunchHook* hook) {
   const int sm_potrf = (2 * TILE + 1) * (TILE + 1) * (int)sizeof(T);
   const int sm_gemm = 2 * TILE * (TILE + 4) * (int)sizeof(T);
   cudaFuncSetAttribute(k_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_potrf);
@@ -328,7 +433,7 @@ static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt,
     hook->before(SFCDD_K_POTRF);
     k_potrf<T><<<nmat, FB, sm_potrf, s>>>(ts, mat0, k, tiles, err);
     hook->after(SFCDD_K_POTRF);
-    const int rows = max_nt - k - 1;
+    const int rows = col_max[k];
     if (rows > 0) {
       hook->before(SFCDD_K_TRSM);
       k_trsm<T><<<dim3(rows, nmat), FB, sm_gemm, s>>>(ts, mat0, k, tiles);
@@ -340,12 +445,12 @@ static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt,
   }
 }
 
-void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, void* tiles, Store st,
-                  ErrWord* err, cudaStream_t s, LaunchHook* hook) {
+void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
+                  void* tiles, Store st, ErrWord* err, cudaStream_t s, LaunchHook* hook) {
   if (st == Store::F64)
-    factor_tiles_t<double>(ts, mat0, nmat, max_nt, (double*)tiles, err, s, hook);
+    factor_tiles_t<double>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, err, s, hook);
   else
-    factor_tiles_t<float>(ts, mat0, nmat, max_nt, (float*)tiles, err, s, hook);
+    factor_tiles_t<float>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, err, s, hook);
 }
 
 __global__ void k_convert_f32_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
@@ -359,11 +464,12 @@ void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, c
   k_convert_f32_bf16<<<152 * 16, 256, 0, s>>>(in, out, n);
 }
 
-// Dense symmetric N x N copy (row-major) of an FP64 packed matrix before
-// factorization (introspection only).
+// Dense symmetric N x N copy (row-major) of an FP64 tile-skyline matrix before
+// factorization (introspection only); entries outside the envelope are zero.
 __global__ void k_unpack_dense(TileSetDev ts, int m, const double* __restrict__ tiles,
                                double* __restrict__ dense) {
   const int n = ts.n[m];
+  const int fb = ts.vbase[m] / TILE;
   const long long tot = (long long)n * n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += stride) {
@@ -374,8 +480,10 @@ __global__ void k_unpack_dense(TileSetDev ts, int m, const double* __restrict__ 
       c = t;
     }
     const int a = r / TILE, b = c / TILE;
-    dense[e] = tiles[ts.tbase[m] + (long long)(a * (a + 1) / 2 + b) * TILE2 + (r % TILE) * TILE +
-                     (c % TILE)];
+    double v = 0.0;
+    if (b >= ts.kmin[fb + a])
+      v = tiles[tile_at(ts, ts.tbase[m], fb, a, b) + (r % TILE) * TILE + (c % TILE)];
+    dense[e] = v;
   }
 }
 

@@ -6,11 +6,15 @@
 //  - invpad[code]   (int32, 2^{sum l_j}): curve position of a code, -1 if the
 //    code is not an interior grid point.
 //  - PCG vectors (FP64, N) in curve order.
-//  - local factors: per subdomain i a packed lower triangle of TILE x TILE tiles,
-//    tile (a, b), a >= b, at tbase[i] + (a(a+1)/2 + b) TILE^2, row-major inside a
-//    tile; the diagonal tile slot holds the INVERSE of the diagonal block of the
-//    Cholesky factor.  Storage type fp64, fp32 or bf16.  The coarse factor has
-//    the same layout in FP64 and is matrix index P.
+//  - local factors: per subdomain i the TILE x TILE tiles of its lower triangle
+//    that lie inside the Cholesky envelope ("tile skyline"): tile row I keeps
+//    tiles K = kmin[I]..I, where kmin[I] is the first tile column holding a
+//    nonzero of A_i in any row of tile row I.  The factor's fill stays inside
+//    each row's envelope, so every tile outside is an exact zero and is neither
+//    stored nor touched.  Tile (I, K) sits at tbase[i] + (rowoff[I] + K - kmin[I])
+//    TILE^2, row-major inside a tile; the diagonal slot holds the INVERSE of the
+//    diagonal block of the Cholesky factor.  Storage fp64, fp32 or bf16.  The
+//    coarse factor has the same layout in FP64 and is matrix index P.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -70,14 +74,24 @@ __host__ __device__ inline int coarse_block_of(const PartDev& pd, int p) {
   return t * pd.q + m;
 }
 
-// Packed tile set of several matrices.
+// Tile-skyline set of several matrices.  Per-tile-row arrays are indexed by
+// fb + I with fb = vbase[m] / TILE (the global tile-row index of row 0 of m).
 struct TileSetDev {
   int nmat;
   const int* n;              // dimension of each matrix
   const int* nt;             // tiles per dimension
   const long long* tbase;    // element offset of the first tile
   const int* vbase;          // offset of the matrix's vector slices (nt*TILE doubles)
+  const int* kmin;           // [fb + I] first stored tile column of tile row I
+  const int* rowoff;         // [fb + I] tiles stored before tile row I in its matrix
+  const int* colptr;         // [fb + K], [fb + K + 1]: range in colidx of rows I > K, kmin[I] <= K
+  const int* colidx;         // those rows, ascending
 };
+
+__device__ __forceinline__ long long tile_at(const TileSetDev& ts, long long tb, int fb, int I,
+                                             int K) {
+  return tb + ((long long)ts.rowoff[fb + I] + (K - ts.kmin[fb + I])) * (long long)(64 * 64);
+}
 
 // Device-side PCG scalars (one struct per handle).
 struct PcgScalars {
@@ -155,16 +169,26 @@ struct LaunchHook {
 
 // factor.cu
 enum class Store { F64 = 0, F32 = 1, BF16 = 2 };
+// Envelopes: tfirst[fb + I] receives the smallest column index with a nonzero
+// in any row of tile row I (initialised by launch_envelope_init).
+void launch_envelope_init(const TileSetDev& ts, int nmat, int max_nt, int* tfirst, cudaStream_t s);
+void launch_envelope_local(const GridDev& g, const PartDev& pd, const unsigned* code,
+                           const int* invpad, const TileSetDev& ts, int nmat, int max_n, int* tfirst,
+                           cudaStream_t s);
+void launch_envelope_coarse(const GridDev& g, const PartDev& pd, const unsigned* code,
+                            const int* invpad, int fb_coarse, int* tfirst, cudaStream_t s);
 void launch_assemble_local(const GridDev& g, const PartDev& pd, const unsigned* code,
                            const int* invpad, const TileSetDev& ts, int mat0, int nmat, int max_tiles,
                            void* tiles, Store st, cudaStream_t s);
 void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned* code,
-                            const int* invpad, int N0, int nt0, double* tiles, double* dense,
+                            const int* invpad, const TileSetDev& cts, int ntiles, double* tiles,
                             cudaStream_t s);
 // Blocked right-looking Cholesky of matrices [mat0, mat0+nmat) of the tile set,
-// in place; diagonal slots end up holding the inverse of the factor's diagonal block.
-void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, void* tiles, Store st,
-                  ErrWord* err, cudaStream_t s, LaunchHook* hook);
+// in place, over the stored tiles only; diagonal slots end up holding the
+// inverse of the factor's diagonal block.  col_max[K] = largest number of rows
+// I > K with kmin[I] <= K over the matrices (sizes the step-K launches).
+void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
+                  void* tiles, Store st, ErrWord* err, cudaStream_t s, LaunchHook* hook);
 void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, cudaStream_t s);
 void launch_unpack_dense(const TileSetDev& ts, int m, const double* tiles, double* dense,
                          cudaStream_t s);

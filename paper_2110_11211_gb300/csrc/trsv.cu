@@ -84,19 +84,22 @@ __device__ void fwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
   const int n = a.ts.n[m];
   const int vb = a.ts.vbase[m];
   const int fb = vb / TILE;
-  const T* rowb = tiles + tb + (long long)(r * (r + 1) / 2) * TILE2;
+  // tile row r is stored contiguously from its first envelope tile kmin to the diagonal
+  const int k0 = a.ts.kmin[fb + r];
+  const T* row0 = tiles + tb + (long long)a.ts.rowoff[fb + r] * TILE2;  // tile (r, k0)
   A part[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) part[i] = A(0);
   A cur[8][2], nxt[8][2];
   const int ep = reinterpret_cast<const int*>(xs + TILE)[0];
-  if (r > 0) {
+  if (r > k0) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) ld_pair(rowb + (8 * w + i) * TILE + 2 * lane, cur[i][0], cur[i][1]);
+    for (int i = 0; i < 8; ++i)
+      ld_pair(row0 + (8 * w + i) * TILE + 2 * lane, cur[i][0], cur[i][1]);
   }
-  for (int c = 0; c < r; ++c) {
+  for (int c = k0; c < r; ++c) {
     if (c + 1 < r) {
-      const T* nt_ = rowb + (long long)(c + 1) * TILE2;
+      const T* nt_ = row0 + (long long)(c + 1 - k0) * TILE2;
 #pragma unroll
       for (int i = 0; i < 8; ++i) ld_pair(nt_ + (8 * w + i) * TILE + 2 * lane, nxt[i][0], nxt[i][1]);
     }
@@ -140,7 +143,7 @@ __device__ void fwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
   }
   __syncthreads();
   // diagonal block: y_r = Linv_rr * xs
-  const T* dt = rowb + (long long)r * TILE2;
+  const T* dt = row0 + (long long)(r - k0) * TILE2;
   const A x0 = A(xs[2 * lane]), x1 = A(xs[2 * lane + 1]);
   A q[8];
 #pragma unroll
@@ -175,15 +178,20 @@ __device__ void bwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
   const int ep = reinterpret_cast<const int*>(xs + TILE)[0];
   A p0 = A(0), p1 = A(0);
   A cur[8][2], nxt[8][2];
-  auto tile_ptr = [&](int c) { return tiles + tb + (long long)(c * (c + 1) / 2 + r) * TILE2; };
-  if (r + 1 < nt) {
-    const T* t0 = tile_ptr(nt - 1);
+  (void)nt;
+  // rows c > r whose envelope reaches column r, ascending; consumed from the last
+  const int* cl = a.ts.colidx + a.ts.colptr[fb + r];
+  const int ncl = a.ts.colptr[fb + r + 1] - a.ts.colptr[fb + r];
+  auto tile_ptr = [&](int c) { return tiles + tile_at(a.ts, tb, fb, c, r); };
+  if (ncl > 0) {
+    const T* t0 = tile_ptr(cl[ncl - 1]);
 #pragma unroll
     for (int i = 0; i < 8; ++i) ld_pair(t0 + (8 * w + i) * TILE + 2 * lane, cur[i][0], cur[i][1]);
   }
-  for (int c = nt - 1; c > r; --c) {
-    if (c - 1 > r) {
-      const T* t1 = tile_ptr(c - 1);
+  for (int q = ncl - 1; q >= 0; --q) {
+    const int c = cl[q];
+    if (q > 0) {
+      const T* t1 = tile_ptr(cl[q - 1]);
 #pragma unroll
       for (int i = 0; i < 8; ++i) ld_pair(t1 + (8 * w + i) * TILE + 2 * lane, nxt[i][0], nxt[i][1]);
     }
@@ -195,7 +203,7 @@ __device__ void bwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
       p0 += cur[i][0] * dv;
       p1 += cur[i][1] * dv;
     }
-    if (c - 1 > r) {
+    if (q > 0) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         cur[i][0] = nxt[i][0];
