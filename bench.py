@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--levels", default=None, help="custom grid levels, e.g. 8,5,3 (profiling runs)")
     ap.add_argument("--P", type=int, default=None, help="custom subdomain count")
     ap.add_argument("--gamma", type=float, default=None, help="custom overlap")
+    ap.add_argument("--stencil-levels", default=None,
+                    help="time only the curve-order stencil on this grid (e.g. 9,9,9)")
     return ap.parse_args()
 
 
@@ -412,8 +414,44 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_stencil(args):
+    """The matrix-free stencil alone, y = A x in curve order, on a grid whose
+    vectors exceed L2; algorithmic bytes 16 N per launch (read x, write y)."""
+    import torch
+    from paper_2110_11211_gb300.solver import Solver
+    torch.cuda.set_device(0)
+    levels = tuple(int(v) for v in args.stencil_levels.split(","))
+    s = Solver(levels, 64, 0.5, variant="coarse_only", q=1)
+    N = s.N
+    x = torch.tensor(inputs.uniform(1, N), device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        s.apply_operator(x, curve_order=True)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.apply_operator(x, curve_order=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    hbm, _, src = load_peaks()
+    gbs = 16.0 * N / (ms * 1e-3) / 1e9
+    print(json.dumps({"kernel": "stencil", "levels": list(levels), "N": N,
+                      "vector_bytes": 8 * N, "ms_per_launch": round(ms, 4),
+                      "algorithmic_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
+                      "dram_bytes_per_point_min": 20, "peak_source": src}), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
+    if args.stencil_levels:
+        run_stencil(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
