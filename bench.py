@@ -447,8 +447,86 @@ def run_stencil(args):
     s.close()
 
 
+def run_batch_bench(args):
+    """Combination-technique set (all d = 4 level vectors with |l|_1 in {12, 13},
+    385 subgrids, P = 64 each, gamma = 1/2): batched setup + one-graph solve of
+    every subgrid to rtol, against a loop of single-problem setups and solves."""
+    import torch
+    from paper_2110_11211_gb300.solver import BatchSolver, Solver
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[args.workload]
+    prec = args.precision or w["precision"]
+    levels = inputs.combi_levels(4, (12, 13))
+    P, gamma = w["P"], w["gamma"]
+    ntot = sum(inputs.grid_size(lv) for lv in levels)
+    f = torch.tensor(inputs.uniform(inputs.workload_seed(args.workload), ntot), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        b = BatchSolver(levels, P, gamma, precision=prec)
+        u, tot, per = b.solve(f, rtol=args.rtol)
+        info = b.info()
+        b.close()
+        return u, tot, per, info
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    setups, solves, iters = [], [], []
+    for _ in range(args.steps):
+        u, tot, per, info = step()
+        setups.append(tot.setup_ms)
+        solves.append(tot.solve_ms)
+        iters.append([p.iters for p in per])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # loop over single-problem handles (same method, one subgrid at a time)
+    offs = [0]
+    for lv in levels:
+        offs.append(offs[-1] + inputs.grid_size(lv))
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k, lv in enumerate(levels):
+        s = Solver(lv, P, gamma, precision=prec)
+        s.solve(f[offs[k]:offs[k + 1]], rtol=args.rtol)
+        s.close()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    looped = t0.elapsed_time(t1)
+    it = np.array(iters[-1])
+    hbm, _, src = load_peaks()
+    print(json.dumps({
+        "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 2),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32+f64", "bf16": "bf16+f32+f64"}[prec],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "subgrids": len(levels), "N_total": ntot, "P": P,
+                   "gamma": gamma, "precision": prec, "rtol": args.rtol,
+                   "mode": "batched setup + one CUDA-graph launch (conditional while node)"},
+        "setup_ms": round(statistics.mean(setups), 2), "solve_ms": round(statistics.mean(solves), 2),
+        "iters": {"min": int(it.min()), "max": int(it.max()), "mean": round(float(it.mean()), 2)},
+        "factor_bytes": info["factor_bytes"],
+        "looped_ms": round(looped, 2), "speedup_vs_looped": round(looped / ms, 2),
+        "clocks": clk}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "combi4d_l12-13_P64" and args.impl == "ours":
+        import numpy as np  # noqa: F401
+        globals()["np"] = np
+        run_batch_bench(args)
+        return
     if args.stencil_levels:
         run_stencil(args)
         return

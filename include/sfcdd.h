@@ -128,6 +128,31 @@ int sfcdd_solve_host(sfcdd_handle* h, const double* f_host, double* u_host, doub
 int sfcdd_solve_backward(sfcdd_handle* h, const double* u_dev, const double* gu_dev, double* gf_dev,
                          double* gc_host, double rtol, int maxit, sfcdd_stats* stats);
 
+/* ---- Batched solves: many independent subgrid problems ----
+ * The subproblems of the sparse-grid combination technique (Sec. 2: one
+ * anisotropic full grid per level vector l, solved independently), all with the
+ * same d, P, overlap and options, set up together and solved in ONE CUDA-graph
+ * launch: a conditional WHILE node repeats the PCG iteration of every subgrid
+ * until each has converged (its own scalars and converged flag) or maxit.
+ * levels: host array nsub x d (subgrid s uses levels[s*d .. s*d+d-1]).
+ * Vectors: the concatenation of the subgrids' vectors, each lexicographic, at
+ * the offsets returned by sfcdd_batch_offsets (nsub + 1 entries, last = total).
+ * Supported options: precision, weighting, q (<= 0: per-subgrid rule), flexible,
+ * coeffs (shared), stream; variant must be SFCDD_ADDITIVE (else UNSUPPORTED).
+ * Errors as sfcdd_setup_ex / sfcdd_solve; per_sub (nsub entries) and total may
+ * be NULL; total->iters is the largest iteration count, total->fail_index the
+ * number of subgrids that did not converge. */
+typedef struct sfcdd_batch sfcdd_batch;
+int sfcdd_batch_setup(const int* levels, int nsub, int d, int P, double overlap,
+                      const sfcdd_options* opt, sfcdd_batch** out);
+int sfcdd_batch_offsets(const sfcdd_batch* b, long long* offsets_host);
+int sfcdd_batch_solve(sfcdd_batch* b, const double* f_dev, double* u_dev, double rtol, int maxit,
+                      sfcdd_stats* per_sub, sfcdd_stats* total);
+/* total unknowns, bytes of all factor tiles (local + coarse), setup device time */
+int sfcdd_batch_info(const sfcdd_batch* b, long long* n_total, long long* factor_bytes,
+                     double* setup_ms);
+int sfcdd_batch_destroy(sfcdd_batch* b);
+
 /* y = A x (the matrix-free stencil, Sec. 4).  curve_order = 0: x, y
  * lexicographic; 1: x, y in curve order (no permutation, the hot-path form). */
 int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, int curve_order);

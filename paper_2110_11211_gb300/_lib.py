@@ -29,7 +29,8 @@ EXPORTS = [
     "sfcdd_solve_backward", "sfcdd_apply_operator", "sfcdd_apply_precond", "sfcdd_get_info",
     "sfcdd_get_curve", "sfcdd_get_partition", "sfcdd_get_coarse_matrix", "sfcdd_get_local_matrix",
     "sfcdd_set_profiling", "sfcdd_get_kernel_stats", "sfcdd_kernel_work", "sfcdd_destroy",
-    "sfcdd_status_string", "sfcdd_curve_order_noalloc",
+    "sfcdd_status_string", "sfcdd_curve_order_noalloc", "sfcdd_batch_setup",
+    "sfcdd_batch_offsets", "sfcdd_batch_solve", "sfcdd_batch_info", "sfcdd_batch_destroy",
 ]
 
 
@@ -99,6 +100,14 @@ def lib() -> C.CDLL:
     L.sfcdd_status_string.argtypes = [C.c_int]
     L.sfcdd_status_string.restype = C.c_char_p
     L.sfcdd_curve_order_noalloc.argtypes = [C.POINTER(C.c_int), C.c_int, P, P, C.c_void_p]
+    L.sfcdd_batch_setup.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_double,
+                                    C.POINTER(Options), C.POINTER(H)]
+    L.sfcdd_batch_offsets.argtypes = [H, C.POINTER(C.c_longlong)]
+    L.sfcdd_batch_solve.argtypes = [H, P, P, C.c_double, C.c_int, C.POINTER(Stats),
+                                    C.POINTER(Stats)]
+    L.sfcdd_batch_info.argtypes = [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_double)]
+    L.sfcdd_batch_destroy.argtypes = [H]
     for name in EXPORTS:
         if name not in ("sfcdd_default_options", "sfcdd_kernel_work", "sfcdd_status_string"):
             getattr(L, name).restype = C.c_int

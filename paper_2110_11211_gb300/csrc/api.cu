@@ -25,6 +25,178 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
           cudaGetErrorString(e), file, line, what);
   return SFCDD_ERR_CUDA;
 }
+
+int make_grid(const int* levels, int d, const double* coeffs, GridDev& g, long long& N, int& B) {
+  if (!levels || d < 1 || d > MAXD) return SFCDD_ERR_INVALID_ARG;
+  N = 1;
+  B = 0;
+  int nbits = 0;
+  for (int j = 0; j < d; ++j) {
+    if (levels[j] < 1 || levels[j] > 30) return SFCDD_ERR_INVALID_ARG;
+    N *= (1ll << levels[j]) - 1;
+    nbits = std::max(nbits, levels[j]);
+    B += levels[j];
+    if (coeffs && (!(coeffs[j] > 0) || !std::isfinite(coeffs[j]))) return SFCDD_ERR_INVALID_ARG;
+  }
+  if (d * nbits > 64) return SFCDD_ERR_KEY_OVERFLOW;
+  if (B > 31 || N >= (1ll << 31)) return SFCDD_ERR_UNSUPPORTED;
+  g = GridDev{};
+  g.d = d;
+  g.N = (int)N;
+  g.nbits = nbits;
+  int off = 0, stride = 1;
+  for (int j = d - 1; j >= 0; --j) {
+    g.lev[j] = levels[j];
+    g.off[j] = off;
+    off += levels[j];
+    g.size[j] = (1 << levels[j]) - 1;
+    g.stride[j] = stride;
+    stride *= g.size[j];
+  }
+  g.diag = 0.0;
+  for (int j = 0; j < d; ++j) {
+    g.w[j] = (coeffs ? coeffs[j] : 1.0) * std::ldexp(1.0, 2 * levels[j]);
+    g.diag += 2.0 * g.w[j];
+  }
+  return SFCDD_OK;
+}
+
+int paper_q(long long N, int P) {
+  const long long fN = N / P;
+  int e = 0;
+  while ((2ll << e) <= fN) ++e;  // floor(log2 floor(N/P))
+  const long long qq = 1ll << std::max(e - 4, 0);
+  return (int)std::min<long long>(std::max<long long>(qq, 1), fN);
+}
+
+// eqs. sloc, enlarge, omegai.  gamma is read as the rational round(gamma 2^16) /
+// 2^16 so ceil/floor(eta tilde N) are exact.
+int partition_ranges(long long N, int P, double gamma, int weighting, std::vector<int>& start,
+                     std::vector<int>& len, std::vector<double>& omega, int& gfloor) {
+  const long long den = 1 << 16;
+  const long long gnum = llround(gamma * (double)den);
+  const int gf = (int)(gnum / den);
+  const long long eta = gnum % den;
+  gfloor = gf;
+  if (gnum <= 0 || 2 * gf + 1 >= P || P > N) return SFCDD_ERR_INVALID_ARG;
+  const long long f = N / P, rr = N % P;
+  auto tsize = [&](int t) { return t < rr ? f + 1 : f; };
+  auto toff = [&](int t) { return t < rr ? t * (f + 1) : rr * (f + 1) + (t - rr) * f; };
+  start.assign(P, 0);
+  len.assign(P, 0);
+  for (int i = 0; i < P; ++i) {
+    const int left = ((i - gf - 1) % P + P) % P;
+    const int right = (i + gf + 1) % P;
+    const long long nl = (eta * tsize(left) + den - 1) / den;
+    const long long nr = (eta * tsize(right)) / den;
+    long long core = 0;
+    for (int k = -gf; k <= gf; ++k) core += tsize(((i + k) % P + P) % P);
+    const long long l = nl + core + nr;
+    if (l > N) return SFCDD_ERR_INVALID_ARG;
+    start[i] = (int)((toff(left) + tsize(left) - nl) % N);
+    len[i] = (int)l;
+  }
+  // coverage counts are constant between range end points: sweep the segments
+  std::vector<long long> cuts;
+  cuts.reserve(2 * P + 2);
+  cuts.push_back(0);
+  cuts.push_back(N);
+  for (int i = 0; i < P; ++i) {
+    cuts.push_back(start[i]);
+    cuts.push_back((start[i] + len[i]) % N);
+  }
+  std::sort(cuts.begin(), cuts.end());
+  cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+  const int nseg = (int)cuts.size() - 1;
+  std::vector<int> cnt(nseg, 0);
+  std::vector<std::pair<int, int>> segs(P);  // (first segment, number of segments)
+  for (int i = 0; i < P; ++i) {
+    const int a = (int)(std::lower_bound(cuts.begin(), cuts.end(), (long long)start[i]) -
+                        cuts.begin());
+    long long covered = 0;
+    int k = a, nsg = 0;
+    while (covered < len[i]) {
+      cnt[k] += 1;
+      covered += cuts[k + 1] - cuts[k];
+      k = (k + 1) % nseg;
+      ++nsg;
+    }
+    segs[i] = {a, nsg};
+  }
+  omega.assign(P, 1.0);
+  if (weighting == SFCDD_WEIGHT_OMEGA) {
+    for (int i = 0; i < P; ++i) {
+      int mn = 1 << 30;
+      for (int k = 0; k < segs[i].second; ++k) mn = std::min(mn, cnt[(segs[i].first + k) % nseg]);
+      omega[i] = 1.0 / (double)mn;
+    }
+  }
+  return SFCDD_OK;
+}
+
+void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
+                   const std::vector<char>& is_coarse, const std::vector<int>& tfirst,
+                   SkylineHost& o) {
+  const int nmat = (int)nt.size();
+  const int nrows = (int)tfirst.size();
+  o.kmin.assign(nrows, 0);
+  o.rowoff.assign(nrows, 0);
+  for (int r = 0; r < nrows; ++r) o.kmin[r] = tfirst[r] / TILE;
+  std::vector<int> colcnt(nrows, 0);
+  o.stored.assign(nmat, 0);
+  o.tbase.assign(nmat, 0);
+  int max_nt_l = 1, max_nt_c = 1;
+  for (int m = 0; m < nmat; ++m) {
+    const int fb = vbase[m] / TILE;
+    int off = 0;
+    for (int I = 0; I < nt[m]; ++I) {
+      o.rowoff[fb + I] = off;
+      off += I - o.kmin[fb + I] + 1;
+      for (int K = o.kmin[fb + I]; K < I; ++K) colcnt[fb + K] += 1;
+    }
+    o.stored[m] = off;
+    if (is_coarse[m]) {
+      o.tbase[m] = o.ctiles * TILE2;
+      o.ctiles += off;
+      o.max_ctiles = std::max(o.max_ctiles, off);
+      max_nt_c = std::max(max_nt_c, nt[m]);
+    } else {
+      o.tbase[m] = o.ltiles * TILE2;
+      o.ltiles += off;
+      o.max_ltiles = std::max(o.max_ltiles, off);
+      max_nt_l = std::max(max_nt_l, nt[m]);
+    }
+  }
+  o.colptr.assign(nrows + 1, 0);
+  for (int r = 0; r < nrows; ++r) o.colptr[r + 1] = o.colptr[r] + colcnt[r];
+  o.colidx.assign(std::max(o.colptr[nrows], 1), 0);
+  std::vector<int> pos(o.colptr.begin(), o.colptr.end() - 1);
+  for (int m = 0; m < nmat; ++m) {
+    const int fb = vbase[m] / TILE;
+    for (int I = 0; I < nt[m]; ++I)
+      for (int K = o.kmin[fb + I]; K < I; ++K) o.colidx[pos[fb + K]++] = I;
+  }
+  o.col_max_local.assign(max_nt_l, 0);
+  o.col_max_coarse.assign(max_nt_c, 0);
+  const double t3 = (double)TILE * TILE * TILE;
+  for (int m = 0; m < nmat; ++m) {
+    const int fb = vbase[m] / TILE;
+    for (int K = 0; K < nt[m]; ++K) {
+      const int c = colcnt[fb + K];
+      const double po = 2.0 * t3 / 3.0, tr = c * 2.0 * t3, sy = c * (c + 1) / 2.0 * 2.0 * t3;
+      if (is_coarse[m]) {
+        o.col_max_coarse[K] = std::max(o.col_max_coarse[K], c);
+        o.coarse += po + tr + sy;
+      } else {
+        o.col_max_local[K] = std::max(o.col_max_local[K], c);
+        o.potrf += po;
+        o.trsm += tr;
+        o.syrk += sy;
+      }
+    }
+  }
+}
+
 }  // namespace sfcdd
 
 struct sfcdd_handle {
@@ -53,6 +225,7 @@ struct sfcdd_handle {
   long long* d_tbase = nullptr;
   long long* d_zero64 = nullptr;
   int *d_kmin = nullptr, *d_rowoff = nullptr, *d_colptr = nullptr, *d_colidx = nullptr;
+  MatDesc* d_md = nullptr;
   std::vector<int> h_kmin, h_rowoff, stored, col_max_local, col_max_coarse;
   TileSetDev ts{};
   Store st = Store::F64;
@@ -172,10 +345,9 @@ struct CoarseHook : LaunchHook {
 TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalars* sc) {
   TrsvArgs a{};
   a.ts = h->ts;
-  a.P = h->P;
+  a.md = h->d_md;
   a.ltiles = h->ltiles;
   a.ctiles = h->ctiles;
-  a.pd = h->pd;
   a.rhs = rhs;
   a.g0 = h->g0;
   a.y = h->ybuf;
@@ -275,71 +447,10 @@ int check_err(sfcdd_handle* h, int* fail_index) {
 }
 
 // ---------------------------------------------------------------------------
-// Host-side partition (eqs. sloc, enlarge, omegai).  gamma is read as the
-// rational round(gamma 2^16) / 2^16 so ceil/floor(eta tilde N) are exact.
+// Host-side partition of one problem into the handle.
 int build_partition(sfcdd_handle* h) {
-  const long long N = h->N;
-  const int P = h->P;
-  const long long den = 1 << 16;
-  const long long gnum = llround(h->gamma * (double)den);
-  const int gf = (int)(gnum / den);
-  const long long eta = gnum % den;
-  h->gfloor = gf;
-  if (gnum <= 0 || 2 * gf + 1 >= P) return SFCDD_ERR_INVALID_ARG;
-  const long long f = N / P, rr = N % P;
-  auto tsize = [&](int t) { return t < rr ? f + 1 : f; };
-  auto toff = [&](int t) { return t < rr ? t * (f + 1) : rr * (f + 1) + (t - rr) * f; };
-  h->h_start.assign(P, 0);
-  h->h_len.assign(P, 0);
-  for (int i = 0; i < P; ++i) {
-    const int left = ((i - gf - 1) % P + P) % P;
-    const int right = (i + gf + 1) % P;
-    const long long nl = (eta * tsize(left) + den - 1) / den;
-    const long long nr = (eta * tsize(right)) / den;
-    long long core = 0;
-    for (int k = -gf; k <= gf; ++k) core += tsize(((i + k) % P + P) % P);
-    const long long len = nl + core + nr;
-    if (len > N) return SFCDD_ERR_INVALID_ARG;
-    h->h_start[i] = (int)((toff(left) + tsize(left) - nl) % N);
-    h->h_len[i] = (int)len;
-  }
-  // coverage counts are constant between range end points: sweep the segments
-  std::vector<long long> cuts;
-  cuts.reserve(2 * P + 2);
-  cuts.push_back(0);
-  cuts.push_back(N);
-  for (int i = 0; i < P; ++i) {
-    cuts.push_back(h->h_start[i]);
-    cuts.push_back((h->h_start[i] + h->h_len[i]) % N);
-  }
-  std::sort(cuts.begin(), cuts.end());
-  cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
-  const int nseg = (int)cuts.size() - 1;
-  std::vector<int> cnt(nseg, 0);
-  // every range is a union of whole segments: walk them from its start
-  std::vector<std::pair<int, int>> segs(P);  // (first segment, number of segments)
-  for (int i = 0; i < P; ++i) {
-    const int a = (int)(std::lower_bound(cuts.begin(), cuts.end(), (long long)h->h_start[i]) -
-                        cuts.begin());
-    long long covered = 0;
-    int k = a, nsg = 0;
-    while (covered < h->h_len[i]) {
-      cnt[k] += 1;
-      covered += cuts[k + 1] - cuts[k];
-      k = (k + 1) % nseg;
-      ++nsg;
-    }
-    segs[i] = {a, nsg};
-  }
-  h->h_omega.assign(P, 1.0);
-  if (h->weighting == SFCDD_WEIGHT_OMEGA) {
-    for (int i = 0; i < P; ++i) {
-      int mn = 1 << 30;
-      for (int k = 0; k < segs[i].second; ++k) mn = std::min(mn, cnt[(segs[i].first + k) % nseg]);
-      h->h_omega[i] = 1.0 / (double)mn;
-    }
-  }
-  return SFCDD_OK;
+  return partition_ranges(h->N, h->P, h->gamma, h->weighting, h->h_start, h->h_len, h->h_omega,
+                          h->gfloor);
 }
 
 int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
@@ -347,18 +458,16 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   if (!levels || d < 1 || d > MAXD || P < 2 || !(overlap > 0)) return SFCDD_ERR_INVALID_ARG;
   h->d = d;
   long long N = 1;
-  int nbits = 0, B = 0;
-  for (int j = 0; j < d; ++j) {
-    if (levels[j] < 1 || levels[j] > 30) return SFCDD_ERR_INVALID_ARG;
-    h->lev[j] = levels[j];
-    N *= (1ll << levels[j]) - 1;
-    nbits = std::max(nbits, levels[j]);
-    B += levels[j];
-    h->coeffs[j] = (opt && opt->coeffs) ? opt->coeffs[j] : 1.0;
-    if (!(h->coeffs[j] > 0) || !std::isfinite(h->coeffs[j])) return SFCDD_ERR_INVALID_ARG;
+  int B = 0;
+  {
+    const int rc = make_grid(levels, d, opt ? opt->coeffs : nullptr, h->g, N, B);
+    if (rc != SFCDD_OK) return rc;
   }
-  if (d * nbits > 64) return SFCDD_ERR_KEY_OVERFLOW;
-  if (B > 31 || N >= (1ll << 31)) return SFCDD_ERR_UNSUPPORTED;
+  const int nbits = h->g.nbits;
+  for (int j = 0; j < d; ++j) {
+    h->lev[j] = levels[j];
+    h->coeffs[j] = (opt && opt->coeffs) ? opt->coeffs[j] : 1.0;
+  }
   if (P > N) return SFCDD_ERR_INVALID_ARG;
   h->N = (int)N;
   h->nbits = nbits;
@@ -379,14 +488,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->stream = (cudaStream_t)o.stream;
   h->profiling = o.profile != 0;
   const long long fN = N / P;
-  if (o.q <= 0) {
-    int e = 0;
-    while ((2ll << e) <= fN) ++e;  // floor(log2 floor(N/P))
-    long long qq = 1ll << std::max(e - 4, 0);
-    h->q = (int)std::min<long long>(std::max<long long>(qq, 1), fN);
-  } else {
-    h->q = o.q;
-  }
+  h->q = o.q <= 0 ? paper_q(N, P) : o.q;
   if (h->q < 1 || h->q > fN) return SFCDD_ERR_INVALID_ARG;
   h->N0 = h->q * P;
   h->st = (Store)h->precision;
@@ -398,28 +500,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   SFCDD_CUDA_OK(cudaEventRecord(e0, h->stream));
   cudaStream_t s = h->stream;
 
-  // grid description
   GridDev& g = h->g;
-  g.d = d;
-  g.N = h->N;
-  g.nbits = nbits;
-  int off = 0;
-  for (int j = d - 1; j >= 0; --j) {
-    g.lev[j] = levels[j];
-    g.off[j] = off;
-    off += levels[j];
-    g.size[j] = (1 << levels[j]) - 1;
-  }
-  int stride = 1;
-  for (int j = d - 1; j >= 0; --j) {
-    g.stride[j] = stride;
-    stride *= g.size[j];
-  }
-  g.diag = 0.0;
-  for (int j = 0; j < d; ++j) {
-    g.w[j] = h->coeffs[j] * std::ldexp(1.0, 2 * levels[j]);
-    g.diag += 2.0 * g.w[j];
-  }
 
   // Algorithm 1, step 3: keys and curve order
   unsigned long long* keys;
@@ -501,6 +582,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
 
   // Cholesky envelopes of every local matrix and of the coarse matrix: the
   // first column with a nonzero in each tile row (the factor keeps that profile)
+  SkylineHost sky;
   {
     const int max_nt_all = std::max(h->max_nt, h->nt0);
     int* tfirst = nullptr;
@@ -516,67 +598,28 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     SFCDD_CUDA_OK(cudaMemcpyAsync(tf.data(), tfirst, nrows * sizeof(int), cudaMemcpyDeviceToHost, s));
     SFCDD_CUDA_OK(cudaStreamSynchronize(s));
     dfree(h, tfirst);
-    h->h_kmin.assign(nrows, 0);
-    h->h_rowoff.assign(nrows, 0);
-    for (int r = 0; r < nrows; ++r) h->h_kmin[r] = tf[r] / TILE;
+    std::vector<char> is_coarse(P + 1, 0);
+    is_coarse[P] = 1;
+    build_skyline(h->h_nt, h->h_vbase, is_coarse, tf, sky);
   }
-  // skyline offsets, per-matrix tile counts, column lists and step sizes
-  std::vector<int> colcnt(nrows, 0);
-  h->stored.assign(P + 1, 0);
-  h->max_ltiles = 0;
-  long long tb = 0;
-  for (int m = 0; m <= P; ++m) {
-    const int fb = h->h_vbase[m] / TILE, nt = h->h_nt[m];
-    int off = 0;
-    for (int I = 0; I < nt; ++I) {
-      h->h_rowoff[fb + I] = off;
-      off += I - h->h_kmin[fb + I] + 1;
-      for (int K = h->h_kmin[fb + I]; K < I; ++K) colcnt[fb + K] += 1;
-    }
-    h->stored[m] = off;
-    if (m < P) {
-      h->h_tbase[m] = tb;
-      tb += (long long)off * TILE2;
-      h->max_ltiles = std::max(h->max_ltiles, off);
-    } else {
-      h->h_tbase[m] = 0;
-    }
+  h->h_kmin = sky.kmin;
+  h->h_rowoff = sky.rowoff;
+  h->stored = sky.stored;
+  for (int m = 0; m <= P; ++m) h->h_tbase[m] = sky.tbase[m];
+  h->max_ltiles = sky.max_ltiles;
+  h->ltile_elems = sky.ltiles * TILE2;
+  h->ctile_elems = sky.ctiles * TILE2;
+  h->col_max_local = sky.col_max_local;
+  h->col_max_coarse = sky.col_max_coarse;
+  if (h->variant != SFCDD_COARSE_ONLY) {
+    h->work_potrf = sky.potrf;
+    h->work_trsm = sky.trsm;
+    h->work_syrk = sky.syrk;
   }
-  h->ltile_elems = tb;
-  h->ctile_elems = (long long)h->stored[P] * TILE2;
-  std::vector<int> colptr(nrows + 1, 0);
-  for (int r = 0; r < nrows; ++r) colptr[r + 1] = colptr[r] + colcnt[r];
-  std::vector<int> colidx(std::max(colptr[nrows], 1));
-  {
-    std::vector<int> pos(colptr.begin(), colptr.end() - 1);
-    for (int m = 0; m <= P; ++m) {
-      const int fb = h->h_vbase[m] / TILE, nt = h->h_nt[m];
-      for (int I = 0; I < nt; ++I)
-        for (int K = h->h_kmin[fb + I]; K < I; ++K) colidx[pos[fb + K]++] = I;
-    }
-  }
-  h->col_max_local.assign(std::max(h->max_nt, 1), 0);
-  h->col_max_coarse.assign(std::max(h->nt0, 1), 0);
-  const double t3 = (double)TILE * TILE * TILE;
-  for (int m = 0; m <= P; ++m) {
-    const int fb = h->h_vbase[m] / TILE, nt = h->h_nt[m];
-    for (int K = 0; K < nt; ++K) {
-      const int c = colcnt[fb + K];
-      const double po = 2.0 * t3 / 3.0, tr = c * 2.0 * t3, sy = c * (c + 1) / 2.0 * 2.0 * t3;
-      if (m < P) {
-        h->col_max_local[K] = std::max(h->col_max_local[K], c);
-        if (h->variant != SFCDD_COARSE_ONLY) {
-          h->work_potrf += po;
-          h->work_trsm += tr;
-          h->work_syrk += sy;
-        }
-      } else {
-        h->col_max_coarse[K] = c;
-        if (h->variant != SFCDD_ONE_LEVEL) h->work_coarse += po + tr + sy;
-      }
-    }
-  }
+  if (h->variant != SFCDD_ONE_LEVEL) h->work_coarse = sky.coarse;
   h->factor_flops = h->work_potrf + h->work_trsm + h->work_syrk;
+  std::vector<int>& colptr = sky.colptr;
+  std::vector<int>& colidx = sky.colidx;
   TRY(dalloc(h, &h->d_colidx, colidx.size()));
   SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_kmin, h->h_kmin.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_rowoff, h->h_rowoff.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -629,6 +672,16 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
                  &ch);
   }
   SFCDD_CUDA_OK(cudaGetLastError());
+
+  // per-matrix right-hand-side descriptors (one problem: scalars index 0)
+  {
+    std::vector<MatDesc> md(P + 1);
+    for (int m = 0; m < P; ++m) md[m] = {0, h->N, h->h_start[m], 0, 0};
+    md[P] = {0, h->N0, 0, 1, 0};
+    TRY(dalloc(h, &h->d_md, P + 1));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_md, md.data(), (P + 1) * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  }
 
   // substitution work lists: tile rows in dependency-safe order
   std::vector<TrsvWork> wf, wb;

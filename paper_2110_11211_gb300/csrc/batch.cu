@@ -1,0 +1,884 @@
+// Batched solve of many independent subgrid problems: the subproblems of the
+// sparse-grid combination technique (Sec. 2: every level vector l of the
+// layers |l|_1 = L + d - 1 - i gets its own anisotropic full grid, solved
+// independently), each with P subdomains of the two-level SFC Schwarz method.
+//
+// One setup builds every subgrid into batch-wide arrays: a single radix sort of
+// (subgrid, Hilbert key), per-subgrid descriptors, one tile-skyline set of all
+// local matrices (FP64/FP32/BF16) and all coarse matrices (FP64).  The solve is
+// one CUDA-graph launch whose conditional WHILE node repeats the PCG iteration
+// of every subgrid until each has converged or maxit is reached: each subgrid
+// has its own scalars and converged flag; converged subgrids skip their work.
+// Per iteration: one kernel per subgrid CTA fuses stencil, p^T A p, the x/r
+// update, the convergence test and the coarse restriction; the batched
+// substitutions run all 24k+ local and coarse matrices; one kernel fuses the
+// prolongation, r^T z, beta and the p update; one CTA sets the loop condition.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+
+using namespace sfcdd;
+
+namespace sfcdd {
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+}
+
+struct sfcdd_batch {
+  int nsub = 0, d = 0, P = 0, precision = 0, weighting = 1, flexible = 0;
+  double gamma = 0;
+  Store st = Store::F64;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  std::vector<SubDesc> hsub;
+  std::vector<long long> offs;  // nsub + 1 vector offsets
+  SubDesc* dsub = nullptr;
+  int Ntot = 0, maxN = 0, nlocal = 0, nmat = 0;
+  unsigned* code = nullptr;
+  int* invpad = nullptr;
+  int *d_start = nullptr, *d_len = nullptr;
+  double* d_omega = nullptr;
+  TileSetDev ts{};
+  MatDesc* d_md = nullptr;
+  void* ltiles = nullptr;
+  double* ctiles = nullptr;
+  SkylineHost sky;
+  std::vector<int> h_nt, h_vbase;
+  int max_nt_local = 0, max_nt_coarse = 0;
+  TrsvWork *work_f = nullptr, *work_b = nullptr;
+  int nwork = 0;
+  int *ready_f = nullptr, *ready_b = nullptr;
+  unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
+  double *ybuf = nullptr, *dbuf = nullptr;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr,
+         *g0 = nullptr;
+  PcgScalars* sc = nullptr;
+  PcgScalars* sc_host = nullptr;
+  ErrWord* err = nullptr;
+  int* iter_counter = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_maxit = -1;
+  double setup_ms = 0, solve_ms = 0;
+  long long factor_bytes = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr int BT = 512;  // threads of a per-subgrid CTA
+
+template <class T>
+int balloc(sfcdd_batch* b, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? SFCDD_ERR_NOMEM : SFCDD_ERR_CUDA;
+  }
+  b->allocs.push_back((void*)*p);
+  return SFCDD_OK;
+}
+
+#define BTRY(x)                      \
+  do {                               \
+    int _rc = (x);                   \
+    if (_rc != SFCDD_OK) return _rc; \
+  } while (0)
+
+// Deterministic block sum over BT threads; every thread gets the total.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < BT / 32; ++k) t += sh[k];
+  return t;
+}
+
+__device__ __forceinline__ int lex_id_of(const GridDev& g, unsigned c) {
+  int id = 0;
+  for (int j = 0; j < g.d; ++j) {
+    const int kj = (int)((c >> g.off[j]) & ((1u << g.lev[j]) - 1u));
+    id += (kj - 1) * g.stride[j];
+  }
+  return id;
+}
+
+// ---------------------------------------------------------------------------
+// Setup kernels.  grid.y = subgrid (or matrix), positions local to the subgrid.
+template <int D>
+__global__ void k_b_keygen(const SubDesc* __restrict__ sub, int kbits,
+                           unsigned long long* __restrict__ keys, unsigned* __restrict__ codes) {
+  const int s = blockIdx.y;
+  const SubDesc& sd = sub[s];
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < sd.g.N; id += gridDim.x * blockDim.x) {
+    unsigned c;
+    const unsigned long long k = hilbert_key_of<D>(sd.g, id, c);
+    keys[sd.base + id] = ((unsigned long long)s << kbits) | k;
+    codes[sd.base + id] = c;
+  }
+}
+
+__global__ void k_b_invpad(const SubDesc* __restrict__ sub, const unsigned* __restrict__ code,
+                           int* __restrict__ invpad) {
+  const SubDesc& sd = sub[blockIdx.y];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < sd.g.N; p += gridDim.x * blockDim.x)
+    invpad[sd.ibase + code[sd.base + p]] = p;
+}
+
+__global__ void k_b_env_local(const SubDesc* __restrict__ sub, int P, const unsigned* __restrict__ code,
+                              const int* __restrict__ invpad, TileSetDev ts, int* tfirst) {
+  const int m = blockIdx.y;
+  const SubDesc& sd = sub[m / P];
+  const int i = m % P;
+  const int n = ts.n[m];
+  const int fb = ts.vbase[m] / TILE;
+  const int start = sd.pd.start[i];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int first = envelope_row(sd.g, code + sd.base, invpad + sd.ibase, start, n, r);
+    if (first < r) atomicMin(&tfirst[fb + r / TILE], first);
+  }
+}
+
+__global__ void k_b_env_coarse(const SubDesc* __restrict__ sub, const unsigned* __restrict__ code,
+                               const int* __restrict__ invpad, TileSetDev ts, int* tfirst) {
+  const SubDesc& sd = sub[blockIdx.y];
+  const int fbc = ts.vbase[sd.cmat] / TILE;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < sd.g.N; p += gridDim.x * blockDim.x) {
+    int a;
+    const int first =
+        envelope_coarse_point(sd.g, sd.pd, code + sd.base, invpad + sd.ibase, p, a);
+    if (first < a) atomicMin(&tfirst[fbc + a / TILE], first);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T to_store(double v) { return T(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_b_assemble_local(const SubDesc* __restrict__ sub, int P,
+                                                          const unsigned* __restrict__ code,
+                                                          const int* __restrict__ invpad,
+                                                          TileSetDev ts, T* __restrict__ tiles) {
+  __shared__ double sm[TILE2];
+  const int m = blockIdx.y;
+  const SubDesc& sd = sub[m / P];
+  const int nt = ts.nt[m];
+  const int fb = ts.vbase[m] / TILE;
+  const int idx = blockIdx.x;
+  if (idx >= stored_tiles(ts, fb, nt)) return;
+  int a, bb;
+  skyline_decode(ts, fb, nt, idx, a, bb);
+  for (int k = threadIdx.x; k < TILE2; k += blockDim.x) sm[k] = 0.0;
+  __syncthreads();
+  assemble_local_tile(sd.g, code + sd.base, invpad + sd.ibase, sd.pd.start[m % P], ts.n[m], a, bb,
+                      sm);
+  __syncthreads();
+  T* out = tiles + ts.tbase[m] + (long long)idx * TILE2;
+  for (int k = threadIdx.x; k < TILE2; k += blockDim.x) out[k] = to_store<T>(sm[k]);
+}
+
+__global__ void __launch_bounds__(256) k_b_assemble_coarse(const SubDesc* __restrict__ sub,
+                                                           const unsigned* __restrict__ code,
+                                                           const int* __restrict__ invpad,
+                                                           TileSetDev ts, double* __restrict__ tiles) {
+  extern __shared__ __align__(16) unsigned char dsm_bc[];
+  double* acc = reinterpret_cast<double*>(dsm_bc);
+  int* cnt = reinterpret_cast<int*>(acc + TILE2);
+  const SubDesc& sd = sub[blockIdx.y];
+  const int m = sd.cmat;
+  const int nt = ts.nt[m];
+  const int fb = ts.vbase[m] / TILE;
+  if ((int)blockIdx.x >= stored_tiles(ts, fb, nt)) return;
+  int R, C;
+  skyline_decode(ts, fb, nt, blockIdx.x, R, C);
+  assemble_coarse_tile(sd.g, sd.pd, sd.N0, code + sd.base, invpad + sd.ibase, R, C, acc, cnt);
+  double* out = tiles + ts.tbase[m] + (long long)blockIdx.x * TILE2;
+  for (int k = threadIdx.x; k < TILE2; k += blockDim.x) out[k] = acc[k];
+}
+
+// ---------------------------------------------------------------------------
+// Solve kernels: one CTA per subgrid.
+__global__ void k_b_lex_to_curve(const SubDesc* __restrict__ sub, const unsigned* __restrict__ code,
+                                 const double* __restrict__ in, double* __restrict__ out) {
+  const SubDesc& sd = sub[blockIdx.y];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < sd.g.N; p += gridDim.x * blockDim.x)
+    out[sd.base + p] = in[sd.base + lex_id_of(sd.g, code[sd.base + p])];
+}
+
+__global__ void k_b_curve_to_lex(const SubDesc* __restrict__ sub, const unsigned* __restrict__ code,
+                                 const double* __restrict__ in, double* __restrict__ out) {
+  const SubDesc& sd = sub[blockIdx.y];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < sd.g.N; p += gridDim.x * blockDim.x)
+    out[sd.base + lex_id_of(sd.g, code[sd.base + p])] = in[sd.base + p];
+}
+
+__global__ void __launch_bounds__(BT) k_b_init(const SubDesc* __restrict__ sub,
+                                               const double* __restrict__ b, double* __restrict__ x,
+                                               double* __restrict__ r, double* __restrict__ p,
+                                               double* __restrict__ z, PcgScalars* sc, double rtol,
+                                               int flexible) {
+  __shared__ double sh[BT / 32];
+  const SubDesc& sd = sub[blockIdx.x];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    const double bi = b[sd.base + i];
+    x[sd.base + i] = 0.0;
+    r[sd.base + i] = bi;
+    p[sd.base + i] = 0.0;
+    z[sd.base + i] = 0.0;
+    acc += bi * bi;
+  }
+  const double bb = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    PcgScalars& c = sc[blockIdx.x];
+    c.bb = bb;
+    c.rr = bb;
+    c.rel = bb > 0.0 ? 1.0 : 0.0;
+    c.rz = c.rz_old = c.pq = c.alpha = c.beta = 0.0;
+    c.iter = 0;
+    c.status = 0;
+    c.rtol = rtol;
+    c.flexible = flexible;
+    c.done = bb > 0.0 ? 0 : 1;
+  }
+}
+
+// g0 = R_0 r for one subgrid (eq. restr): warp per coarse block.
+__device__ __forceinline__ void restrict_sub(const SubDesc& sd, const double* __restrict__ r,
+                                             double* __restrict__ g0) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const PartDev& pd = sd.pd;
+  for (int a = w; a < sd.N0; a += BT / 32) {
+    const int t = a / pd.q, mm = a % pd.q;
+    const int n = tilde_size(pd, t);
+    const int bf = n / pd.q, br = n % pd.q;
+    const int start = tilde_off(pd, t) + (mm < br ? mm * (bf + 1) : br * (bf + 1) + (mm - br) * bf);
+    const int size = mm < br ? bf + 1 : bf;
+    double s = 0.0;
+    for (int k = lane; k < size; k += 32) s += r[sd.base + start + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) g0[sd.g0base + a] = s;
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_b_restrict(const SubDesc* __restrict__ sub,
+                                                   const double* __restrict__ r,
+                                                   double* __restrict__ g0, const PcgScalars* sc) {
+  if (sc[blockIdx.x].done) return;
+  restrict_sub(sub[blockIdx.x], r, g0);
+}
+
+// q = A p, alpha = r^T z / p^T q, x += alpha p, r -= alpha q, convergence test,
+// then the coarse right-hand side R_0 r of the next preconditioner apply.
+template <int D>
+__global__ void __launch_bounds__(BT) k_b_iter(const SubDesc* __restrict__ sub,
+                                               const unsigned* __restrict__ code,
+                                               const int* __restrict__ invpad,
+                                               const double* __restrict__ p, double* __restrict__ q,
+                                               double* __restrict__ x, double* __restrict__ r,
+                                               double* __restrict__ g0, PcgScalars* sc) {
+  __shared__ double sh[BT / 32];
+  PcgScalars& c = sc[blockIdx.x];
+  if (c.done) return;
+  const SubDesc& sd = sub[blockIdx.x];
+  const unsigned* cs = code + sd.base;
+  const int* ip = invpad + sd.ibase;
+  const double* ps = p + sd.base;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    double pi;
+    const double v = stencil_point<D>(sd.g, cs, ip, ps, i, pi);
+    q[sd.base + i] = v;
+    acc += pi * v;
+  }
+  const double pq = block_sum(acc, sh);
+  const double alpha = c.rz / pq;
+  acc = 0.0;
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    x[sd.base + i] += alpha * ps[i];
+    const double ri = r[sd.base + i] - alpha * q[sd.base + i];
+    r[sd.base + i] = ri;
+    acc += ri * ri;
+  }
+  const double rr = block_sum(acc, sh);
+  const double rel = sqrt(rr / c.bb);
+  bool done = false;
+  if (threadIdx.x == 0) {
+    c.pq = pq;
+    c.alpha = alpha;
+    c.rr = rr;
+    c.rel = rel;
+    c.iter += 1;
+    if (!(rel == rel) || isinf(rel) || !(alpha == alpha) || isinf(alpha)) {
+      c.status = SFCDD_ERR_NAN;
+      c.done = 1;
+    } else if (rel <= c.rtol) {
+      c.done = 1;
+    }
+  }
+  done = !(rel == rel) || isinf(rel) || rel <= c.rtol;
+  __syncthreads();
+  if (!done) restrict_sub(sd, r, g0);
+}
+
+// z = R_0^T d_0 + sum_i omega_i R_i^T d_i, r^T z -> beta, p = z + beta p.
+__global__ void __launch_bounds__(BT) k_b_prolong(const SubDesc* __restrict__ sub, TileSetDev ts,
+                                                  const double* __restrict__ dvec,
+                                                  const double* __restrict__ r,
+                                                  double* __restrict__ z, double* __restrict__ p,
+                                                  PcgScalars* sc) {
+  __shared__ double sh[BT / 32];
+  PcgScalars& c = sc[blockIdx.x];
+  if (c.done) return;
+  const SubDesc& sd = sub[blockIdx.x];
+  const int cbase = ts.vbase[sd.cmat];
+  auto lvbase = [&](int i) { return __ldg(&ts.vbase[sd.mat0 + i]); };
+  double a1 = 0.0, a2 = 0.0;
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    const double v = prolong_point(sd.pd, 0, dvec, cbase, lvbase, i);
+    const double ri = r[sd.base + i];
+    a1 += ri * v;
+    a2 += ri * z[sd.base + i];
+    z[sd.base + i] = v;
+  }
+  const double rz_new = block_sum(a1, sh);
+  const double rz_old = block_sum(a2, sh);
+  double beta;
+  if (c.iter == 0) beta = 0.0;
+  else if (c.flexible) beta = (rz_new - rz_old) / c.rz;
+  else beta = rz_new / c.rz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.beta = beta;
+    c.rz_old = rz_old;
+    c.rz = rz_new;
+  }
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) p[sd.base + i] = z[sd.base + i] + beta * p[sd.base + i];
+}
+
+// Loop condition of the graph's WHILE node: another iteration while any
+// subgrid is still running and fewer than maxit iterations have been done.
+__global__ void k_b_cond(const PcgScalars* sc, int nsub, int* iter_counter, int maxit,
+                         cudaGraphConditionalHandle cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int s = threadIdx.x; s < nsub; s += blockDim.x) mine |= (sc[s].done == 0);
+  if (mine) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int it = *iter_counter + 1;
+    *iter_counter = it;
+    cudaGraphSetConditional(cond, (any && it < maxit) ? 1u : 0u);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(BT) k_b_true_res(const SubDesc* __restrict__ sub,
+                                                   const unsigned* __restrict__ code,
+                                                   const int* __restrict__ invpad,
+                                                   const double* __restrict__ b,
+                                                   const double* __restrict__ x, PcgScalars* sc) {
+  __shared__ double sh[BT / 32];
+  const SubDesc& sd = sub[blockIdx.x];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    double xi;
+    const double v = b[sd.base + i] -
+                     stencil_point<D>(sd.g, code + sd.base, invpad + sd.ibase, x + sd.base, i, xi);
+    acc += v * v;
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) sc[blockIdx.x].true_rel = sc[blockIdx.x].bb > 0 ? sqrt(t / sc[blockIdx.x].bb) : 0.0;
+}
+
+#define SFCDD_DISPATCH_D(KERNEL, d, grid, block, smem, stream, ...)                 \
+  switch (d) {                                                                      \
+    case 1: KERNEL<1><<<grid, block, smem, stream>>>(__VA_ARGS__); break;           \
+    case 2: KERNEL<2><<<grid, block, smem, stream>>>(__VA_ARGS__); break;           \
+    case 3: KERNEL<3><<<grid, block, smem, stream>>>(__VA_ARGS__); break;           \
+    case 4: KERNEL<4><<<grid, block, smem, stream>>>(__VA_ARGS__); break;           \
+    case 5: KERNEL<5><<<grid, block, smem, stream>>>(__VA_ARGS__); break;           \
+    case 6: KERNEL<6><<<grid, block, smem, stream>>>(__VA_ARGS__); break;           \
+    case 7: KERNEL<7><<<grid, block, smem, stream>>>(__VA_ARGS__); break;           \
+    default: KERNEL<8><<<grid, block, smem, stream>>>(__VA_ARGS__); break;          \
+  }
+
+TrsvArgs batch_trsv_args(sfcdd_batch* b, bool fwd) {
+  TrsvArgs a{};
+  a.ts = b->ts;
+  a.md = b->d_md;
+  a.ltiles = b->ltiles;
+  a.ctiles = b->ctiles;
+  a.rhs = b->r;
+  a.g0 = b->g0;
+  a.y = b->ybuf;
+  a.dout = b->dbuf;
+  a.work = fwd ? b->work_f : b->work_b;
+  a.nwork = b->nwork;
+  a.ready = fwd ? b->ready_f : b->ready_b;
+  a.ticket = fwd ? b->ticket_f : b->ticket_b;
+  a.err = b->err;
+  a.sc = b->sc;
+  return a;
+}
+
+void enqueue_apply(sfcdd_batch* b, cudaStream_t s) {
+  launch_trsv_fwd(batch_trsv_args(b, true), b->st, s);
+  launch_trsv_bwd(batch_trsv_args(b, false), b->st, s);
+  k_b_prolong<<<b->nsub, BT, 0, s>>>(b->dsub, b->ts, b->dbuf, b->r, b->z, b->p, b->sc);
+}
+
+int build_graph(sfcdd_batch* b, int maxit) {
+  if (b->graph && b->graph_maxit == maxit) return SFCDD_OK;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaGraph_t graph;
+  SFCDD_CUDA_OK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  SFCDD_CUDA_OK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  SFCDD_CUDA_OK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = b->cap_stream;
+  SFCDD_CUDA_OK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+  SFCDD_DISPATCH_D(k_b_iter, b->d, b->nsub, BT, 0, cs, b->dsub, b->code, b->invpad, b->p, b->q,
+                   b->x, b->r, b->g0, b->sc);
+  enqueue_apply(b, cs);
+  k_b_cond<<<1, 256, 0, cs>>>(b->sc, b->nsub, b->iter_counter, maxit, cond);
+  cudaGraph_t captured;
+  cudaError_t e = cudaStreamEndCapture(cs, &captured);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  }
+  e = cudaGraphInstantiate(&b->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  SFCDD_CUDA_OK(e);
+  b->graph_maxit = maxit;
+  return SFCDD_OK;
+}
+
+int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, double overlap,
+                     const sfcdd_options* opt) {
+  if (!levels || nsub < 1 || d < 1 || d > MAXD || P < 2 || !(overlap > 0))
+    return SFCDD_ERR_INVALID_ARG;
+  sfcdd_options o;
+  sfcdd_default_options(&o);
+  if (opt) o = *opt;
+  if (o.variant != SFCDD_ADDITIVE || o.precision < 0 || o.precision > 2 || o.weighting < 0 ||
+      o.weighting > 1)
+    return o.variant != SFCDD_ADDITIVE ? SFCDD_ERR_UNSUPPORTED : SFCDD_ERR_INVALID_ARG;
+  b->nsub = nsub;
+  b->d = d;
+  b->P = P;
+  b->gamma = overlap;
+  b->precision = o.precision;
+  b->weighting = o.weighting;
+  b->flexible = o.flexible < 0 ? (o.precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
+  b->st = (Store)o.precision;
+  b->stream = (cudaStream_t)o.stream;
+  cudaStream_t s = b->stream;
+  SFCDD_CUDA_OK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  SFCDD_CUDA_OK(cudaEventRecord(e0, s));
+
+  // per-subgrid grids and partitions (host)
+  b->hsub.resize(nsub);
+  b->offs.assign(nsub + 1, 0);
+  std::vector<int> start_all, len_all;
+  std::vector<double> omega_all;
+  std::vector<int> N0s(nsub);
+  long long ibase = 0, base = 0;
+  int kbits = 0;
+  for (int si = 0; si < nsub; ++si) {
+    SubDesc& sd = b->hsub[si];
+    long long N;
+    int B;
+    BTRY(make_grid(levels + (size_t)si * d, d, o.coeffs, sd.g, N, B));
+    if (P > N) return SFCDD_ERR_INVALID_ARG;
+    std::vector<int> st, ln;
+    std::vector<double> om;
+    int gf;
+    BTRY(partition_ranges(N, P, overlap, o.weighting, st, ln, om, gf));
+    const int q = o.q <= 0 ? paper_q(N, P) : o.q;
+    if (q < 1 || q > N / P) return SFCDD_ERR_INVALID_ARG;
+    sd.pd.N = (int)N;
+    sd.pd.P = P;
+    sd.pd.q = q;
+    sd.pd.g = gf;
+    sd.pd.f = (int)(N / P);
+    sd.pd.r = (int)(N % P);
+    sd.base = (int)base;
+    sd.ibase = (int)ibase;
+    sd.N0 = q * P;
+    N0s[si] = sd.N0;
+    start_all.insert(start_all.end(), st.begin(), st.end());
+    len_all.insert(len_all.end(), ln.begin(), ln.end());
+    omega_all.insert(omega_all.end(), om.begin(), om.end());
+    b->offs[si] = base;
+    base += N;
+    ibase += 1ll << B;
+    kbits = std::max(kbits, d * sd.g.nbits);
+    b->maxN = std::max(b->maxN, (int)N);
+  }
+  b->offs[nsub] = base;
+  if (base >= (1ll << 31) || ibase >= (1ll << 31)) return SFCDD_ERR_UNSUPPORTED;
+  int sbits = 0;
+  while ((1 << sbits) < nsub) ++sbits;
+  if (kbits + sbits > 64) return SFCDD_ERR_KEY_OVERFLOW;
+  b->Ntot = (int)base;
+  BTRY(balloc(b, &b->d_start, (size_t)nsub * P));
+  BTRY(balloc(b, &b->d_len, (size_t)nsub * P));
+  BTRY(balloc(b, &b->d_omega, (size_t)nsub * P));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_start, start_all.data(), start_all.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_len, len_all.data(), len_all.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_omega, omega_all.data(), omega_all.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+
+  // matrices: locals s * P + i, coarse nsub * P + s
+  b->nlocal = nsub * P;
+  b->nmat = b->nlocal + nsub;
+  std::vector<int> h_n(b->nmat);
+  b->h_nt.assign(b->nmat, 0);
+  b->h_vbase.assign(b->nmat, 0);
+  std::vector<char> is_coarse(b->nmat, 0);
+  long long vb = 0;
+  for (int m = 0; m < b->nmat; ++m) {
+    int n;
+    if (m < b->nlocal) {
+      n = len_all[m];
+    } else {
+      n = N0s[m - b->nlocal];
+      is_coarse[m] = 1;
+    }
+    h_n[m] = n;
+    b->h_nt[m] = (n + TILE - 1) / TILE;
+    b->h_vbase[m] = (int)vb;
+    vb += (long long)b->h_nt[m] * TILE;
+    if (m < b->nlocal) b->max_nt_local = std::max(b->max_nt_local, b->h_nt[m]);
+    else b->max_nt_coarse = std::max(b->max_nt_coarse, b->h_nt[m]);
+  }
+  if (vb >= (1ll << 31)) return SFCDD_ERR_UNSUPPORTED;
+  const int nrows = (int)(vb / TILE);
+  long long g0base = 0;
+  for (int si = 0; si < nsub; ++si) {
+    SubDesc& sd = b->hsub[si];
+    sd.pd.start = b->d_start + (size_t)si * P;
+    sd.pd.len = b->d_len + (size_t)si * P;
+    sd.pd.omega = b->d_omega + (size_t)si * P;
+    sd.mat0 = si * P;
+    sd.cmat = b->nlocal + si;
+    sd.g0base = (int)g0base;
+    g0base += (long long)b->h_nt[sd.cmat] * TILE;
+  }
+  BTRY(balloc(b, &b->dsub, nsub));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->dsub, b->hsub.data(), nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
+
+  // curve order of every subgrid: one sort of (subgrid, key)
+  unsigned long long* keys;
+  unsigned char* sort_tmp;
+  BTRY(balloc(b, &keys, b->Ntot));
+  BTRY(balloc(b, &b->code, b->Ntot));
+  BTRY(balloc(b, &sort_tmp, radix_sort_temp_bytes(b->Ntot)));
+  BTRY(balloc(b, &b->invpad, ibase));
+  const dim3 gsub((b->maxN + 255) / 256, nsub);
+  SFCDD_DISPATCH_D(k_b_keygen, d, gsub, 256, 0, s, b->dsub, kbits, keys, b->code);
+  radix_sort_pairs(keys, b->code, b->Ntot, kbits + sbits, sort_tmp, s, nullptr);
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->invpad, 0xff, ibase * sizeof(int), s));
+  k_b_invpad<<<gsub, 256, 0, s>>>(b->dsub, b->code, b->invpad);
+  SFCDD_CUDA_OK(cudaGetLastError());
+
+  // tile layout and envelopes
+  int *d_n, *d_nt, *d_vbase, *tfirst;
+  long long* d_tbase;
+  BTRY(balloc(b, &d_n, b->nmat));
+  BTRY(balloc(b, &d_nt, b->nmat));
+  BTRY(balloc(b, &d_vbase, b->nmat));
+  BTRY(balloc(b, &d_tbase, b->nmat));
+  BTRY(balloc(b, &tfirst, nrows));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_n, h_n.data(), b->nmat * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_nt, b->h_nt.data(), b->nmat * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_vbase, b->h_vbase.data(), b->nmat * sizeof(int), cudaMemcpyHostToDevice, s));
+  b->ts.nmat = b->nmat;
+  b->ts.n = d_n;
+  b->ts.nt = d_nt;
+  b->ts.vbase = d_vbase;
+  b->ts.tbase = d_tbase;
+  const int max_nt_all = std::max(b->max_nt_local, b->max_nt_coarse);
+  launch_envelope_init(b->ts, b->nmat, max_nt_all, tfirst, s);
+  int max_nl = 0;
+  for (int m = 0; m < b->nlocal; ++m) max_nl = std::max(max_nl, h_n[m]);
+  k_b_env_local<<<dim3((max_nl + 255) / 256, b->nlocal), 256, 0, s>>>(b->dsub, P, b->code,
+                                                                      b->invpad, b->ts, tfirst);
+  k_b_env_coarse<<<gsub, 256, 0, s>>>(b->dsub, b->code, b->invpad, b->ts, tfirst);
+  std::vector<int> tf(nrows);
+  SFCDD_CUDA_OK(cudaMemcpyAsync(tf.data(), tfirst, nrows * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  build_skyline(b->h_nt, b->h_vbase, is_coarse, tf, b->sky);
+  int *d_kmin, *d_rowoff, *d_colptr, *d_colidx;
+  BTRY(balloc(b, &d_kmin, nrows));
+  BTRY(balloc(b, &d_rowoff, nrows));
+  BTRY(balloc(b, &d_colptr, nrows + 1));
+  BTRY(balloc(b, &d_colidx, b->sky.colidx.size()));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_kmin, b->sky.kmin.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_rowoff, b->sky.rowoff.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_colptr, b->sky.colptr.data(), (nrows + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_colidx, b->sky.colidx.data(), b->sky.colidx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_tbase, b->sky.tbase.data(), b->nmat * sizeof(long long), cudaMemcpyHostToDevice, s));
+  b->ts.kmin = d_kmin;
+  b->ts.rowoff = d_rowoff;
+  b->ts.colptr = d_colptr;
+  b->ts.colidx = d_colidx;
+
+  // local matrices and factors (Sec. 3.1), coarse matrices and FP64 factors (eq. csm)
+  BTRY(balloc(b, &b->err, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->err, 0, sizeof(ErrWord), s));
+  const Store cst = b->st == Store::BF16 ? Store::F32 : b->st;
+  const size_t esz = cst == Store::F64 ? 8 : 4;
+  void* work_tiles = nullptr;
+  BTRY(balloc(b, (unsigned char**)&work_tiles, b->sky.ltiles * TILE2 * esz));
+  switch (cst) {
+    case Store::F64:
+      k_b_assemble_local<double><<<dim3(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
+          b->dsub, P, b->code, b->invpad, b->ts, (double*)work_tiles);
+      break;
+    default:
+      k_b_assemble_local<float><<<dim3(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
+          b->dsub, P, b->code, b->invpad, b->ts, (float*)work_tiles);
+      break;
+  }
+  struct NoHook : LaunchHook {
+    void before(int) override {}
+    void after(int) override {}
+  } nohook;
+  factor_tiles(b->ts, 0, b->nlocal, b->max_nt_local, b->sky.col_max_local.data(), work_tiles, cst,
+               b->err, s, &nohook);
+  if (b->st == Store::BF16) {
+    BTRY(balloc(b, (__nv_bfloat16**)&b->ltiles, b->sky.ltiles * TILE2));
+    launch_convert_f32_bf16((const float*)work_tiles, (__nv_bfloat16*)b->ltiles, b->sky.ltiles * TILE2, s);
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    cudaFree(work_tiles);
+    for (auto& a : b->allocs)
+      if (a == work_tiles) a = nullptr;
+  } else {
+    b->ltiles = work_tiles;
+  }
+  BTRY(balloc(b, &b->ctiles, b->sky.ctiles * TILE2));
+  {
+    const int smem = TILE2 * (int)(sizeof(double) + sizeof(int));
+    cudaFuncSetAttribute(k_b_assemble_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_b_assemble_coarse<<<dim3(b->sky.max_ctiles, nsub), 256, smem, s>>>(b->dsub, b->code, b->invpad,
+                                                                        b->ts, b->ctiles);
+  }
+  factor_tiles(b->ts, b->nlocal, nsub, b->max_nt_coarse, b->sky.col_max_coarse.data(), b->ctiles,
+               Store::F64, b->err, s, &nohook);
+  SFCDD_CUDA_OK(cudaGetLastError());
+  b->factor_bytes = b->sky.ltiles * TILE2 * (b->precision == 0 ? 8 : b->precision == 1 ? 4 : 2) +
+                    b->sky.ctiles * TILE2 * 8;
+
+  // substitution descriptors and work lists
+  std::vector<MatDesc> md(b->nmat);
+  for (int si = 0; si < nsub; ++si) {
+    const SubDesc& sd = b->hsub[si];
+    for (int i = 0; i < P; ++i)
+      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)si * P + i], 0, si};
+    md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si};
+  }
+  BTRY(balloc(b, &b->d_md, b->nmat));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_md, md.data(), b->nmat * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
+  std::vector<TrsvWork> wf, wb;
+  for (int rr = 0; rr < max_nt_all; ++rr)
+    for (int m = 0; m < b->nmat; ++m)
+      if (rr < b->h_nt[m]) {
+        wf.push_back({m, rr});
+        wb.push_back({m, b->h_nt[m] - 1 - rr});
+      }
+  b->nwork = (int)wf.size();
+  BTRY(balloc(b, &b->work_f, b->nwork));
+  BTRY(balloc(b, &b->work_b, b->nwork));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+  BTRY(balloc(b, &b->ready_f, nrows));
+  BTRY(balloc(b, &b->ready_b, nrows));
+  BTRY(balloc(b, &b->ticket_f, 1));
+  BTRY(balloc(b, &b->ticket_b, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->ready_f, 0, nrows * sizeof(int), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->ready_b, 0, nrows * sizeof(int), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_f, 0, sizeof(unsigned long long), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_b, 0, sizeof(unsigned long long), s));
+  BTRY(balloc(b, &b->ybuf, vb));
+  BTRY(balloc(b, &b->dbuf, vb));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->ybuf, 0, vb * sizeof(double), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->dbuf, 0, vb * sizeof(double), s));
+
+  // PCG state
+  BTRY(balloc(b, &b->b, b->Ntot));
+  BTRY(balloc(b, &b->x, b->Ntot));
+  BTRY(balloc(b, &b->r, b->Ntot));
+  BTRY(balloc(b, &b->p, b->Ntot));
+  BTRY(balloc(b, &b->q, b->Ntot));
+  BTRY(balloc(b, &b->z, b->Ntot));
+  BTRY(balloc(b, &b->g0, std::max<long long>(g0base, 1)));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->g0, 0, std::max<long long>(g0base, 1) * sizeof(double), s));
+  BTRY(balloc(b, &b->sc, nsub));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->sc, 0, nsub * sizeof(PcgScalars), s));
+  SFCDD_CUDA_OK(cudaMallocHost((void**)&b->sc_host, nsub * sizeof(PcgScalars)));
+  BTRY(balloc(b, &b->iter_counter, 1));
+
+  SFCDD_CUDA_OK(cudaEventRecord(e1, s));
+  SFCDD_CUDA_OK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  b->setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (auto& a : b->allocs)
+    if (a == keys || a == sort_tmp || a == tfirst) {
+      cudaFree(a);
+      a = nullptr;
+    }
+  ErrWord ew{};
+  SFCDD_CUDA_OK(cudaMemcpy(&ew, b->err, sizeof(ErrWord), cudaMemcpyDeviceToHost));
+  return ew.code;
+}
+
+void batch_destroy(sfcdd_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs)
+    if (p) cudaFree(p);
+  if (b->sc_host) cudaFreeHost(b->sc_host);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfcdd_batch_setup(const int* levels, int nsub, int d, int P, double overlap,
+                      const sfcdd_options* opt, sfcdd_batch** out) {
+  if (!out) return SFCDD_ERR_INVALID_ARG;
+  *out = nullptr;
+  sfcdd_batch* b = new (std::nothrow) sfcdd_batch();
+  if (!b) return SFCDD_ERR_NOMEM;
+  const int rc = batch_setup_impl(b, levels, nsub, d, P, overlap, opt);
+  if (rc != SFCDD_OK) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return SFCDD_OK;
+}
+
+int sfcdd_batch_offsets(const sfcdd_batch* b, long long* offsets_host) {
+  if (!b || !offsets_host) return SFCDD_ERR_INVALID_ARG;
+  for (int si = 0; si <= b->nsub; ++si) offsets_host[si] = b->offs[si];
+  return SFCDD_OK;
+}
+
+int sfcdd_batch_solve(sfcdd_batch* b, const double* f_dev, double* u_dev, double rtol, int maxit,
+                      sfcdd_stats* per_sub, sfcdd_stats* total) {
+  if (!b || !f_dev || !u_dev || !(rtol >= 0) || maxit < 1) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = b->stream;
+  BTRY(build_graph(b, maxit));
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  SFCDD_CUDA_OK(cudaEventRecord(e0, s));
+  const dim3 gsub((b->maxN + 255) / 256, b->nsub);
+  k_b_lex_to_curve<<<gsub, 256, 0, s>>>(b->dsub, b->code, f_dev, b->b);
+  k_b_init<<<b->nsub, BT, 0, s>>>(b->dsub, b->b, b->x, b->r, b->p, b->z, b->sc, rtol, b->flexible);
+  k_b_restrict<<<b->nsub, BT, 0, s>>>(b->dsub, b->r, b->g0, b->sc);
+  enqueue_apply(b, s);  // z_0 = C^{-1} r_0, beta = 0, p = z_0
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->iter_counter, 0, sizeof(int), s));
+  SFCDD_CUDA_OK(cudaGraphLaunch(b->graph, s));  // every PCG iteration of every subgrid
+  SFCDD_CUDA_OK(cudaEventRecord(e1, s));
+  SFCDD_DISPATCH_D(k_b_true_res, b->d, b->nsub, BT, 0, s, b->dsub, b->code, b->invpad, b->b, b->x,
+                   b->sc);
+  k_b_curve_to_lex<<<gsub, 256, 0, s>>>(b->dsub, b->code, b->x, u_dev);
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->sc_host, b->sc, b->nsub * sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  SFCDD_CUDA_OK(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->solve_ms = ms;
+  ErrWord ew{};
+  SFCDD_CUDA_OK(cudaMemcpy(&ew, b->err, sizeof(ErrWord), cudaMemcpyDeviceToHost));
+  int rc = ew.code;
+  int maxits = 0, not_done = 0;
+  double worst = 0.0, worst_true = 0.0;
+  for (int si = 0; si < b->nsub; ++si) {
+    const PcgScalars& c = b->sc_host[si];
+    const int st = c.status ? c.status : (c.done ? SFCDD_OK : SFCDD_ERR_MAXIT);
+    if (!c.done) ++not_done;
+    if (rc == SFCDD_OK && st != SFCDD_OK) rc = st;
+    maxits = std::max(maxits, c.iter);
+    worst = std::max(worst, c.rel);
+    worst_true = std::max(worst_true, c.true_rel);
+    if (per_sub) {
+      per_sub[si].iters = c.iter;
+      per_sub[si].status = st;
+      per_sub[si].fail_index = ew.index;
+      per_sub[si].rel_res = c.rel;
+      per_sub[si].true_rel_res = c.true_rel;
+      per_sub[si].setup_ms = b->setup_ms;
+      per_sub[si].solve_ms = ms;
+    }
+  }
+  if (total) {
+    total->iters = maxits;
+    total->status = rc;
+    total->fail_index = not_done;
+    total->rel_res = worst;
+    total->true_rel_res = worst_true;
+    total->setup_ms = b->setup_ms;
+    total->solve_ms = ms;
+  }
+  return rc;
+}
+
+int sfcdd_batch_info(const sfcdd_batch* b, long long* n_total, long long* factor_bytes,
+                     double* setup_ms) {
+  if (!b) return SFCDD_ERR_INVALID_ARG;
+  if (n_total) *n_total = b->Ntot;
+  if (factor_bytes) *factor_bytes = b->factor_bytes;
+  if (setup_ms) *setup_ms = b->setup_ms;
+  return SFCDD_OK;
+}
+
+int sfcdd_batch_destroy(sfcdd_batch* b) {
+  if (!b) return SFCDD_ERR_INVALID_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  batch_destroy(b);
+  return SFCDD_OK;
+}
+
+}  // extern "C"

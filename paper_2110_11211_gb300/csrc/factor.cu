@@ -15,37 +15,11 @@
 // the same factor.  Per step k one launch factors the diagonal tiles (and
 // inverts the factor's diagonal block in place), one solves the panel tiles of
 // column k, one updates the trailing tiles they touch.
-#include "sfcdd_internal.cuh"
+#include "device_common.cuh"
 
 namespace sfcdd {
 
 constexpr int FB = 256;
-
-// packed lower-triangular index -> (a, b), a >= b
-__device__ __forceinline__ void tri_decode(int idx, int& a, int& b) {
-  int t = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-  while ((t + 1) * (t + 2) / 2 <= idx) ++t;
-  while (t * (t + 1) / 2 > idx) --t;
-  a = t;
-  b = idx - t * (t + 1) / 2;
-}
-
-// stored tile number t of matrix (fb, nt) -> (I, K)
-__device__ __forceinline__ void skyline_decode(const TileSetDev& ts, int fb, int nt, int t, int& I,
-                                               int& K) {
-  int lo = 0, hi = nt - 1;
-  while (lo < hi) {  // last I with rowoff[I] <= t
-    const int mid = (lo + hi + 1) >> 1;
-    if (ts.rowoff[fb + mid] <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  I = lo;
-  K = ts.kmin[fb + I] + (t - ts.rowoff[fb + I]);
-}
-
-__device__ __forceinline__ int stored_tiles(const TileSetDev& ts, int fb, int nt) {
-  return ts.rowoff[fb + nt - 1] + (nt - ts.kmin[fb + nt - 1]);
-}
 
 template <class T>
 __device__ __forceinline__ T from_double(double v) { return T(v); }
@@ -77,24 +51,7 @@ __global__ void k_envelope_local(GridDev g, PartDev pd, const unsigned* __restri
   const int fb = ts.vbase[m] / TILE;
   const int start = pd.start[m];
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    int p = start + r;
-    if (p >= g.N) p -= g.N;
-    const unsigned c = code[p];
-    int first = r;
-    for (int j = 0; j < g.d; ++j) {
-      const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
-      const unsigned unit = 1u << g.off[j];
-      if (kj > 1u) {
-        int cg = invpad[c - unit] - start;
-        if (cg < 0) cg += g.N;
-        if (cg < n && cg < first) first = cg;
-      }
-      if (kj < (unsigned)g.size[j]) {
-        int cg = invpad[c + unit] - start;
-        if (cg < 0) cg += g.N;
-        if (cg < n && cg < first) first = cg;
-      }
-    }
+    const int first = envelope_row(g, code, invpad, start, n, r);
     if (first < r) atomicMin(&tfirst[fb + r / TILE], first);
   }
 }
@@ -110,15 +67,8 @@ void launch_envelope_local(const GridDev& g, const PartDev& pd, const unsigned* 
 __global__ void k_envelope_coarse(GridDev g, PartDev pd, const unsigned* __restrict__ code,
                                   const int* __restrict__ invpad, int fbc, int* tfirst) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += gridDim.x * blockDim.x) {
-    const int a = coarse_block_of(pd, p);
-    const unsigned c = code[p];
-    int first = a;
-    for (int j = 0; j < g.d; ++j) {
-      const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
-      const unsigned unit = 1u << g.off[j];
-      if (kj > 1u) first = min(first, coarse_block_of(pd, invpad[c - unit]));
-      if (kj < (unsigned)g.size[j]) first = min(first, coarse_block_of(pd, invpad[c + unit]));
-    }
+    int a;
+    const int first = envelope_coarse_point(g, pd, code, invpad, p, a);
     if (first < a) atomicMin(&tfirst[fbc + a / TILE], first);
   }
 }
@@ -146,33 +96,7 @@ __global__ void __launch_bounds__(FB) k_assemble_local(GridDev g, PartDev pd,
   skyline_decode(ts, fb, nt, idx, a, b);
   for (int k = threadIdx.x; k < TILE2; k += FB) sm[k] = 0.0;
   __syncthreads();
-  const int n = ts.n[m];
-  const int start = pd.start[m];
-  if (threadIdx.x < TILE) {
-    const int tr = threadIdx.x;
-    const int rg = a * TILE + tr;
-    if (rg >= n) {
-      if (a == b) sm[tr * TILE + tr] = 1.0;  // padding: identity
-    } else {
-      int p = start + rg;
-      if (p >= g.N) p -= g.N;
-      if (a == b) sm[tr * TILE + tr] = g.diag;
-      const unsigned c = code[p];
-      for (int j = 0; j < g.d; ++j) {
-        const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
-        const unsigned unit = 1u << g.off[j];
-        for (int s = 0; s < 2; ++s) {
-          if (s == 0 && kj <= 1u) continue;
-          if (s == 1 && kj >= (unsigned)g.size[j]) continue;
-          const int q = invpad[s == 0 ? c - unit : c + unit];
-          int cg = q - start;
-          if (cg < 0) cg += g.N;
-          if (cg < n && cg < rg && cg >= b * TILE && cg < (b + 1) * TILE)
-            sm[tr * TILE + (cg - b * TILE)] = -g.w[j];
-        }
-      }
-    }
-  }
+  assemble_local_tile(g, code, invpad, pd.start[m], ts.n[m], a, b, sm);
   __syncthreads();
   T* out = tiles + ts.tbase[m] + (long long)idx * TILE2;
   for (int k = threadIdx.x; k < TILE2; k += FB) out[k] = from_double<T>(sm[k]);
@@ -206,60 +130,11 @@ __global__ void __launch_bounds__(FB) k_assemble_coarse(GridDev g, PartDev pd,
   extern __shared__ __align__(16) unsigned char dsm_coarse[];
   double* acc = reinterpret_cast<double*>(dsm_coarse);
   int* cnt = reinterpret_cast<int*>(acc + TILE2);
-  const int N0 = cts.n[0];
   const int nt = cts.nt[0];
   const int fb = cts.vbase[0] / TILE;
   int R, C;
   skyline_decode(cts, fb, nt, blockIdx.x, R, C);
-  const int tr = threadIdx.x >> 2, sub = threadIdx.x & 3;
-  const int arow = R * TILE + tr;
-  int bstart = 0, bsize = 0;
-  if (arow < N0) {
-    const int t = arow / pd.q, mm = arow % pd.q;
-    const int n = tilde_size(pd, t);
-    const int bf = n / pd.q, br = n % pd.q;
-    bstart = tilde_off(pd, t) + (mm < br ? mm * (bf + 1) : br * (bf + 1) + (mm - br) * bf);
-    bsize = mm < br ? bf + 1 : bf;
-  }
-  for (int k = threadIdx.x; k < TILE2; k += FB) {
-    const int r = k / TILE, c = k % TILE;
-    const int ar = R * TILE + r, bc = C * TILE + c;
-    double v = 0.0;
-    if (ar == bc) {
-      if (ar < N0) {
-        const int t = ar / pd.q, mm = ar % pd.q;
-        const int n = tilde_size(pd, t);
-        const int bf = n / pd.q, br = n % pd.q;
-        v = (double)(mm < br ? bf + 1 : bf) * g.diag;
-      } else {
-        v = 1.0;  // padding: identity
-      }
-    }
-    acc[k] = v;
-  }
-  for (int j = 0; j < g.d; ++j) {
-    for (int k = threadIdx.x; k < TILE2; k += FB) cnt[k] = 0;
-    __syncthreads();
-    if (arow < N0) {
-      const unsigned unit = 1u << g.off[j];
-      for (int u = sub; u < bsize; u += 4) {
-        const unsigned c = code[bstart + u];
-        const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
-        for (int s = 0; s < 2; ++s) {
-          if (s == 0 && kj <= 1u) continue;
-          if (s == 1 && kj >= (unsigned)g.size[j]) continue;
-          const int q = invpad[s == 0 ? c - unit : c + unit];
-          const int bcol = coarse_block_of(pd, q);
-          if (bcol >= C * TILE && bcol < (C + 1) * TILE && bcol <= arow)
-            atomicAdd(&cnt[tr * TILE + (bcol - C * TILE)], 1);
-        }
-      }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < TILE2; k += FB)
-      if (cnt[k]) acc[k] -= g.w[j] * (double)cnt[k];
-    __syncthreads();
-  }
+  assemble_coarse_tile(g, pd, cts.n[0], code, invpad, R, C, acc, cnt);
   double* out = tiles + cts.tbase[0] + (long long)blockIdx.x * TILE2;
   for (int k = threadIdx.x; k < TILE2; k += FB) out[k] = acc[k];
 }

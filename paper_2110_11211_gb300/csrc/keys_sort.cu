@@ -17,49 +17,8 @@ __global__ void k_keygen(GridDev g, unsigned long long* __restrict__ keys,
                          unsigned* __restrict__ codes) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= g.N) return;
-  unsigned long long X[D];
-  unsigned code = 0;
-  int rem = id;
-#pragma unroll
-  for (int j = D - 1; j >= 0; --j) {
-    const int kj = rem % g.size[j] + 1;
-    rem /= g.size[j];
-    X[j] = (unsigned long long)kj << (g.nbits - g.lev[j]);
-    code |= (unsigned)kj << g.off[j];
-  }
-  const int nb = g.nbits;
-  if (nb > 0) {
-    const unsigned long long top = 1ull << (nb - 1);
-    // undo excess work from the top bit down to bit 1
-    for (unsigned long long Q = top; Q > 1; Q >>= 1) {
-      const unsigned long long low = Q - 1;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        if (X[i] & Q) {
-          X[0] ^= low;                       // invert
-        } else {
-          const unsigned long long t = (X[0] ^ X[i]) & low;  // exchange
-          X[0] ^= t;
-          X[i] ^= t;
-        }
-      }
-    }
-    // Gray encode
-#pragma unroll
-    for (int i = 1; i < D; ++i) X[i] ^= X[i - 1];
-    unsigned long long t = 0;
-    for (unsigned long long Q = top; Q > 1; Q >>= 1)
-      if (X[D - 1] & Q) t ^= Q - 1;
-#pragma unroll
-    for (int i = 0; i < D; ++i) X[i] ^= t;
-  }
-  // interleave: bit b of axis i, levels from the most significant, axis 0 first
-  unsigned long long key = 0;
-  for (int b = nb - 1; b >= 0; --b) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) key = (key << 1) | ((X[i] >> b) & 1ull);
-  }
-  keys[id] = key;
+  unsigned code;
+  keys[id] = hilbert_key_of<D>(g, id, code);
   codes[id] = code;
 }
 

@@ -74,6 +74,66 @@ __host__ __device__ inline int coarse_block_of(const PartDev& pd, int p) {
   return t * pd.q + m;
 }
 
+// Hilbert key (Sec. 3.2, Skilling's transform) of the point with lexicographic
+// id `id`; also returns its packed code.  D = dimension.
+template <int D>
+__device__ __forceinline__ unsigned long long hilbert_key_of(const GridDev& g, int id,
+                                                             unsigned& code) {
+  unsigned long long X[D];
+  code = 0;
+  int rem = id;
+#pragma unroll
+  for (int j = D - 1; j >= 0; --j) {
+    const int kj = rem % g.size[j] + 1;
+    rem /= g.size[j];
+    X[j] = (unsigned long long)kj << (g.nbits - g.lev[j]);
+    code |= (unsigned)kj << g.off[j];
+  }
+  const int nb = g.nbits;
+  if (nb > 0) {
+    const unsigned long long top = 1ull << (nb - 1);
+    for (unsigned long long Q = top; Q > 1; Q >>= 1) {  // undo excess work
+      const unsigned long long low = Q - 1;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        if (X[i] & Q) {
+          X[0] ^= low;  // invert
+        } else {
+          const unsigned long long t = (X[0] ^ X[i]) & low;  // exchange
+          X[0] ^= t;
+          X[i] ^= t;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 1; i < D; ++i) X[i] ^= X[i - 1];  // Gray encode
+    unsigned long long t = 0;
+    for (unsigned long long Q = top; Q > 1; Q >>= 1)
+      if (X[D - 1] & Q) t ^= Q - 1;
+#pragma unroll
+    for (int i = 0; i < D; ++i) X[i] ^= t;
+  }
+  unsigned long long key = 0;  // bits level by level, axis 0 first
+  for (int b = nb - 1; b >= 0; --b) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) key = (key << 1) | ((X[i] >> b) & 1ull);
+  }
+  return key;
+}
+
+// One subgrid problem of a batch: its grid, partition, and where its data
+// sits in the batch-wide arrays (positions are local to the subgrid).
+struct SubDesc {
+  GridDev g;
+  PartDev pd;      // start/len/omega point into the batch arrays at this subgrid
+  int base;        // first batch-wide curve position / vector entry
+  int ibase;       // offset of this subgrid's invpad table
+  int g0base;      // offset of its coarse vector (nt0 * TILE doubles)
+  int mat0;        // first local matrix; the coarse matrix is cmat
+  int cmat;
+  int N0;
+};
+
 // Tile-skyline set of several matrices.  Per-tile-row arrays are indexed by
 // fb + I with fb = vbase[m] / TILE (the global tile-row index of row 0 of m).
 struct TileSetDev {
@@ -123,6 +183,29 @@ struct ErrWord {
   int code;    // sfcdd_status
   int index;
 };
+
+// ---------------- host helpers (api.cu) ----------------
+// Grid description from levels and coefficients (coeffs may be null = ones).
+int make_grid(const int* levels, int d, const double* coeffs, GridDev& g, long long& N, int& B);
+// eqs. sloc / enlarge / omegai on the host (gamma read as round(gamma 2^16)/2^16).
+int partition_ranges(long long N, int P, double gamma, int weighting, std::vector<int>& start,
+                     std::vector<int>& len, std::vector<double>& omega, int& gfloor);
+// q of the "four levels coarser" rule, clamped to 1..floor(N/P).
+int paper_q(long long N, int P);
+// Tile-skyline bookkeeping of nmat matrices from the envelope of every tile row
+// (tfirst = first nonzero column of the tile row): per-row kmin/rowoff, stored
+// tile counts, element offsets (local matrices in one buffer, coarse ones in
+// another), column lists, per-step launch sizes and operation counts.
+struct SkylineHost {
+  std::vector<int> kmin, rowoff, colptr, colidx, stored, col_max_local, col_max_coarse;
+  std::vector<long long> tbase;
+  long long ltiles = 0, ctiles = 0;  // stored tiles in the local / coarse buffers
+  int max_ltiles = 0, max_ctiles = 0;
+  double potrf = 0, trsm = 0, syrk = 0, coarse = 0;
+};
+void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
+                   const std::vector<char>& is_coarse, const std::vector<int>& tfirst,
+                   SkylineHost& out);
 
 // ---------------- kernels / launchers (defined in the .cu files) ----------------
 
@@ -198,14 +281,23 @@ struct TrsvWork {
   int mat;
   int row;
 };
+// Where the right-hand side of a matrix comes from and which solve it belongs to:
+// a local matrix reads rhs[rhs_base + (start + row) mod rhs_len] (a cyclic slice of
+// its problem's curve-order vector), a coarse matrix reads g0[rhs_base + row].
+struct MatDesc {
+  int rhs_base;
+  int rhs_len;
+  int start;
+  int coarse;   // 1: FP64 coarse factor tiles, 0: local factor tiles
+  int sub;      // index of the PCG scalars (problem) the matrix belongs to
+};
 struct TrsvArgs {
   TileSetDev ts;
-  int P;                       // matrices 0..P-1 local (storage st), P = coarse (fp64)
+  const MatDesc* md;           // per matrix
   const void* ltiles;          // local factor tiles
-  const double* ctiles;        // coarse factor tiles (matrix P), may be null if no coarse
-  PartDev pd;
+  const double* ctiles;        // coarse factor tiles, may be null if no coarse
   const double* rhs;           // curve-order vector the local right-hand sides are sliced from
-  const double* g0;            // coarse right-hand side (length N0)
+  const double* g0;            // coarse right-hand sides
   double* y;                   // forward results, per matrix vbase
   double* dout;                // backward results, per matrix vbase
   const TrsvWork* work;        // work list, dependency-safe order
@@ -213,7 +305,7 @@ struct TrsvArgs {
   int* ready;                  // per (matrix, row) flags, indexed vbase/TILE + row
   unsigned long long* ticket;  // monotone ticket counter
   ErrWord* err;
-  const PcgScalars* sc;        // may be null: no early exit
+  const PcgScalars* sc;        // per problem (md.sub); null: no early exit
 };
 void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s);
 void launch_trsv_bwd(const TrsvArgs& a, Store st, cudaStream_t s);

@@ -131,12 +131,13 @@ __device__ void fwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
     const int grow = r * TILE + row;
     double g = 0.0;
     if (grow < n) {
-      if (m == a.P) {
-        g = a.g0[grow];
+      const MatDesc md = a.md[m];
+      if (md.coarse) {
+        g = a.g0[md.rhs_base + grow];
       } else {
-        int pos = a.pd.start[m] + grow;
-        if (pos >= a.pd.N) pos -= a.pd.N;
-        g = a.rhs[pos];
+        int pos = md.start + grow;
+        if (pos >= md.rhs_len) pos -= md.rhs_len;
+        g = a.rhs[md.rhs_base + pos];
       }
     }
     xs[row] = double(A(g) - mine);
@@ -257,17 +258,18 @@ __global__ void __launch_bounds__(TB) k_trsv(TrsvArgs a) {
   const unsigned long long raw = s_ticket;
   const int t = (int)(raw % (unsigned long long)a.nwork);
   const int epoch = (int)(raw / (unsigned long long)a.nwork) + 1;
-  if (a.sc && a.sc->done) return;
+  const TrsvWork wk = a.work[t];
+  const MatDesc md = a.md[wk.mat];
+  if (a.sc && a.sc[md.sub].done) return;
   if (threadIdx.x == 0) reinterpret_cast<int*>(xs + TILE)[0] = epoch;
   __syncthreads();
-  const TrsvWork wk = a.work[t];
   if (FWD) {
-    if (wk.mat == a.P)
+    if (md.coarse)
       fwd_row<double, double>(a, a.ctiles, wk.mat, wk.row, xs);
     else
       fwd_row<T, A>(a, reinterpret_cast<const T*>(a.ltiles), wk.mat, wk.row, xs);
   } else {
-    if (wk.mat == a.P)
+    if (md.coarse)
       bwd_row<double, double>(a, a.ctiles, wk.mat, wk.row, xs, red);
     else
       bwd_row<T, A>(a, reinterpret_cast<const T*>(a.ltiles), wk.mat, wk.row, xs, red);

@@ -6,7 +6,7 @@
 // Reductions are deterministic: a fixed grid (a function of N only) assigns
 // every element to one block, each block writes its partial, and the last
 // block to arrive sums the partials in block order and updates the scalars.
-#include "sfcdd_internal.cuh"
+#include "device_common.cuh"
 
 namespace sfcdd {
 
@@ -86,16 +86,8 @@ __global__ void __launch_bounds__(VB) k_stencil(GridDev g, const unsigned* __res
   double acc = 0.0;
   const int stride = gridDim.x * VB;
   for (int p = blockIdx.x * VB + threadIdx.x; p < g.N; p += stride) {
-    const unsigned c = __ldg(&code[p]);
-    const double xc = __ldg(&x[p]);
-    double v = g.diag * xc;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const unsigned kj = (c >> g.off[j]) & ((1u << g.lev[j]) - 1u);
-      const unsigned unit = 1u << g.off[j];
-      if (kj > 1u) v -= g.w[j] * __ldg(&x[__ldg(&invpad[c - unit])]);
-      if (kj < (unsigned)g.size[j]) v -= g.w[j] * __ldg(&x[__ldg(&invpad[c + unit])]);
-    }
+    double xc;
+    double v = stencil_point<D>(g, code, invpad, x, p, xc);
     if (MODE == 2) {
       v = b[p] - v;
       acc += v * v;
@@ -226,22 +218,10 @@ __global__ void __launch_bounds__(VB) k_prolong(PartDev pd, TileSetDev ts, int m
   if (DOT && sc->done) return;
   double acc[2] = {0.0, 0.0};
   const int stride = gridDim.x * VB;
-  const int ncand = min(2 * pd.g + 3, pd.P);
   const int coarse_base = mode != 1 ? __ldg(&ts.vbase[pd.P]) : 0;
+  auto lvbase = [&](int i) { return __ldg(&ts.vbase[i]); };
   for (int p = blockIdx.x * VB + threadIdx.x; p < pd.N; p += stride) {
-    double v = 0.0;
-    if (mode != 1) v = __ldg(&dvec[coarse_base + coarse_block_of(pd, p)]);
-    if (mode != 2) {
-      const int t = tilde_of(pd, p);
-      int i = t - pd.g - 1;
-      i = ((i % pd.P) + pd.P) % pd.P;
-      for (int k = 0; k < ncand; ++k) {
-        int o = p - __ldg(&pd.start[i]);
-        if (o < 0) o += pd.N;
-        if (o < __ldg(&pd.len[i])) v += __ldg(&pd.omega[i]) * __ldg(&dvec[__ldg(&ts.vbase[i]) + o]);
-        if (++i == pd.P) i = 0;
-      }
-    }
+    const double v = prolong_point(pd, mode, dvec, coarse_base, lvbase, p);
     if (DOT) {
       const double rp = r[p];
       acc[0] += rp * v;

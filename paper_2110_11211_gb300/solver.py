@@ -166,3 +166,78 @@ class Solver:
 
     def kernel_work(self, cls: str) -> float:
         return float(self._L.sfcdd_kernel_work(self._h, _lib.KERNEL_CLASSES.index(cls)))
+
+
+class BatchSolver:
+    """Many independent subgrid problems (same d, P, overlap, options), set up
+    together and solved in one CUDA-graph launch (sfcdd_batch_*).  Vectors are
+    the concatenation of the subgrids' lexicographic vectors at `offsets`."""
+
+    def __init__(self, levels_list, P, overlap, *, precision="fp64", weighting="omega", q=0,
+                 coeffs=None, flexible=-1, stream=None):
+        L = _lib.lib()
+        self.levels = [tuple(int(l) for l in lv) for lv in levels_list]
+        self.nsub = len(self.levels)
+        self.d = len(self.levels[0])
+        if any(len(lv) != self.d for lv in self.levels):
+            raise ValueError("all subgrids must have the same dimension")
+        opt = Options()
+        L.sfcdd_default_options(C.byref(opt))
+        self._coeffs = None
+        if coeffs is not None:
+            self._coeffs = (C.c_double * self.d)(*[float(c) for c in coeffs])
+            opt.coeffs = C.cast(self._coeffs, C.POINTER(C.c_double))
+        opt.q = int(q)
+        opt.weighting = _lib.WEIGHTING[weighting]
+        opt.precision = _lib.PRECISION[precision]
+        opt.flexible = int(flexible)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = C.c_void_p(stream.cuda_stream)
+        flat = (C.c_int * (self.nsub * self.d))(*[l for lv in self.levels for l in lv])
+        h = C.c_void_p()
+        check("sfcdd_batch_setup", L.sfcdd_batch_setup(flat, self.nsub, self.d, int(P),
+                                                       float(overlap), C.byref(opt), C.byref(h)))
+        self._h = h
+        self._L = L
+        offs = (C.c_longlong * (self.nsub + 1))()
+        check("sfcdd_batch_offsets", L.sfcdd_batch_offsets(h, offs))
+        self.offsets = [int(offs[i]) for i in range(self.nsub + 1)]
+        self.N = self.offsets[-1]
+
+    def info(self):
+        n = C.c_longlong()
+        fb = C.c_longlong()
+        ms = C.c_double()
+        check("sfcdd_batch_info", self._L.sfcdd_batch_info(self._h, C.byref(n), C.byref(fb),
+                                                           C.byref(ms)))
+        return {"N": n.value, "factor_bytes": fb.value, "setup_ms": ms.value}
+
+    def solve(self, f: torch.Tensor, rtol=1e-10, maxit=1000, check_status=True):
+        f = f.reshape(-1)
+        u = torch.empty_like(f)
+        per = (Stats * self.nsub)()
+        tot = Stats()
+        rc = self._L.sfcdd_batch_solve(self._h, _dev_ptr(f), _dev_ptr(u), float(rtol), int(maxit),
+                                       per, C.byref(tot))
+        if check_status:
+            check("sfcdd_batch_solve", rc)
+        return u, tot, [per[i] for i in range(self.nsub)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sfcdd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

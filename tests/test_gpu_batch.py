@@ -1,0 +1,78 @@
+"""GPU parity of the batched solve of many subgrid problems in one graph launch
+(the combination-technique subproblems of Sec. 2) against the oracle.
+
+Every subgrid must reach the same bars as a single solve: true relative
+residual <= 2e-10, solution within 1e-8 of the exact solution, and PCG
+iteration count within +-1 of the oracle's PCG on that subgrid."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import exact, krylov, schwarz
+from paper_2110_11211_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2110_11211_gb300.build import build
+    build()
+
+
+def run_batch(levels, P, gamma, precision, seed=71, rtol=1e-10):
+    from paper_2110_11211_gb300.solver import BatchSolver
+    f = np.concatenate([inputs.uniform(seed + k, inputs.grid_size(lv)) for k, lv in enumerate(levels)])
+    with BatchSolver(levels, P, gamma, precision=precision) as b:
+        u, tot, per = b.solve(torch.tensor(f, device="cuda"), rtol=rtol)
+        offs = b.offsets
+    return f, u.cpu().numpy(), tot, per, offs
+
+
+@pytest.mark.parametrize("d,norms,P,gamma,precision", [
+    (2, (6, 7), 4, 0.5, "fp64"), (2, (7, 8), 5, 1.0, "fp64"), (3, (7, 8), 4, 0.5, "fp64"),
+    (4, (7, 8), 4, 0.5, "fp64"), (2, (6, 7), 4, 0.5, "fp32"), (3, (7, 8), 4, 0.5, "bf16")])
+def test_batched_solves_match_oracle(d, norms, P, gamma, precision):
+    levels = [lv for lv in inputs.combi_levels(d, norms) if inputs.grid_size(lv) >= P]
+    f, u, tot, per, offs = run_batch(levels, P, gamma, precision)
+    assert tot.status == 0 and tot.fail_index == 0
+    for k, lv in enumerate(levels):
+        fs = f[offs[k]:offs[k + 1]]
+        us = u[offs[k]:offs[k + 1]]
+        ue = exact.solve(lv, fs)
+        assert per[k].true_rel_res <= 2e-10, (lv, per[k].true_rel_res)
+        assert np.linalg.norm(us - ue) <= 1e-8 * np.linalg.norm(ue), lv
+        if precision == "fp64":
+            S = schwarz.Schwarz(lv, P, gamma)
+            _, its, _ = krylov.pcg(lambda v: S.A @ v, S.apply, fs, rtol=1e-10)
+            assert abs(per[k].iters - its) <= 1, (lv, per[k].iters, its)
+
+
+def test_batched_matches_single_handle_solves():
+    from paper_2110_11211_gb300.solver import Solver
+    levels = inputs.combi_levels(3, (7,))
+    f, u, tot, per, offs = run_batch(levels, 4, 0.5, "fp64", seed=81)
+    for k, lv in enumerate(levels):
+        with Solver(lv, 4, 0.5) as s:
+            us, st = s.solve(torch.tensor(f[offs[k]:offs[k + 1]], device="cuda"))
+        assert abs(st.iters - per[k].iters) <= 1
+        ref = us.cpu().numpy()
+        assert np.linalg.norm(u[offs[k]:offs[k + 1]] - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_combination_set_d4_l12_13_P64():
+    """All 385 level vectors of d = 4 with |l|_1 in {12, 13}, P = 64, gamma = 1/2,
+    FP32 local factors: every subgrid converges; a sample is checked against
+    the exact solution."""
+    levels = inputs.combi_levels(4, (12, 13))
+    assert len(levels) == 385
+    f, u, tot, per, offs = run_batch(levels, 64, 0.5, "fp32", seed=91)
+    assert tot.status == 0 and tot.fail_index == 0
+    assert max(p.true_rel_res for p in per) <= 2e-10
+    for k in range(0, 385, 48):
+        lv = levels[k]
+        fs = f[offs[k]:offs[k + 1]]
+        ue = exact.solve(lv, fs)
+        assert np.linalg.norm(u[offs[k]:offs[k + 1]] - ue) <= 1e-8 * np.linalg.norm(ue), lv
