@@ -236,7 +236,6 @@ struct sfcdd_handle {
   // substitution
   TrsvWork *work_f = nullptr, *work_b = nullptr;
   int nwork = 0;
-  int *ready_f = nullptr, *ready_b = nullptr;
   unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
   double *ybuf = nullptr, *dbuf = nullptr;
   long long vtotal = 0;
@@ -354,7 +353,6 @@ TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalar
   a.dout = h->dbuf;
   a.work = fwd ? h->work_f : h->work_b;
   a.nwork = h->nwork;
-  a.ready = fwd ? h->ready_f : h->ready_b;
   a.ticket = fwd ? h->ticket_f : h->ticket_b;
   a.err = h->err;
   a.sc = sc;
@@ -700,19 +698,14 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   TRY(dalloc(h, &h->work_b, h->nwork));
   SFCDD_CUDA_OK(cudaMemcpyAsync(h->work_f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(h->work_b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-  const long long nflags = h->vtotal / TILE;
-  TRY(dalloc(h, &h->ready_f, nflags));
-  TRY(dalloc(h, &h->ready_b, nflags));
   TRY(dalloc(h, &h->ticket_f, 1));
   TRY(dalloc(h, &h->ticket_b, 1));
-  SFCDD_CUDA_OK(cudaMemsetAsync(h->ready_f, 0, nflags * sizeof(int), s));
-  SFCDD_CUDA_OK(cudaMemsetAsync(h->ready_b, 0, nflags * sizeof(int), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->ticket_f, 0, sizeof(unsigned long long), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->ticket_b, 0, sizeof(unsigned long long), s));
   TRY(dalloc(h, &h->ybuf, h->vtotal));
   TRY(dalloc(h, &h->dbuf, h->vtotal));
-  SFCDD_CUDA_OK(cudaMemsetAsync(h->ybuf, 0, h->vtotal * sizeof(double), s));
-  SFCDD_CUDA_OK(cudaMemsetAsync(h->dbuf, 0, h->vtotal * sizeof(double), s));
+  launch_fill_pending(h->ybuf, h->vtotal, s);
+  launch_fill_pending(h->dbuf, h->vtotal, s);
 
   // PCG state
   TRY(dalloc(h, &h->b, N));

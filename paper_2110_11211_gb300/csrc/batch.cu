@@ -47,7 +47,6 @@ struct sfcdd_batch {
   int max_nt_local = 0, max_nt_coarse = 0;
   TrsvWork *work_f = nullptr, *work_b = nullptr;
   int nwork = 0;
-  int *ready_f = nullptr, *ready_b = nullptr;
   unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
   double *ybuf = nullptr, *dbuf = nullptr;
   double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr,
@@ -428,7 +427,6 @@ TrsvArgs batch_trsv_args(sfcdd_batch* b, bool fwd) {
   a.dout = b->dbuf;
   a.work = fwd ? b->work_f : b->work_b;
   a.nwork = b->nwork;
-  a.ready = fwd ? b->ready_f : b->ready_b;
   a.ticket = fwd ? b->ticket_f : b->ticket_b;
   a.err = b->err;
   a.sc = b->sc;
@@ -720,18 +718,14 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   BTRY(balloc(b, &b->work_b, b->nwork));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-  BTRY(balloc(b, &b->ready_f, nrows));
-  BTRY(balloc(b, &b->ready_b, nrows));
   BTRY(balloc(b, &b->ticket_f, 1));
   BTRY(balloc(b, &b->ticket_b, 1));
-  SFCDD_CUDA_OK(cudaMemsetAsync(b->ready_f, 0, nrows * sizeof(int), s));
-  SFCDD_CUDA_OK(cudaMemsetAsync(b->ready_b, 0, nrows * sizeof(int), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_f, 0, sizeof(unsigned long long), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_b, 0, sizeof(unsigned long long), s));
   BTRY(balloc(b, &b->ybuf, vb));
   BTRY(balloc(b, &b->dbuf, vb));
-  SFCDD_CUDA_OK(cudaMemsetAsync(b->ybuf, 0, vb * sizeof(double), s));
-  SFCDD_CUDA_OK(cudaMemsetAsync(b->dbuf, 0, vb * sizeof(double), s));
+  launch_fill_pending(b->ybuf, vb, s);
+  launch_fill_pending(b->dbuf, vb, s);
 
   // PCG state
   BTRY(balloc(b, &b->b, b->Ntot));

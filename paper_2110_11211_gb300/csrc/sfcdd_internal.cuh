@@ -291,6 +291,10 @@ struct MatDesc {
   int coarse;   // 1: FP64 coarse factor tiles, 0: local factor tiles
   int sub;      // index of the PCG scalars (problem) the matrix belongs to
 };
+// Bit pattern (a signalling NaN) marking a substitution result slot as not yet
+// written in the current launch.
+constexpr unsigned long long TRSV_PENDING = 0x7FF4DEADBEEF0000ull;
+void launch_fill_pending(double* p, long long n, cudaStream_t s);
 struct TrsvArgs {
   TileSetDev ts;
   const MatDesc* md;           // per matrix
@@ -302,7 +306,6 @@ struct TrsvArgs {
   double* dout;                // backward results, per matrix vbase
   const TrsvWork* work;        // work list, dependency-safe order
   int nwork;
-  int* ready;                  // per (matrix, row) flags, indexed vbase/TILE + row
   unsigned long long* ticket;  // monotone ticket counter
   ErrWord* err;
   const PcgScalars* sc;        // per problem (md.sub); null: no early exit
