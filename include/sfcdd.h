@@ -64,6 +64,10 @@ typedef struct {
   void* stream;         /* cudaStream_t for all work of this handle; NULL = legacy default stream */
   int profile;          /* != 0: time every kernel launch of setup and solves with CUDA events
                            (see sfcdd_set_profiling); 0 (default): no events */
+  int local_order;      /* numbering of the unknowns inside each subdomain for its Cholesky
+                           factor: 0 (default) lexicographic grid order (a fill-reducing order:
+                           the factor's envelope shrinks to a band), 1 ascending curve position.
+                           A_i^{-1} and therefore the preconditioner are the same either way. */
 } sfcdd_options;
 
 typedef struct {

@@ -134,6 +134,28 @@ int partition_ranges(long long N, int P, double gamma, int weighting, std::vecto
   return SFCDD_OK;
 }
 
+void build_worklists(const std::vector<int>& nt, const std::vector<char>& include,
+                     std::vector<TrsvWork>& wf, std::vector<TrsvWork>& wb) {
+  struct Item {
+    long long num, den;  // progress (r + 1) / nt as an exact fraction
+    int m, r;
+  };
+  std::vector<Item> items;
+  for (int m = 0; m < (int)nt.size(); ++m)
+    if (include[m])
+      for (int r = 0; r < nt[m]; ++r) items.push_back({r + 1, nt[m], m, r});
+  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+    const long long l = a.num * b.den, rr = b.num * a.den;
+    return l != rr ? l < rr : a.m < b.m;
+  });
+  wf.clear();
+  wb.clear();
+  for (const Item& it : items) {
+    wf.push_back({it.m, it.r});
+    wb.push_back({it.m, nt[it.m] - 1 - it.r});
+  }
+}
+
 void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
                    const std::vector<char>& is_coarse, const std::vector<int>& tfirst,
                    SkylineHost& o) {
@@ -226,6 +248,9 @@ struct sfcdd_handle {
   long long* d_zero64 = nullptr;
   int *d_kmin = nullptr, *d_rowoff = nullptr, *d_colptr = nullptr, *d_colidx = nullptr;
   MatDesc* d_md = nullptr;
+  int* d_lperm = nullptr;
+  int* d_linv = nullptr;
+  int local_order = 0;
   std::vector<int> h_kmin, h_rowoff, stored, col_max_local, col_max_coarse;
   TileSetDev ts{};
   Store st = Store::F64;
@@ -362,6 +387,8 @@ TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalar
 // One-matrix views (tile base 0) of the coarse matrix and of local matrix i.
 TileSetDev coarse_view(const sfcdd_handle* h) {
   TileSetDev v = h->ts;
+  v.lperm = nullptr;  // the local numbering does not apply to the coarse matrix
+  v.linv = nullptr;
   v.nmat = 1;
   v.n = h->d_n + h->P;
   v.nt = h->d_nt + h->P;
@@ -578,6 +605,46 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->ts.tbase = h->d_tbase;
   h->ts.vbase = h->d_vbase;
 
+  // numbering inside each subdomain: lexicographic grid order by default (a
+  // fill-reducing order; A_i^{-1} does not depend on it)
+  h->local_order = o.local_order;
+  if (h->local_order == 0 && h->variant != SFCDD_COARSE_ONLY) {
+    std::vector<int> mstart(P), mN(P, h->N), mcb(P, 0), lb(P);
+    long long tot = 0;
+    for (int m = 0; m < P; ++m) {
+      mstart[m] = h->h_start[m];
+      lb[m] = (int)tot;
+      tot += h->h_n[m];
+    }
+    int *d_ms, *d_mN, *d_mcb, *d_lb;
+    unsigned long long* okeys;
+    unsigned* ovals;
+    unsigned char* otemp;
+    TRY(dalloc(h, &d_ms, P));
+    TRY(dalloc(h, &d_mN, P));
+    TRY(dalloc(h, &d_mcb, P));
+    TRY(dalloc(h, &d_lb, P));
+    TRY(dalloc(h, &h->d_lperm, h->vtotal));
+    TRY(dalloc(h, &h->d_linv, h->vtotal));
+    TRY(dalloc(h, &okeys, tot));
+    TRY(dalloc(h, &ovals, tot));
+    TRY(dalloc(h, &otemp, radix_sort_temp_bytes((int)tot)));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_ms, mstart.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_mN, mN.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_mcb, mcb.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_lb, lb.data(), P * sizeof(int), cudaMemcpyHostToDevice, s));
+    pf.run(SFCDD_K_SORT, [&] {
+      local_order_lex(h->ts, P, max_nlocal, d_ms, d_mN, d_mcb, d_lb, tot, h->curve_code, okeys,
+                      ovals, otemp, h->d_lperm, h->d_linv, s);
+    });
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    for (void* t : {(void*)okeys, (void*)ovals, (void*)otemp, (void*)d_ms, (void*)d_mN,
+                    (void*)d_mcb, (void*)d_lb})
+      dfree(h, t);
+    h->ts.lperm = h->d_lperm;
+    h->ts.linv = h->d_linv;
+  }
+
   // Cholesky envelopes of every local matrix and of the coarse matrix: the
   // first column with a nonzero in each tile row (the factor keeps that profile)
   SkylineHost sky;
@@ -683,16 +750,13 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
 
   // substitution work lists: tile rows in dependency-safe order
   std::vector<TrsvWork> wf, wb;
-  const int m_lo = h->variant == SFCDD_COARSE_ONLY ? P : 0;
-  const int m_hi = h->variant == SFCDD_ONE_LEVEL ? P - 1 : P;
-  int maxall = 0;
-  for (int m = m_lo; m <= m_hi; ++m) maxall = std::max(maxall, h->h_nt[m]);
-  for (int rr = 0; rr < maxall; ++rr)
-    for (int m = m_lo; m <= m_hi; ++m)
-      if (rr < h->h_nt[m]) {
-        wf.push_back({m, rr});
-        wb.push_back({m, h->h_nt[m] - 1 - rr});
-      }
+  {
+    std::vector<char> include(P + 1, 1);
+    if (h->variant == SFCDD_COARSE_ONLY)
+      for (int m = 0; m < P; ++m) include[m] = 0;
+    if (h->variant == SFCDD_ONE_LEVEL) include[P] = 0;
+    build_worklists(h->h_nt, include, wf, wb);
+  }
   h->nwork = (int)wf.size();
   TRY(dalloc(h, &h->work_f, h->nwork));
   TRY(dalloc(h, &h->work_b, h->nwork));
@@ -837,6 +901,7 @@ void sfcdd_default_options(sfcdd_options* opt) {
   opt->flexible = -1;
   opt->stream = nullptr;
   opt->profile = 0;
+  opt->local_order = 0;
 }
 
 int sfcdd_setup_ex(const int* levels, int d, int P, double overlap, const sfcdd_options* opt,

@@ -138,8 +138,10 @@ __global__ void k_b_env_local(const SubDesc* __restrict__ sub, int P, const unsi
   const int n = ts.n[m];
   const int fb = ts.vbase[m] / TILE;
   const int start = sd.pd.start[i];
+  const int vb = ts.vbase[m];
+  const LocalOrder lo{ts.lperm ? ts.lperm + vb : nullptr, ts.linv ? ts.linv + vb : nullptr};
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const int first = envelope_row(sd.g, code + sd.base, invpad + sd.ibase, start, n, r);
+    const int first = envelope_row(sd.g, code + sd.base, invpad + sd.ibase, start, n, lo, r);
     if (first < r) atomicMin(&tfirst[fb + r / TILE], first);
   }
 }
@@ -179,8 +181,10 @@ __global__ void __launch_bounds__(256) k_b_assemble_local(const SubDesc* __restr
   skyline_decode(ts, fb, nt, idx, a, bb);
   for (int k = threadIdx.x; k < TILE2; k += blockDim.x) sm[k] = 0.0;
   __syncthreads();
-  assemble_local_tile(sd.g, code + sd.base, invpad + sd.ibase, sd.pd.start[m % P], ts.n[m], a, bb,
-                      sm);
+  const int vb = ts.vbase[m];
+  const LocalOrder lo{ts.lperm ? ts.lperm + vb : nullptr, ts.linv ? ts.linv + vb : nullptr};
+  assemble_local_tile(sd.g, code + sd.base, invpad + sd.ibase, sd.pd.start[m % P], ts.n[m], lo, a,
+                      bb, sm);
   __syncthreads();
   T* out = tiles + ts.tbase[m] + (long long)idx * TILE2;
   for (int k = threadIdx.x; k < TILE2; k += blockDim.x) out[k] = to_store<T>(sm[k]);
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(BT) k_b_prolong(const SubDesc* __restrict__ su
   auto lvbase = [&](int i) { return __ldg(&ts.vbase[sd.mat0 + i]); };
   double a1 = 0.0, a2 = 0.0;
   for (int i = threadIdx.x; i < sd.g.N; i += BT) {
-    const double v = prolong_point(sd.pd, 0, dvec, cbase, lvbase, i);
+    const double v = prolong_point(sd.pd, 0, dvec, cbase, lvbase, ts.linv, i);
     const double ri = r[sd.base + i];
     a1 += ri * v;
     a2 += ri * z[sd.base + i];
@@ -608,7 +612,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   k_b_invpad<<<gsub, 256, 0, s>>>(b->dsub, b->code, b->invpad);
   SFCDD_CUDA_OK(cudaGetLastError());
 
-  // tile layout and envelopes
+  // tile layout, local numbering (lexicographic by default) and envelopes
   int *d_n, *d_nt, *d_vbase, *tfirst;
   long long* d_tbase;
   BTRY(balloc(b, &d_n, b->nmat));
@@ -625,9 +629,48 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   b->ts.vbase = d_vbase;
   b->ts.tbase = d_tbase;
   const int max_nt_all = std::max(b->max_nt_local, b->max_nt_coarse);
-  launch_envelope_init(b->ts, b->nmat, max_nt_all, tfirst, s);
   int max_nl = 0;
   for (int m = 0; m < b->nlocal; ++m) max_nl = std::max(max_nl, h_n[m]);
+  if (o.local_order == 0) {
+    std::vector<int> mstart(b->nlocal), mN(b->nlocal), mcb(b->nlocal), lb(b->nlocal);
+    long long tot = 0;
+    for (int m = 0; m < b->nlocal; ++m) {
+      const SubDesc& sd = b->hsub[m / P];
+      mstart[m] = start_all[m];
+      mN[m] = sd.pd.N;
+      mcb[m] = sd.base;
+      lb[m] = (int)tot;
+      tot += h_n[m];
+    }
+    int *d_ms, *d_mN, *d_mcb, *d_lb, *lperm, *linv;
+    unsigned long long* okeys;
+    unsigned* ovals;
+    unsigned char* otemp;
+    BTRY(balloc(b, &d_ms, b->nlocal));
+    BTRY(balloc(b, &d_mN, b->nlocal));
+    BTRY(balloc(b, &d_mcb, b->nlocal));
+    BTRY(balloc(b, &d_lb, b->nlocal));
+    BTRY(balloc(b, &lperm, vb));
+    BTRY(balloc(b, &linv, vb));
+    BTRY(balloc(b, &okeys, tot));
+    BTRY(balloc(b, &ovals, tot));
+    BTRY(balloc(b, &otemp, radix_sort_temp_bytes((int)tot)));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_ms, mstart.data(), b->nlocal * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_mN, mN.data(), b->nlocal * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_mcb, mcb.data(), b->nlocal * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_lb, lb.data(), b->nlocal * sizeof(int), cudaMemcpyHostToDevice, s));
+    local_order_lex(b->ts, b->nlocal, max_nl, d_ms, d_mN, d_mcb, d_lb, tot, b->code, okeys, ovals,
+                    otemp, lperm, linv, s);
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    for (auto& a : b->allocs)
+      if (a == okeys || a == ovals || a == otemp) {
+        cudaFree(a);
+        a = nullptr;
+      }
+    b->ts.lperm = lperm;
+    b->ts.linv = linv;
+  }
+  launch_envelope_init(b->ts, b->nmat, max_nt_all, tfirst, s);
   k_b_env_local<<<dim3((max_nl + 255) / 256, b->nlocal), 256, 0, s>>>(b->dsub, P, b->code,
                                                                       b->invpad, b->ts, tfirst);
   k_b_env_coarse<<<gsub, 256, 0, s>>>(b->dsub, b->code, b->invpad, b->ts, tfirst);
@@ -707,12 +750,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   BTRY(balloc(b, &b->d_md, b->nmat));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_md, md.data(), b->nmat * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
   std::vector<TrsvWork> wf, wb;
-  for (int rr = 0; rr < max_nt_all; ++rr)
-    for (int m = 0; m < b->nmat; ++m)
-      if (rr < b->h_nt[m]) {
-        wf.push_back({m, rr});
-        wb.push_back({m, b->h_nt[m] - 1 - rr});
-      }
+  build_worklists(b->h_nt, std::vector<char>(b->nmat, 1), wf, wb);
   b->nwork = (int)wf.size();
   BTRY(balloc(b, &b->work_f, b->nwork));
   BTRY(balloc(b, &b->work_b, b->nwork));

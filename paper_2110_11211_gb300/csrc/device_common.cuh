@@ -42,22 +42,39 @@ __device__ __forceinline__ int neighbour(const GridDev& g, const int* __restrict
   return kj < (unsigned)g.size[j] ? __ldg(&invpad[c + unit]) : -1;
 }
 
+// Local numbering of a subdomain (start, n): local row r sits at curve position
+// lperm[r] (lperm null: start + r, cyclic), and the point at offset
+// o = (p - start) mod N inside the range has local row linv[o] (null: o).
+struct LocalOrder {
+  const int* lperm;
+  const int* linv;
+  __device__ __forceinline__ int pos(const GridDev& g, int start, int r) const {
+    if (lperm) return lperm[r];
+    int p = start + r;
+    return p >= g.N ? p - g.N : p;
+  }
+  // local row of curve position q, or -1 if q lies outside the range
+  __device__ __forceinline__ int row(const GridDev& g, int start, int n, int q) const {
+    int o = q - start;
+    if (o < 0) o += g.N;
+    if (o >= n) return -1;
+    return linv ? linv[o] : o;
+  }
+};
+
 // Smallest local column with a nonzero in row r of the local matrix that starts
 // at curve position `start` and has n rows (Cholesky envelope of the row).
 __device__ __forceinline__ int envelope_row(const GridDev& g, const unsigned* __restrict__ code,
                                             const int* __restrict__ invpad, int start, int n,
-                                            int r) {
-  int p = start + r;
-  if (p >= g.N) p -= g.N;
-  const unsigned c = code[p];
+                                            LocalOrder lo, int r) {
+  const unsigned c = code[lo.pos(g, start, r)];
   int first = r;
   for (int j = 0; j < g.d; ++j)
     for (int s = 0; s < 2; ++s) {
       const int q = neighbour(g, invpad, c, j, s);
       if (q < 0) continue;
-      int cg = q - start;
-      if (cg < 0) cg += g.N;
-      if (cg < n && cg < first) first = cg;
+      const int cg = lo.row(g, start, n, q);
+      if (cg >= 0 && cg < first) first = cg;
     }
   return first;
 }
@@ -83,7 +100,8 @@ __device__ __forceinline__ int envelope_coarse_point(const GridDev& g, const Par
 __device__ __forceinline__ void assemble_local_tile(const GridDev& g,
                                                     const unsigned* __restrict__ code,
                                                     const int* __restrict__ invpad, int start,
-                                                    int n, int a, int b, double* sm) {
+                                                    int n, LocalOrder lo, int a, int b,
+                                                    double* sm) {
   if (threadIdx.x >= TILE) return;
   const int tr = threadIdx.x;
   const int rg = a * TILE + tr;
@@ -91,17 +109,14 @@ __device__ __forceinline__ void assemble_local_tile(const GridDev& g,
     if (a == b) sm[tr * TILE + tr] = 1.0;  // padding: identity
     return;
   }
-  int p = start + rg;
-  if (p >= g.N) p -= g.N;
   if (a == b) sm[tr * TILE + tr] = g.diag;
-  const unsigned c = code[p];
+  const unsigned c = code[lo.pos(g, start, rg)];
   for (int j = 0; j < g.d; ++j)
     for (int s = 0; s < 2; ++s) {
       const int q = neighbour(g, invpad, c, j, s);
       if (q < 0) continue;
-      int cg = q - start;
-      if (cg < 0) cg += g.N;
-      if (cg < n && cg < rg && cg >= b * TILE && cg < (b + 1) * TILE)
+      const int cg = lo.row(g, start, n, q);
+      if (cg >= 0 && cg < rg && cg >= b * TILE && cg < (b + 1) * TILE)
         sm[tr * TILE + (cg - b * TILE)] = -g.w[j];
     }
 }
@@ -180,13 +195,15 @@ __device__ __forceinline__ double stencil_point(const GridDev& g, const unsigned
   return v;
 }
 
-// z_p = d_0[block(p)] + sum_i omega_i d_i[p - start_i] (eq. addSW), reading the
+// z_p = d_0[block(p)] + sum_i omega_i d_i[row_i(p)] (eq. addSW), reading the
 // coarse result at dvec[coarse_base + block] and subdomain i's result at
-// dvec[lvbase(i) + offset]; mode 0 two-level, 1 one level, 2 coarse only.
+// dvec[lvbase(i) + row], row = linv[lvbase(i) + offset] (linv null: the offset);
+// mode 0 two-level, 1 one level, 2 coarse only.
 template <class LocalBase>
 __device__ __forceinline__ double prolong_point(const PartDev& pd, int mode,
                                                 const double* __restrict__ dvec, int coarse_base,
-                                                LocalBase lvbase, int p) {
+                                                LocalBase lvbase, const int* __restrict__ linv,
+                                                int p) {
   double v = 0.0;
   if (mode != 1) v = __ldg(&dvec[coarse_base + coarse_block_of(pd, p)]);
   if (mode != 2) {
@@ -197,7 +214,11 @@ __device__ __forceinline__ double prolong_point(const PartDev& pd, int mode,
     for (int k = 0; k < ncand; ++k) {
       int o = p - __ldg(&pd.start[i]);
       if (o < 0) o += pd.N;
-      if (o < __ldg(&pd.len[i])) v += __ldg(&pd.omega[i]) * __ldg(&dvec[lvbase(i) + o]);
+      if (o < __ldg(&pd.len[i])) {
+        const int vb = lvbase(i);
+        const int row = linv ? __ldg(&linv[vb + o]) : o;
+        v += __ldg(&pd.omega[i]) * __ldg(&dvec[vb + row]);
+      }
       if (++i == pd.P) i = 0;
     }
   }

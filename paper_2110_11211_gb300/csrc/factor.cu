@@ -50,8 +50,10 @@ __global__ void k_envelope_local(GridDev g, PartDev pd, const unsigned* __restri
   const int n = ts.n[m];
   const int fb = ts.vbase[m] / TILE;
   const int start = pd.start[m];
+  const int vb = ts.vbase[m];
+  const LocalOrder lo{ts.lperm ? ts.lperm + vb : nullptr, ts.linv ? ts.linv + vb : nullptr};
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const int first = envelope_row(g, code, invpad, start, n, r);
+    const int first = envelope_row(g, code, invpad, start, n, lo, r);
     if (first < r) atomicMin(&tfirst[fb + r / TILE], first);
   }
 }
@@ -96,7 +98,9 @@ __global__ void __launch_bounds__(FB) k_assemble_local(GridDev g, PartDev pd,
   skyline_decode(ts, fb, nt, idx, a, b);
   for (int k = threadIdx.x; k < TILE2; k += FB) sm[k] = 0.0;
   __syncthreads();
-  assemble_local_tile(g, code, invpad, pd.start[m], ts.n[m], a, b, sm);
+  const int vb = ts.vbase[m];
+  const LocalOrder lo{ts.lperm ? ts.lperm + vb : nullptr, ts.linv ? ts.linv + vb : nullptr};
+  assemble_local_tile(g, code, invpad, pd.start[m], ts.n[m], lo, a, b, sm);
   __syncthreads();
   T* out = tiles + ts.tbase[m] + (long long)idx * TILE2;
   for (int k = threadIdx.x; k < TILE2; k += FB) out[k] = from_double<T>(sm[k]);
@@ -340,15 +344,22 @@ void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, c
 }
 
 // Dense symmetric N x N copy (row-major) of an FP64 tile-skyline matrix before
-// factorization (introspection only); entries outside the envelope are zero.
+// factorization (introspection only), rows and columns in ascending cyclic
+// curve order (mapped through the local numbering); entries outside the
+// envelope are zero.
 __global__ void k_unpack_dense(TileSetDev ts, int m, const double* __restrict__ tiles,
                                double* __restrict__ dense) {
   const int n = ts.n[m];
   const int fb = ts.vbase[m] / TILE;
+  const int* linv = ts.linv ? ts.linv + ts.vbase[m] : nullptr;
   const long long tot = (long long)n * n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += stride) {
     int r = (int)(e / n), c = (int)(e % n);
+    if (linv) {
+      r = linv[r];
+      c = linv[c];
+    }
     if (c > r) {
       const int t = r;
       r = c;
@@ -360,6 +371,51 @@ __global__ void k_unpack_dense(TileSetDev ts, int m, const double* __restrict__ 
       v = tiles[tile_at(ts, ts.tbase[m], fb, a, b) + (r % TILE) * TILE + (c % TILE)];
     dense[e] = v;
   }
+}
+
+__global__ void k_lorder_keys(TileSetDev ts, const int* __restrict__ mstart, const int* __restrict__ mN,
+                              const int* __restrict__ mcbase, const int* __restrict__ lbase,
+                              const unsigned* __restrict__ code, unsigned long long* __restrict__ keys,
+                              unsigned* __restrict__ vals) {
+  const int m = blockIdx.y;
+  const int n = ts.n[m], start = mstart[m], N = mN[m];
+  const unsigned* cs = code + mcbase[m];
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    int p = start + o;
+    if (p >= N) p -= N;
+    keys[lbase[m] + o] = ((unsigned long long)m << 32) | cs[p];
+    vals[lbase[m] + o] = (unsigned)o;
+  }
+}
+
+__global__ void k_lorder_scatter(TileSetDev ts, const int* __restrict__ mstart, const int* __restrict__ mN,
+                                 const int* __restrict__ lbase, long long total,
+                                 const unsigned long long* __restrict__ keys,
+                                 const unsigned* __restrict__ vals, int* __restrict__ lperm,
+                                 int* __restrict__ linv) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
+    const int m = (int)(keys[k] >> 32);
+    const int r = (int)(k - lbase[m]);
+    const int o = (int)vals[k];
+    int p = mstart[m] + o;
+    if (p >= mN[m]) p -= mN[m];
+    const int vb = ts.vbase[m];
+    lperm[vb + r] = p;
+    linv[vb + o] = r;
+  }
+}
+
+void local_order_lex(const TileSetDev& ts, int nmat, int max_n, const int* mstart, const int* mN,
+                     const int* mcbase, const int* lbase, long long total, const unsigned* code,
+                     unsigned long long* keys, unsigned* vals, void* temp, int* lperm, int* linv,
+                     cudaStream_t s) {
+  int mbits = 1;
+  while ((1 << mbits) < nmat) ++mbits;
+  k_lorder_keys<<<dim3((max_n + 255) / 256, nmat), 256, 0, s>>>(ts, mstart, mN, mcbase, lbase, code,
+                                                                 keys, vals);
+  radix_sort_pairs(keys, vals, (int)total, 32 + mbits, temp, s, nullptr);
+  k_lorder_scatter<<<152 * 8, 256, 0, s>>>(ts, mstart, mN, lbase, total, keys, vals, lperm, linv);
 }
 
 void launch_unpack_dense(const TileSetDev& ts, int m, const double* tiles, double* dense,

@@ -146,6 +146,8 @@ struct TileSetDev {
   const int* rowoff;         // [fb + I] tiles stored before tile row I in its matrix
   const int* colptr;         // [fb + K], [fb + K + 1]: range in colidx of rows I > K, kmin[I] <= K
   const int* colidx;         // those rows, ascending
+  const int* lperm;          // [vbase + r] curve position of local row r (null: curve order)
+  const int* linv;           // [vbase + o] local row of offset o in the range (null: curve order)
 };
 
 __device__ __forceinline__ long long tile_at(const TileSetDev& ts, long long tb, int fb, int I,
@@ -192,6 +194,13 @@ int partition_ranges(long long N, int P, double gamma, int weighting, std::vecto
                      std::vector<int>& len, std::vector<double>& omega, int& gfloor);
 // q of the "four levels coarser" rule, clamped to 1..floor(N/P).
 int paper_q(long long N, int P);
+// Substitution work lists over the matrices with include[m] != 0: rows ordered
+// by relative progress (r + 1) / nt[m] (backward: from the last row), so every
+// matrix advances at the same relative rate and each row follows its
+// predecessors in its own matrix.
+struct TrsvWork;
+void build_worklists(const std::vector<int>& nt, const std::vector<char>& include,
+                     std::vector<TrsvWork>& wf, std::vector<TrsvWork>& wb);
 // Tile-skyline bookkeeping of nmat matrices from the envelope of every tile row
 // (tfirst = first nonzero column of the tile row): per-row kmin/rowoff, stored
 // tile counts, element offsets (local matrices in one buffer, coarse ones in
@@ -273,6 +282,14 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                   void* tiles, Store st, ErrWord* err, cudaStream_t s, LaunchHook* hook);
 void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, cudaStream_t s);
+// Lexicographic numbering inside each local matrix: matrices [0, nmat) of ts,
+// matrix m covers the cyclic range (mstart[m], ts.n[m]) of a problem with
+// mN[m] points whose codes start at code + mcbase[m]; lbase[m] = sum of the
+// earlier sizes.  keys/vals/temp: scratch of total entries (+ sort temp).
+void local_order_lex(const TileSetDev& ts, int nmat, int max_n, const int* mstart, const int* mN,
+                     const int* mcbase, const int* lbase, long long total, const unsigned* code,
+                     unsigned long long* keys, unsigned* vals, void* temp, int* lperm, int* linv,
+                     cudaStream_t s);
 void launch_unpack_dense(const TileSetDev& ts, int m, const double* tiles, double* dense,
                          cudaStream_t s);
 

@@ -221,8 +221,13 @@ __device__ void fwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, i
       if (md.coarse) {
         gval = a.g0[md.rhs_base + grow];
       } else {
-        int pos = md.start + grow;
-        if (pos >= md.rhs_len) pos -= md.rhs_len;
+        int pos;
+        if (a.ts.lperm) {
+          pos = a.ts.lperm[vb + grow];
+        } else {
+          pos = md.start + grow;
+          if (pos >= md.rhs_len) pos -= md.rhs_len;
+        }
         gval = a.rhs[md.rhs_base + pos];
       }
     }

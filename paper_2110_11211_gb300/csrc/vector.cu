@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(VB) k_prolong(PartDev pd, TileSetDev ts, int m
   const int coarse_base = mode != 1 ? __ldg(&ts.vbase[pd.P]) : 0;
   auto lvbase = [&](int i) { return __ldg(&ts.vbase[i]); };
   for (int p = blockIdx.x * VB + threadIdx.x; p < pd.N; p += stride) {
-    const double v = prolong_point(pd, mode, dvec, coarse_base, lvbase, p);
+    const double v = prolong_point(pd, mode, dvec, coarse_base, lvbase, ts.linv, p);
     if (DOT) {
       const double rp = r[p];
       acc[0] += rp * v;

@@ -22,7 +22,7 @@ class Solver:
 
     def __init__(self, levels, P, overlap, *, precision="fp64", variant="additive",
                  weighting="omega", q=0, coeffs=None, flexible=-1, stream=None,
-                 profile=False):
+                 profile=False, local_order="lex"):
         L = _lib.lib()
         self.levels = tuple(int(l) for l in levels)
         self.d = len(self.levels)
@@ -42,6 +42,7 @@ class Solver:
         opt.precision = _lib.PRECISION[precision]
         opt.flexible = int(flexible)
         opt.profile = int(bool(profile))
+        opt.local_order = {"lex": 0, "curve": 1}[local_order]
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -174,7 +175,7 @@ class BatchSolver:
     the concatenation of the subgrids' lexicographic vectors at `offsets`."""
 
     def __init__(self, levels_list, P, overlap, *, precision="fp64", weighting="omega", q=0,
-                 coeffs=None, flexible=-1, stream=None):
+                 coeffs=None, flexible=-1, stream=None, local_order="lex"):
         L = _lib.lib()
         self.levels = [tuple(int(l) for l in lv) for lv in levels_list]
         self.nsub = len(self.levels)
@@ -191,6 +192,7 @@ class BatchSolver:
         opt.weighting = _lib.WEIGHTING[weighting]
         opt.precision = _lib.PRECISION[precision]
         opt.flexible = int(flexible)
+        opt.local_order = {"lex": 0, "curve": 1}[local_order]
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

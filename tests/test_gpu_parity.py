@@ -201,3 +201,25 @@ def test_full_size_aniso3d_sampled():
         ids = S.local_ids(i)
         ref[ids] += S.omega[i] * S.local_solve(i, g[ids])
     assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("levels,P,gamma", [((6, 6), 8, 0.5), ((4, 3, 3), 6, 1.0),
+                                            ((3, 2, 3, 2), 8, 0.5)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_local_order_does_not_change_the_preconditioner(levels, P, gamma, precision):
+    """The numbering inside a subdomain only changes the factor's envelope:
+    A_i^{-1} is the same, so applies agree to rounding and solves converge alike."""
+    N = grid.num_unknowns(levels)
+    g = torch.tensor(inputs.uniform(14, N), device="cuda")
+    out = {}
+    for order in ("lex", "curve"):
+        with make(levels, P, gamma, precision=precision, local_order=order) as s:
+            z = s.apply_precond(g).cpu().numpy()
+            u, st = s.solve(g, rtol=1e-10)
+            out[order] = (z, u.cpu().numpy(), st.iters, s.get_info().factor_bytes)
+    tol = 1e-12 if precision == "fp64" else 1e-4
+    zl, zc = out["lex"][0], out["curve"][0]
+    assert np.linalg.norm(zl - zc) <= tol * np.linalg.norm(zc)
+    assert np.linalg.norm(out["lex"][1] - out["curve"][1]) <= 1e-8 * np.linalg.norm(out["curve"][1])
+    assert abs(out["lex"][2] - out["curve"][2]) <= 1
+    assert out["lex"][3] <= out["curve"][3]
