@@ -156,21 +156,27 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 
 // Diagonal tile k of every matrix with nt > k: Cholesky in shared memory, then
 // the inverse of the lower-triangular factor block replaces the tile.
+// Right-looking unblocked Cholesky with a 16 x 16 thread grid (each thread
+// updates rows ty + 16a, columns tx + 16b), reciprocal pivots instead of
+// divisions, then X = L^{-1} row by row with every column in parallel (four
+// threads split each dot product), which keeps the dependent FP64 chains short.
 template <class T>
 __global__ void __launch_bounds__(FB) k_potrf(TileSetDev ts, int mat0, int k, T* __restrict__ tiles,
                                               ErrWord* err) {
   extern __shared__ __align__(16) unsigned char dsm_potrf[];
   T (*L)[TILE + 1] = reinterpret_cast<T (*)[TILE + 1]>(dsm_potrf);
   T (*X)[TILE + 1] = L + TILE;
-  T& s_inv = X[TILE][0];
+  T* rinv = &X[TILE][0];  // TILE reciprocal pivots (row TILE of X, TILE + 1 entries)
   const int m = mat0 + blockIdx.x;
   if (ts.nt[m] <= k) return;
   const int fb = ts.vbase[m] / TILE;
   T* tp = tiles + tile_at(ts, ts.tbase[m], fb, k, k);
-  for (int e = threadIdx.x; e < TILE2; e += FB) L[e / TILE][e % TILE] = tp[e];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < TILE2; e += FB) L[e / TILE][e % TILE] = tp[e];
   __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;
   for (int j = 0; j < TILE; ++j) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       T dj = L[j][j];
       if (!(dj > T(0))) {
         if (atomicCAS(&err->code, 0, (int)SFCDD_ERR_NOT_SPD) == 0) err->index = m;
@@ -178,31 +184,36 @@ __global__ void __launch_bounds__(FB) k_potrf(TileSetDev ts, int mat0, int k, T*
       }
       const T piv = sqrt(dj);
       L[j][j] = piv;
-      s_inv = T(1) / piv;
+      rinv[j] = T(1) / piv;
     }
     __syncthreads();
-    const T inv = s_inv;
-    for (int i = j + 1 + threadIdx.x; i < TILE; i += FB) L[i][j] *= inv;
+    if (tid > j && tid < TILE) L[tid][j] *= rinv[j];
     __syncthreads();
-    const int rem = TILE - j - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += FB) {
-      const int i = j + 1 + e / rem, l = j + 1 + e % rem;
-      if (l <= i) L[i][l] -= L[i][j] * L[l][j];
+#pragma unroll
+    for (int aa = 0; aa < TILE / 16; ++aa) {
+      const int i = ty + 16 * aa;
+      if (i <= j) continue;
+      const T lij = L[i][j];
+#pragma unroll
+      for (int bb = 0; bb < TILE / 16; ++bb) {
+        const int l = tx + 16 * bb;
+        if (l > j && l <= i) L[i][l] -= lij * L[l][j];
+      }
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular block, one column per thread
-  if (threadIdx.x < TILE) {
-    const int c = threadIdx.x;
-    for (int i = 0; i < c; ++i) X[i][c] = T(0);
-    for (int i = c; i < TILE; ++i) {
-      T s = (i == c) ? T(1) : T(0);
-      for (int kk = c; kk < i; ++kk) s -= L[i][kk] * X[kk][c];
-      X[i][c] = s / L[i][i];
-    }
+  // X = L^{-1}: row i needs rows < i; columns c <= i are independent
+  const int c = tid >> 2, part = tid & 3;
+  for (int i = 0; i < TILE; ++i) {
+    T sacc = T(0);
+    if (c < i)
+      for (int kk = c + part; kk < i; kk += 4) sacc += L[i][kk] * X[kk][c];
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+    if (part == 0) X[i][c] = c > i ? T(0) : ((c == i ? T(1) : T(0)) - sacc) * rinv[i];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TILE2; e += FB) tp[e] = X[e / TILE][e % TILE];
+  for (int e = tid; e < TILE2; e += FB) tp[e] = X[e / TILE][e % TILE];
 }
 
 // C = X * Y^T on 64x64 tiles (X, Y row-major in global), each thread a 4x4 block.
