@@ -68,6 +68,10 @@ typedef struct {
                            factor: 0 (default) lexicographic grid order (a fill-reducing order:
                            the factor's envelope shrinks to a band), 1 ascending curve position.
                            A_i^{-1} and therefore the preconditioner are the same either way. */
+  int slabs_local;      /* row slabs per 64-row tile row in the local substitutions (one CTA
+                           each): 1 or 2; 0 (default) = 1.  Splitting shortens the FP64 GEMV on
+                           the dependency chain from one tile row to the next. */
+  int slabs_coarse;     /* the same for the coarse substitutions: 1 or 4; 0 (default) = 4 */
 } sfcdd_options;
 
 typedef struct {
@@ -87,8 +91,9 @@ typedef struct {
   int d, P, q, nbits;   /* nbits = max_j l_j (curve resolution, Sec. 3.3) */
   int tile;             /* tile edge of the packed local factors */
   int precision, variant, weighting, flexible;
-  long long factor_bytes; /* bytes of all local factor tiles (read twice per apply) */
-  long long coarse_bytes; /* bytes of the coarse factor tiles (read twice per apply) */
+  long long factor_bytes; /* bytes of the local factor tiles, both substitution copies:
+                             Lh (read by the forward sweep) and Lh^T with E_K (backward) */
+  long long coarse_bytes; /* the same for the coarse factor (FP64) */
   double setup_ms;
 } sfcdd_info;
 

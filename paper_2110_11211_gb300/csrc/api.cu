@@ -135,15 +135,17 @@ int partition_ranges(long long N, int P, double gamma, int weighting, std::vecto
 }
 
 void build_worklists(const std::vector<int>& nt, const std::vector<char>& include,
-                     std::vector<TrsvWork>& wf, std::vector<TrsvWork>& wb) {
+                     const std::vector<int>& nsub, std::vector<TrsvWork>& wf,
+                     std::vector<TrsvWork>& wb) {
   struct Item {
     long long num, den;  // progress (r + 1) / nt as an exact fraction
-    int m, r;
+    int m, r, s;
   };
   std::vector<Item> items;
   for (int m = 0; m < (int)nt.size(); ++m)
     if (include[m])
-      for (int r = 0; r < nt[m]; ++r) items.push_back({r + 1, nt[m], m, r});
+      for (int r = 0; r < nt[m]; ++r)
+        for (int sl = 0; sl < nsub[m]; ++sl) items.push_back({r + 1, nt[m], m, r, sl});
   std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
     const long long l = a.num * b.den, rr = b.num * a.den;
     return l != rr ? l < rr : a.m < b.m;
@@ -151,9 +153,77 @@ void build_worklists(const std::vector<int>& nt, const std::vector<char>& includ
   wf.clear();
   wb.clear();
   for (const Item& it : items) {
-    wf.push_back({it.m, it.r});
-    wb.push_back({it.m, nt[it.m] - 1 - it.r});
+    wf.push_back({it.m, it.r, it.s});
+    wb.push_back({it.m, nt[it.m] - 1 - it.r, it.s});
   }
+}
+
+// Reverse Cuthill-McKee numbering of an undirected graph given as adjacency
+// lists adj[v * stride + k], k < deg[v]: per connected component a breadth-first
+// sweep from a pseudo-peripheral node (repeated sweeps from a minimum-degree
+// node of the last level while the number of levels grows), neighbours taken
+// by increasing degree (ties by index); the concatenated order is reversed.
+// order[r] = node numbered r.  Deterministic.
+void rcm_order(int n, const std::vector<int>& deg, const std::vector<int>& adj, int stride,
+               std::vector<int>& order) {
+  std::vector<std::vector<int>> nb(n);
+  for (int v = 0; v < n; ++v) {
+    nb[v].assign(adj.begin() + (size_t)v * stride, adj.begin() + (size_t)v * stride + deg[v]);
+    std::sort(nb[v].begin(), nb[v].end(), [&](int a, int b) {
+      return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+    });
+  }
+  std::vector<int> stamp(n, -1);
+  int stampv = 0;
+  // number of breadth-first levels from root; last = min-degree node of the last level
+  auto sweep = [&](int root, int& last) {
+    ++stampv;
+    std::vector<int> cur{root}, next;
+    stamp[root] = stampv;
+    int nlev = 1;
+    for (;;) {
+      next.clear();
+      for (int v : cur)
+        for (int u : nb[v])
+          if (stamp[u] != stampv) {
+            stamp[u] = stampv;
+            next.push_back(u);
+          }
+      if (next.empty()) break;
+      cur.swap(next);
+      ++nlev;
+    }
+    last = cur[0];
+    for (int v : cur)
+      if (deg[v] < deg[last] || (deg[v] == deg[last] && v < last)) last = v;
+    return nlev;
+  };
+  std::vector<char> seen(n, 0);
+  order.clear();
+  order.reserve(n);
+  for (int s0 = 0; s0 < n; ++s0) {
+    if (seen[s0]) continue;
+    int root = s0, levels = 0;
+    for (int it = 0; it < 8; ++it) {
+      int last;
+      const int l = sweep(root, last);
+      if (l <= levels) break;
+      levels = l;
+      root = last;
+    }
+    size_t head = order.size();
+    order.push_back(root);
+    seen[root] = 1;
+    while (head < order.size()) {
+      const int v = order[head++];
+      for (int u : nb[v])
+        if (!seen[u]) {
+          seen[u] = 1;
+          order.push_back(u);
+        }
+    }
+  }
+  std::reverse(order.begin(), order.end());
 }
 
 void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
@@ -231,6 +301,7 @@ struct sfcdd_handle {
   int precision = 0, variant = 0, weighting = 1, flexible = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;  // coarse factorization, concurrent with the local one
   GridDev g{};
   PartDev pd{};
   std::vector<int> h_start, h_len;
@@ -250,19 +321,24 @@ struct sfcdd_handle {
   MatDesc* d_md = nullptr;
   int* d_lperm = nullptr;
   int* d_linv = nullptr;
+  int* d_crow = nullptr;    // coarse block -> coarse factor row
+  int* d_cblock = nullptr;  // coarse factor row -> coarse block
   int local_order = 0;
   std::vector<int> h_kmin, h_rowoff, stored, col_max_local, col_max_coarse;
   TileSetDev ts{};
   Store st = Store::F64;
-  void* ltiles = nullptr;
+  void* ltiles = nullptr;   // Lh tiles of the local factors
+  void* lut = nullptr;      // Lh^T tiles, E_K on the diagonal
   double* ctiles = nullptr;
-  long long ltile_elems = 0, ctile_elems = 0;
-  int max_nt = 0, nt0 = 0, max_ltiles = 0;
+  double* cut = nullptr;
+  long long ltile_elems = 0, ctile_elems = 0, ldiag_elems = 0, cdiag_elems = 0;
+  int max_nt = 0, nt0 = 0, max_ltiles = 0, max_ctiles = 0;
+  int nsub_local = 1, nsub_coarse = 4;
   // substitution
   TrsvWork *work_f = nullptr, *work_b = nullptr;
   int nwork = 0;
   unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
-  double *ybuf = nullptr, *dbuf = nullptr;
+  double *ybuf = nullptr, *dbuf = nullptr, *zcbuf = nullptr;
   long long vtotal = 0;
   // PCG
   double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *qv = nullptr, *z = nullptr,
@@ -371,11 +447,15 @@ TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalar
   a.ts = h->ts;
   a.md = h->d_md;
   a.ltiles = h->ltiles;
+  a.lut = h->lut;
   a.ctiles = h->ctiles;
+  a.cut = h->cut;
   a.rhs = rhs;
   a.g0 = h->g0;
+  a.cblock = h->pd.cblock;
   a.y = h->ybuf;
   a.dout = h->dbuf;
+  a.zc = h->zcbuf;
   a.work = fwd ? h->work_f : h->work_b;
   a.nwork = h->nwork;
   a.ticket = fwd ? h->ticket_f : h->ticket_b;
@@ -509,6 +589,10 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
       h->weighting < 0 || h->weighting > 1)
     return SFCDD_ERR_INVALID_ARG;
   if (h->variant == SFCDD_BALANCED) return SFCDD_ERR_UNSUPPORTED;
+  h->nsub_local = o.slabs_local == 0 ? 1 : o.slabs_local;
+  h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
+  if ((h->nsub_local != 1 && h->nsub_local != 2) || (h->nsub_coarse != 1 && h->nsub_coarse != 4))
+    return SFCDD_ERR_INVALID_ARG;
   h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
   h->stream = (cudaStream_t)o.stream;
   h->profiling = o.profile != 0;
@@ -519,6 +603,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->st = (Store)h->precision;
 
   SFCDD_CUDA_OK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  SFCDD_CUDA_OK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
   cudaEvent_t e0, e1;
   SFCDD_CUDA_OK(cudaEventCreate(&e0));
   SFCDD_CUDA_OK(cudaEventCreate(&e1));
@@ -645,6 +730,50 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     h->ts.linv = h->d_linv;
   }
 
+  // Numbering of the coarse unknowns in the coarse factor: reverse
+  // Cuthill-McKee on the graph of adjacent coarse blocks, a profile-reducing
+  // order (A_0^{-1}, and so the coarse correction, is unchanged by it).  The
+  // adjacency lists come from the device; the ordering is host bookkeeping on
+  // N0 nodes.
+  if (h->variant != SFCDD_ONE_LEVEL && h->N0 > 1) {
+    const int N0 = h->N0;
+    const int bmax = (pd.f + (pd.r > 0 ? 1 : 0) + h->q - 1) / h->q;
+    const int maxdeg = std::min(N0 - 1, std::min(2048, std::max(32, bmax * 2 * d)));
+    int *d_adj = nullptr, *d_deg = nullptr;
+    TRY(dalloc(h, &d_adj, (size_t)N0 * maxdeg));
+    TRY(dalloc(h, &d_deg, N0));
+    pf.run(SFCDD_K_COARSE_ASSEMBLE, [&] {
+      launch_coarse_adjacency(g, pd, h->curve_code, h->invpad, maxdeg, d_adj, d_deg, s);
+    });
+    std::vector<int> deg(N0);
+    SFCDD_CUDA_OK(cudaMemcpyAsync(deg.data(), d_deg, N0 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    int dmax = 0;
+    bool ok = true;
+    for (int v : deg) {
+      if (v < 0) ok = false;
+      dmax = std::max(dmax, v);
+    }
+    if (ok && dmax > 0) {  // otherwise the coarse blocks keep the eq. restr order
+      std::vector<int> adj((size_t)N0 * dmax);
+      SFCDD_CUDA_OK(cudaMemcpy2DAsync(adj.data(), dmax * sizeof(int), d_adj, maxdeg * sizeof(int),
+                                      dmax * sizeof(int), N0, cudaMemcpyDeviceToHost, s));
+      SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+      std::vector<int> order, crow(N0);
+      rcm_order(N0, deg, adj, dmax, order);
+      for (int r = 0; r < N0; ++r) crow[order[r]] = r;
+      TRY(dalloc(h, &h->d_crow, N0));
+      TRY(dalloc(h, &h->d_cblock, N0));
+      SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_crow, crow.data(), N0 * sizeof(int), cudaMemcpyHostToDevice, s));
+      SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_cblock, order.data(), N0 * sizeof(int), cudaMemcpyHostToDevice, s));
+      SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
+      pd.crow = h->d_crow;
+      pd.cblock = h->d_cblock;
+    }
+    dfree(h, d_adj);
+    dfree(h, d_deg);
+  }
+
   // Cholesky envelopes of every local matrix and of the coarse matrix: the
   // first column with a nonzero in each tile row (the factor keeps that profile)
   SkylineHost sky;
@@ -672,8 +801,12 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->stored = sky.stored;
   for (int m = 0; m <= P; ++m) h->h_tbase[m] = sky.tbase[m];
   h->max_ltiles = sky.max_ltiles;
+  h->max_ctiles = sky.max_ctiles;
   h->ltile_elems = sky.ltiles * TILE2;
   h->ctile_elems = sky.ctiles * TILE2;
+  h->ldiag_elems = 0;
+  for (int m = 0; m < P; ++m) h->ldiag_elems += (long long)h->h_nt[m] * TILE2;
+  h->cdiag_elems = (long long)h->nt0 * TILE2;
   h->col_max_local = sky.col_max_local;
   h->col_max_coarse = sky.col_max_coarse;
   if (h->variant != SFCDD_COARSE_ONLY) {
@@ -700,6 +833,33 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   TRY(dalloc(h, &h->err, 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->err, 0, sizeof(ErrWord), s));
 
+  // Algorithm 1, steps 9-10: coarse matrix and its FP64 factor, on a side
+  // stream so that it overlaps the local factorization (the two are independent)
+  TRY(dalloc(h, &h->ctiles, h->ctile_elems));
+  TRY(dalloc(h, &h->cut, h->ctile_elems));
+  cudaEvent_t ev_fork = nullptr, ev_coarse = nullptr;
+  SFCDD_CUDA_OK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  SFCDD_CUDA_OK(cudaEventCreateWithFlags(&ev_coarse, cudaEventDisableTiming));
+  SFCDD_CUDA_OK(cudaEventRecord(ev_fork, s));
+  SFCDD_CUDA_OK(cudaStreamWaitEvent(h->side_stream, ev_fork, 0));
+  cudaEventDestroy(ev_fork);
+  Prof pf2(h, h->side_stream);
+  if (h->variant != SFCDD_ONE_LEVEL) {
+    cudaStream_t s2 = h->side_stream;
+    // the coarse matrix is a one-matrix tile set with base 0
+    const TileSetDev cts = coarse_view(h);
+    pf2.run(SFCDD_K_COARSE_ASSEMBLE, [&] {
+      launch_assemble_coarse(g, pd, h->curve_code, h->invpad, cts, h->stored[P], h->ctiles, s2);
+    });
+    CoarseHook ch(pf2);
+    factor_tiles(cts, 0, 1, h->nt0, h->col_max_coarse.data(), h->ctiles, Store::F64, h->err, s2,
+                 &ch);
+    pf2.run(SFCDD_K_COARSE_FACTOR, [&] {
+      unitize_tiles(cts, 0, 1, h->max_ctiles, h->ctiles, h->cut, Store::F64, s2);
+    });
+  }
+  SFCDD_CUDA_OK(cudaEventRecord(ev_coarse, h->side_stream));
+
   // Algorithm 1, steps 6-7 and Sec. 3.1: local matrices and their factors
   const Store compute_st = h->st == Store::BF16 ? Store::F32 : h->st;
   const size_t esz = compute_st == Store::F64 ? 8 : 4;
@@ -714,35 +874,36 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     factor_tiles(h->ts, 0, P, h->max_nt, h->col_max_local.data(), work_tiles, compute_st, h->err,
                  s, &pf);
   }
+  // substitution form: Lh in place, Lh^T and E_K into a second tile array
+  void* work_ut = nullptr;
+  TRY(dalloc(h, (unsigned char**)&work_ut, h->ltile_elems * esz));
+  if (h->variant != SFCDD_COARSE_ONLY)
+    pf.run(SFCDD_K_TRSM, [&] {
+      unitize_tiles(h->ts, 0, P, h->max_ltiles, work_tiles, work_ut, compute_st, s);
+    });
   if (h->st == Store::BF16) {
     TRY(dalloc(h, (__nv_bfloat16**)&h->ltiles, h->ltile_elems));
+    TRY(dalloc(h, (__nv_bfloat16**)&h->lut, h->ltile_elems));
     pf.run(SFCDD_K_VECTOR, [&] {
       launch_convert_f32_bf16((const float*)work_tiles, (__nv_bfloat16*)h->ltiles, h->ltile_elems, s);
+      launch_convert_f32_bf16((const float*)work_ut, (__nv_bfloat16*)h->lut, h->ltile_elems, s);
     });
     SFCDD_CUDA_OK(cudaStreamSynchronize(s));
     dfree(h, work_tiles);
+    dfree(h, work_ut);
   } else {
     h->ltiles = work_tiles;
+    h->lut = work_ut;
   }
-  // Algorithm 1, steps 9-10: coarse matrix and its FP64 factor
-  TRY(dalloc(h, &h->ctiles, h->ctile_elems));
-  if (h->variant != SFCDD_ONE_LEVEL) {
-    // the coarse matrix is a one-matrix tile set with base 0
-    const TileSetDev cts = coarse_view(h);
-    pf.run(SFCDD_K_COARSE_ASSEMBLE, [&] {
-      launch_assemble_coarse(g, pd, h->curve_code, h->invpad, cts, h->stored[P], h->ctiles, s);
-    });
-    CoarseHook ch(pf);
-    factor_tiles(cts, 0, 1, h->nt0, h->col_max_coarse.data(), h->ctiles, Store::F64, h->err, s,
-                 &ch);
-  }
+  SFCDD_CUDA_OK(cudaStreamWaitEvent(s, ev_coarse, 0));
+  cudaEventDestroy(ev_coarse);
   SFCDD_CUDA_OK(cudaGetLastError());
 
   // per-matrix right-hand-side descriptors (one problem: scalars index 0)
   {
     std::vector<MatDesc> md(P + 1);
-    for (int m = 0; m < P; ++m) md[m] = {0, h->N, h->h_start[m], 0, 0};
-    md[P] = {0, h->N0, 0, 1, 0};
+    for (int m = 0; m < P; ++m) md[m] = {0, h->N, h->h_start[m], 0, 0, h->nsub_local};
+    md[P] = {0, h->N0, 0, 1, 0, h->nsub_coarse};
     TRY(dalloc(h, &h->d_md, P + 1));
     SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_md, md.data(), (P + 1) * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
     SFCDD_CUDA_OK(cudaStreamSynchronize(s));
@@ -755,7 +916,9 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     if (h->variant == SFCDD_COARSE_ONLY)
       for (int m = 0; m < P; ++m) include[m] = 0;
     if (h->variant == SFCDD_ONE_LEVEL) include[P] = 0;
-    build_worklists(h->h_nt, include, wf, wb);
+    std::vector<int> nsub(P + 1, h->nsub_local);
+    nsub[P] = h->nsub_coarse;
+    build_worklists(h->h_nt, include, nsub, wf, wb);
   }
   h->nwork = (int)wf.size();
   TRY(dalloc(h, &h->work_f, h->nwork));
@@ -768,6 +931,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   SFCDD_CUDA_OK(cudaMemsetAsync(h->ticket_b, 0, sizeof(unsigned long long), s));
   TRY(dalloc(h, &h->ybuf, h->vtotal));
   TRY(dalloc(h, &h->dbuf, h->vtotal));
+  TRY(dalloc(h, &h->zcbuf, h->vtotal));
   launch_fill_pending(h->ybuf, h->vtotal, s);
   launch_fill_pending(h->dbuf, h->vtotal, s);
 
@@ -793,6 +957,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   SFCDD_CUDA_OK(cudaEventRecord(e1, s));
   SFCDD_CUDA_OK(cudaEventSynchronize(e1));
   pf.collect();
+  pf2.collect();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   h->setup_ms = ms;
@@ -813,6 +978,7 @@ void destroy_impl(sfcdd_handle* h) {
     if (p) cudaFree(p);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
   delete h;
 }
 
@@ -902,6 +1068,8 @@ void sfcdd_default_options(sfcdd_options* opt) {
   opt->stream = nullptr;
   opt->profile = 0;
   opt->local_order = 0;
+  opt->slabs_local = 0;
+  opt->slabs_coarse = 0;
 }
 
 int sfcdd_setup_ex(const int* levels, int d, int P, double overlap, const sfcdd_options* opt,
@@ -1029,8 +1197,9 @@ int sfcdd_get_info(const sfcdd_handle* h, sfcdd_info* info) {
   info->weighting = h->weighting;
   info->flexible = h->flexible;
   const long long esz = h->precision == SFCDD_FP64 ? 8 : (h->precision == SFCDD_FP32 ? 4 : 2);
-  info->factor_bytes = h->variant == SFCDD_COARSE_ONLY ? 0 : h->ltile_elems * esz;
-  info->coarse_bytes = h->variant == SFCDD_ONE_LEVEL ? 0 : h->ctile_elems * 8;
+  // both substitution copies (Lh and Lh^T / E_K)
+  info->factor_bytes = h->variant == SFCDD_COARSE_ONLY ? 0 : 2 * h->ltile_elems * esz;
+  info->coarse_bytes = h->variant == SFCDD_ONE_LEVEL ? 0 : 2 * h->ctile_elems * 8;
   info->setup_ms = h->setup_ms;
   return SFCDD_OK;
 }
@@ -1074,7 +1243,7 @@ int sfcdd_get_coarse_matrix(const sfcdd_handle* hc, double* A0_dev) {
   SFCDD_CUDA_OK(cudaMalloc(&t, std::max<long long>(h->ctile_elems, 1) * sizeof(double)));
   const TileSetDev cts = coarse_view(h);
   launch_assemble_coarse(h->g, h->pd, h->curve_code, h->invpad, cts, h->stored[h->P], t, s);
-  launch_unpack_dense(cts, 0, t, A0_dev, s);
+  launch_unpack_dense(cts, 0, t, A0_dev, h->pd.crow, s);
   h->launches[SFCDD_K_COARSE_ASSEMBLE] += 1;
   h->launches[SFCDD_K_VECTOR] += 1;
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
@@ -1094,7 +1263,7 @@ int sfcdd_get_local_matrix(const sfcdd_handle* hc, int i, double* Ai_dev) {
   pd.start = h->d_start + i;
   launch_assemble_local(h->g, pd, h->curve_code, h->invpad, lts, 0, 1, h->stored[i], t,
                         Store::F64, s);
-  launch_unpack_dense(lts, 0, t, Ai_dev, s);
+  launch_unpack_dense(lts, 0, t, Ai_dev, nullptr, s);
   h->launches[SFCDD_K_ASSEMBLE] += 1;
   h->launches[SFCDD_K_VECTOR] += 1;
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
@@ -1124,12 +1293,17 @@ int sfcdd_get_kernel_stats(sfcdd_handle* h, double* ms_total, long long* launche
 double sfcdd_kernel_work(const sfcdd_handle* h, int kc) {
   if (!h) return 0.0;
   const double esz = h->precision == SFCDD_FP64 ? 8 : (h->precision == SFCDD_FP32 ? 4 : 2);
-  const double lb = h->variant == SFCDD_COARSE_ONLY ? 0.0 : (double)h->ltile_elems * esz;
-  const double cb = h->variant == SFCDD_ONE_LEVEL ? 0.0 : (double)h->ctile_elems * 8.0;
+  const bool loc = h->variant != SFCDD_COARSE_ONLY, crs = h->variant != SFCDD_ONE_LEVEL;
+  // forward: the off-diagonal Lh tiles; backward: the Lh^T tiles and the E_K blocks
+  const double lall = loc ? (double)h->ltile_elems * esz : 0.0;
+  const double call = crs ? (double)h->ctile_elems * 8.0 : 0.0;
+  const double ldia = loc ? (double)h->ldiag_elems * esz : 0.0;
+  const double cdia = crs ? (double)h->cdiag_elems * 8.0 : 0.0;
   switch (kc) {
     case SFCDD_K_TRSV_FWD:
+      return (lall - ldia) + (call - cdia);
     case SFCDD_K_TRSV_BWD:
-      return lb + cb;
+      return lall + call;
     case SFCDD_K_STENCIL:
       return 16.0 * (double)h->N;
     case SFCDD_K_POTRF:

@@ -40,15 +40,17 @@ struct sfcdd_batch {
   double* d_omega = nullptr;
   TileSetDev ts{};
   MatDesc* d_md = nullptr;
-  void* ltiles = nullptr;
+  void* ltiles = nullptr;  // Lh tiles (unit diagonal blocks implied)
+  void* lut = nullptr;     // Lh^T tiles, E_K on the diagonal
   double* ctiles = nullptr;
+  double* cut = nullptr;
   SkylineHost sky;
   std::vector<int> h_nt, h_vbase;
   int max_nt_local = 0, max_nt_coarse = 0;
   TrsvWork *work_f = nullptr, *work_b = nullptr;
   int nwork = 0;
   unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
-  double *ybuf = nullptr, *dbuf = nullptr;
+  double *ybuf = nullptr, *dbuf = nullptr, *zcbuf = nullptr;
   double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr,
          *g0 = nullptr;
   PcgScalars* sc = nullptr;
@@ -424,7 +426,10 @@ TrsvArgs batch_trsv_args(sfcdd_batch* b, bool fwd) {
   a.ts = b->ts;
   a.md = b->d_md;
   a.ltiles = b->ltiles;
+  a.lut = b->lut;
   a.ctiles = b->ctiles;
+  a.cut = b->cut;
+  a.zc = b->zcbuf;
   a.rhs = b->r;
   a.g0 = b->g0;
   a.y = b->ybuf;
@@ -716,15 +721,23 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   } nohook;
   factor_tiles(b->ts, 0, b->nlocal, b->max_nt_local, b->sky.col_max_local.data(), work_tiles, cst,
                b->err, s, &nohook);
+  // substitution form: Lh in place, Lh^T and E_K into a second tile array
+  void* work_ut = nullptr;
+  BTRY(balloc(b, (unsigned char**)&work_ut, b->sky.ltiles * TILE2 * esz));
+  unitize_tiles(b->ts, 0, b->nlocal, b->sky.max_ltiles, work_tiles, work_ut, cst, s);
   if (b->st == Store::BF16) {
     BTRY(balloc(b, (__nv_bfloat16**)&b->ltiles, b->sky.ltiles * TILE2));
+    BTRY(balloc(b, (__nv_bfloat16**)&b->lut, b->sky.ltiles * TILE2));
     launch_convert_f32_bf16((const float*)work_tiles, (__nv_bfloat16*)b->ltiles, b->sky.ltiles * TILE2, s);
+    launch_convert_f32_bf16((const float*)work_ut, (__nv_bfloat16*)b->lut, b->sky.ltiles * TILE2, s);
     SFCDD_CUDA_OK(cudaStreamSynchronize(s));
     cudaFree(work_tiles);
+    cudaFree(work_ut);
     for (auto& a : b->allocs)
-      if (a == work_tiles) a = nullptr;
+      if (a == work_tiles || a == work_ut) a = nullptr;
   } else {
     b->ltiles = work_tiles;
+    b->lut = work_ut;
   }
   BTRY(balloc(b, &b->ctiles, b->sky.ctiles * TILE2));
   {
@@ -735,6 +748,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   }
   factor_tiles(b->ts, b->nlocal, nsub, b->max_nt_coarse, b->sky.col_max_coarse.data(), b->ctiles,
                Store::F64, b->err, s, &nohook);
+  BTRY(balloc(b, &b->cut, b->sky.ctiles * TILE2));
+  unitize_tiles(b->ts, b->nlocal, nsub, b->sky.max_ctiles, b->ctiles, b->cut, Store::F64, s);
   SFCDD_CUDA_OK(cudaGetLastError());
   b->factor_bytes = b->sky.ltiles * TILE2 * (b->precision == 0 ? 8 : b->precision == 1 ? 4 : 2) +
                     b->sky.ctiles * TILE2 * 8;
@@ -744,13 +759,13 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   for (int si = 0; si < nsub; ++si) {
     const SubDesc& sd = b->hsub[si];
     for (int i = 0; i < P; ++i)
-      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)si * P + i], 0, si};
-    md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si};
+      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)si * P + i], 0, si, 1};
+    md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si, 1};
   }
   BTRY(balloc(b, &b->d_md, b->nmat));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_md, md.data(), b->nmat * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
   std::vector<TrsvWork> wf, wb;
-  build_worklists(b->h_nt, std::vector<char>(b->nmat, 1), wf, wb);
+  build_worklists(b->h_nt, std::vector<char>(b->nmat, 1), std::vector<int>(b->nmat, 1), wf, wb);
   b->nwork = (int)wf.size();
   BTRY(balloc(b, &b->work_f, b->nwork));
   BTRY(balloc(b, &b->work_b, b->nwork));
@@ -762,6 +777,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_b, 0, sizeof(unsigned long long), s));
   BTRY(balloc(b, &b->ybuf, vb));
   BTRY(balloc(b, &b->dbuf, vb));
+  BTRY(balloc(b, &b->zcbuf, vb));
   launch_fill_pending(b->ybuf, vb, s);
   launch_fill_pending(b->dbuf, vb, s);
 

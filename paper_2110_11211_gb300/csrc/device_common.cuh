@@ -79,18 +79,19 @@ __device__ __forceinline__ int envelope_row(const GridDev& g, const unsigned* __
   return first;
 }
 
-// Smallest coarse block adjacent to the block of curve position p.
+// Smallest coarse row adjacent to the row of the block of curve position p
+// (returned in a).
 __device__ __forceinline__ int envelope_coarse_point(const GridDev& g, const PartDev& pd,
                                                      const unsigned* __restrict__ code,
                                                      const int* __restrict__ invpad, int p,
                                                      int& a) {
-  a = coarse_block_of(pd, p);
+  a = coarse_row(pd, coarse_block_of(pd, p));
   const unsigned c = code[p];
   int first = a;
   for (int j = 0; j < g.d; ++j)
     for (int s = 0; s < 2; ++s) {
       const int q = neighbour(g, invpad, c, j, s);
-      if (q >= 0) first = min(first, coarse_block_of(pd, q));
+      if (q >= 0) first = min(first, coarse_row(pd, coarse_block_of(pd, q)));
     }
   return first;
 }
@@ -121,9 +122,10 @@ __device__ __forceinline__ void assemble_local_tile(const GridDev& g,
     }
 }
 
-// Tile (R, C) of the coarse matrix A_0 = R_0 A R_0^T (eq. csm) into acc (TILE^2
-// doubles) using cnt (TILE^2 ints) for the integer edge counts of each axis;
-// 4 threads per coarse row walk the points of the row's block.  Needs FB >= 256.
+// Tile (R, C) of the coarse matrix A_0 = R_0 A R_0^T (eq. csm), rows and
+// columns in the coarse factor's numbering, into acc (TILE^2 doubles) using cnt
+// (TILE^2 ints) for the integer edge counts of each axis; 4 threads per coarse
+// row walk the points of the row's block.  Needs FB >= 256.
 __device__ __forceinline__ void assemble_coarse_tile(const GridDev& g, const PartDev& pd, int N0,
                                                      const unsigned* __restrict__ code,
                                                      const int* __restrict__ invpad, int R, int C,
@@ -132,23 +134,17 @@ __device__ __forceinline__ void assemble_coarse_tile(const GridDev& g, const Par
   const int tr = threadIdx.x >> 2, sub = threadIdx.x & 3;
   const int arow = R * TILE + tr;
   int bstart = 0, bsize = 0;
-  if (threadIdx.x < 4 * TILE && arow < N0) {
-    const int t = arow / pd.q, mm = arow % pd.q;
-    const int n = tilde_size(pd, t);
-    const int bf = n / pd.q, br = n % pd.q;
-    bstart = tilde_off(pd, t) + (mm < br ? mm * (bf + 1) : br * (bf + 1) + (mm - br) * bf);
-    bsize = mm < br ? bf + 1 : bf;
-  }
+  if (threadIdx.x < 4 * TILE && arow < N0)
+    coarse_block_range(pd, coarse_block_at(pd, arow), bstart, bsize);
   for (int k = threadIdx.x; k < TILE2; k += nthr) {
     const int r = k / TILE, c = k % TILE;
     const int ar = R * TILE + r, bc = C * TILE + c;
     double v = 0.0;
     if (ar == bc) {
       if (ar < N0) {
-        const int t = ar / pd.q, mm = ar % pd.q;
-        const int n = tilde_size(pd, t);
-        const int bf = n / pd.q, br = n % pd.q;
-        v = (double)(mm < br ? bf + 1 : bf) * g.diag;
+        int bs, bn;
+        coarse_block_range(pd, coarse_block_at(pd, ar), bs, bn);
+        v = (double)bn * g.diag;
       } else {
         v = 1.0;  // padding: identity
       }
@@ -164,7 +160,7 @@ __device__ __forceinline__ void assemble_coarse_tile(const GridDev& g, const Par
         for (int s = 0; s < 2; ++s) {
           const int q = neighbour(g, invpad, c, j, s);
           if (q < 0) continue;
-          const int bcol = coarse_block_of(pd, q);
+          const int bcol = coarse_row(pd, coarse_block_of(pd, q));
           if (bcol >= C * TILE && bcol < (C + 1) * TILE && bcol <= arow)
             atomicAdd(&cnt[tr * TILE + (bcol - C * TILE)], 1);
         }
@@ -196,7 +192,7 @@ __device__ __forceinline__ double stencil_point(const GridDev& g, const unsigned
 }
 
 // z_p = d_0[block(p)] + sum_i omega_i d_i[row_i(p)] (eq. addSW), reading the
-// coarse result at dvec[coarse_base + block] and subdomain i's result at
+// coarse result at dvec[coarse_base + coarse_row(block)] and subdomain i's result at
 // dvec[lvbase(i) + row], row = linv[lvbase(i) + offset] (linv null: the offset);
 // mode 0 two-level, 1 one level, 2 coarse only.
 template <class LocalBase>
@@ -205,7 +201,7 @@ __device__ __forceinline__ double prolong_point(const PartDev& pd, int mode,
                                                 LocalBase lvbase, const int* __restrict__ linv,
                                                 int p) {
   double v = 0.0;
-  if (mode != 1) v = __ldg(&dvec[coarse_base + coarse_block_of(pd, p)]);
+  if (mode != 1) v = __ldg(&dvec[coarse_base + coarse_row(pd, coarse_block_of(pd, p))]);
   if (mode != 2) {
     const int ncand = min(2 * pd.g + 3, pd.P);
     const int t = tilde_of(pd, p);

@@ -65,7 +65,7 @@ void launch_envelope_local(const GridDev& g, const PartDev& pd, const unsigned* 
   k_envelope_local<<<grid, 256, 0, s>>>(g, pd, code, invpad, ts, tfirst);
 }
 
-// Coarse row a: smallest coarse block adjacent to block a.
+// Coarse row a: smallest coarse row adjacent to row a (factor numbering).
 __global__ void k_envelope_coarse(GridDev g, PartDev pd, const unsigned* __restrict__ code,
                                   const int* __restrict__ invpad, int fbc, int* tfirst) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += gridDim.x * blockDim.x) {
@@ -343,6 +343,104 @@ void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const in
     factor_tiles_t<float>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, err, s, hook);
 }
 
+// A 64 x 64 row-major tile into a padded shared array, rows kept as rows.
+template <class T>
+__device__ __forceinline__ void load_plain(T (*dst)[TILE + 4], const T* __restrict__ src) {
+  for (int e = threadIdx.x; e < TILE2; e += FB) dst[e / TILE][e % TILE] = src[e];
+}
+
+// acc[i][j] = sum_{s >= s0} Xt[s][r0 + i] Yt[s][c0 + j]
+template <class T>
+__device__ __forceinline__ void mma_4x4_from(T (&acc)[4][4], T (*Xt)[TILE + 4],
+                                             T (*Yt)[TILE + 4], int r0, int c0, int s0) {
+#pragma unroll 4
+  for (int s = s0; s < TILE; ++s) {
+    T xv[4], yv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      xv[i] = Xt[s][r0 + i];
+      yv[i] = Yt[s][c0 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[i][jj] += xv[i] * yv[jj];
+  }
+}
+
+// One stored tile per CTA.  With X = L_KK^{-1} (lower triangular, held in the
+// diagonal slot): off-diagonal tile (I, K) -> Lh = L_IK X in place and Lh^T
+// into ut; diagonal tile K -> E_K = X^T X into ut.  Both products only involve
+// k >= column, so each warp starts its k loop at its first column (threads of
+// a warp share a column block: c0 = 4 (tid / 16)).  grid = (max stored, nmat)
+template <class T>
+__global__ void __launch_bounds__(FB) k_unitize(TileSetDev ts, int mat0, T* __restrict__ tiles,
+                                                T* __restrict__ ut) {
+  extern __shared__ __align__(16) unsigned char dsm_unit[];
+  T (*Xt)[TILE + 4] = reinterpret_cast<T (*)[TILE + 4]>(dsm_unit);
+  T (*Yt)[TILE + 4] = Xt + TILE;
+  const int m = mat0 + blockIdx.y;
+  const int nt = ts.nt[m];
+  const int fb = ts.vbase[m] / TILE;
+  if ((int)blockIdx.x >= stored_tiles(ts, fb, nt)) return;
+  int I, K;
+  skyline_decode(ts, fb, nt, blockIdx.x, I, K);
+  const long long tb = ts.tbase[m];
+  const T* xinv = tiles + tile_at(ts, tb, fb, K, K);
+  T* tile = tiles + tile_at(ts, tb, fb, I, K);
+  T* tout = ut + tile_at(ts, tb, fb, I, K);
+  const int r0 = (threadIdx.x % 16) * 4, c0 = (threadIdx.x / 16) * 4;
+  const int s0 = (threadIdx.x / 32) * 8;  // smallest column of the warp
+  if (I == K) {
+    load_plain<T>(Xt, xinv);  // Xt[s][a] = X[s][a]: E = X^T X
+  } else {
+    load_transposed<T>(Xt, tile);  // Xt[s][a] = L_IK[a][s]
+    load_plain<T>(Yt, xinv);       // Yt[s][b] = X[s][b]: Lh = L_IK X
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  mma_4x4_from<T>(acc, Xt, I == K ? Xt : Yt, r0, c0, s0);
+  __syncthreads();
+  // stage the result (rows in Xt) and its transpose (rows in Yt), then copy out
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      Xt[r0 + a][c0 + b] = acc[a][b];
+      Yt[c0 + b][r0 + a] = acc[a][b];
+    }
+  __syncthreads();
+  if (I == K) {
+    for (int e = threadIdx.x; e < TILE2; e += FB) tout[e] = Xt[e / TILE][e % TILE];
+  } else {
+    for (int e = threadIdx.x; e < TILE2; e += FB) {
+      tile[e] = Xt[e / TILE][e % TILE];
+      tout[e] = Yt[e / TILE][e % TILE];
+    }
+  }
+}
+
+template <class T>
+static void unitize_t(const TileSetDev& ts, int mat0, int nmat, int max_stored, T* tiles, T* ut,
+                      cudaStream_t s) {
+  if (nmat <= 0 || max_stored <= 0) return;
+  const int sm = 2 * TILE * (TILE + 4) * (int)sizeof(T);
+  cudaFuncSetAttribute(k_unitize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  k_unitize<T><<<dim3(max_stored, nmat), FB, sm, s>>>(ts, mat0, tiles, ut);
+}
+
+void unitize_tiles(const TileSetDev& ts, int mat0, int nmat, int max_stored, void* tiles, void* ut,
+                   Store st, cudaStream_t s) {
+  if (st == Store::F64)
+    unitize_t<double>(ts, mat0, nmat, max_stored, (double*)tiles, (double*)ut, s);
+  else
+    unitize_t<float>(ts, mat0, nmat, max_stored, (float*)tiles, (float*)ut, s);
+}
+
 __global__ void k_convert_f32_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
                                    long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -359,10 +457,10 @@ void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, c
 // curve order (mapped through the local numbering); entries outside the
 // envelope are zero.
 __global__ void k_unpack_dense(TileSetDev ts, int m, const double* __restrict__ tiles,
-                               double* __restrict__ dense) {
+                               double* __restrict__ dense, const int* __restrict__ rowmap) {
   const int n = ts.n[m];
   const int fb = ts.vbase[m] / TILE;
-  const int* linv = ts.linv ? ts.linv + ts.vbase[m] : nullptr;
+  const int* linv = rowmap ? rowmap : (ts.linv ? ts.linv + ts.vbase[m] : nullptr);
   const long long tot = (long long)n * n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += stride) {
@@ -430,8 +528,70 @@ void local_order_lex(const TileSetDev& ts, int nmat, int max_n, const int* mstar
 }
 
 void launch_unpack_dense(const TileSetDev& ts, int m, const double* tiles, double* dense,
-                         cudaStream_t s) {
-  k_unpack_dense<<<152 * 8, 256, 0, s>>>(ts, m, tiles, dense);
+                         const int* rowmap, cudaStream_t s) {
+  k_unpack_dense<<<152 * 8, 256, 0, s>>>(ts, m, tiles, dense, rowmap);
+}
+
+// ---------------------------------------------------------------------------
+// Coarse-block adjacency (input of the coarse numbering): one warp per coarse
+// block b walks the block's points and their 2d neighbours, 32 candidates at a
+// time.  A candidate is kept if it is another block, not yet in b's list and
+// the lowest lane holding that block in its chunk (warp match), so each list
+// ends up with every adjacent block exactly once, in order of first sight.
+constexpr int ADJ_WARPS = 4;
+
+__global__ void __launch_bounds__(ADJ_WARPS * 32)
+    k_coarse_adjacency(GridDev g, PartDev pd, const unsigned* __restrict__ code,
+                       const int* __restrict__ invpad, int maxdeg, int* __restrict__ adj,
+                       int* __restrict__ deg) {
+  extern __shared__ int sm_adj[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = blockIdx.x * ADJ_WARPS + w;
+  const int N0 = pd.q * pd.P;
+  if (b >= N0) return;  // whole warp
+  int* list = sm_adj + w * maxdeg;
+  int bstart, bsize;
+  coarse_block_range(pd, b, bstart, bsize);
+  const int nd = 2 * g.d;
+  const int ncand = bsize * nd;
+  int cnt = 0;
+  bool overflow = false;
+  for (int c0 = 0; c0 < ncand; c0 += 32) {
+    const int k = c0 + lane;
+    int nb = -1;
+    if (k < ncand) {
+      const int u = k / nd, dir = k % nd;
+      const int q = neighbour(g, invpad, code[bstart + u], dir >> 1, dir & 1);
+      if (q >= 0) nb = coarse_block_of(pd, q);
+    }
+    bool keep = nb >= 0 && nb != b;
+    const int listed = cnt < maxdeg ? cnt : maxdeg;
+    for (int i = 0; keep && i < listed; ++i)
+      if (list[i] == nb) keep = false;
+    // lanes with equal candidates: only the lowest keeps it (others get distinct keys)
+    const unsigned same = __match_any_sync(0xffffffffu, keep ? nb : -2 - lane);
+    if (keep && (__ffs(same) - 1) != lane) keep = false;
+    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+    const int pos = cnt + __popc(kb & ((1u << lane) - 1u));
+    if (keep) {
+      if (pos < maxdeg) list[pos] = nb;
+      else overflow = true;
+    }
+    cnt += __popc(kb);
+    __syncwarp();
+  }
+  overflow = __any_sync(0xffffffffu, overflow) || cnt > maxdeg;
+  for (int i = lane; i < cnt && !overflow; i += 32) adj[(long long)b * maxdeg + i] = list[i];
+  if (lane == 0) deg[b] = overflow ? -1 : cnt;
+}
+
+void launch_coarse_adjacency(const GridDev& g, const PartDev& pd, const unsigned* code,
+                             const int* invpad, int maxdeg, int* adj, int* deg, cudaStream_t s) {
+  const int N0 = pd.q * pd.P;
+  const int smem = ADJ_WARPS * maxdeg * (int)sizeof(int);
+  cudaFuncSetAttribute(k_coarse_adjacency, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_coarse_adjacency<<<(N0 + ADJ_WARPS - 1) / ADJ_WARPS, ADJ_WARPS * 32, smem, s>>>(
+      g, pd, code, invpad, maxdeg, adj, deg);
 }
 
 }  // namespace sfcdd

@@ -12,9 +12,14 @@
 //    nonzero of A_i in any row of tile row I.  The factor's fill stays inside
 //    each row's envelope, so every tile outside is an exact zero and is neither
 //    stored nor touched.  Tile (I, K) sits at tbase[i] + (rowoff[I] + K - kmin[I])
-//    TILE^2, row-major inside a tile; the diagonal slot holds the INVERSE of the
-//    diagonal block of the Cholesky factor.  Storage fp64, fp32 or bf16.  The
-//    coarse factor has the same layout in FP64 and is matrix index P.
+//    TILE^2, row-major inside a tile.  After the setup the factor is kept in its
+//    substitution form L = Lh blockdiag(L_KK): the first array holds
+//    Lh_IK = L_IK L_KK^{-1} off the diagonal (its diagonal slot keeps L_KK^{-1},
+//    which the solves do not read), a second array of the same layout holds
+//    Lh_IK^T in slot (I, K) and E_K = L_KK^{-T} L_KK^{-1} in the diagonal slot.
+//    Storage fp64, fp32 or bf16.  The coarse factor has the same layout in FP64
+//    and is matrix index P; its rows follow a reverse Cuthill-McKee numbering of
+//    the coarse blocks (PartDev::crow / cblock).
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -49,6 +54,10 @@ struct PartDev {
   const int* start;          // P: first curve position of Omega_i
   const int* len;            // P: N_i
   const double* omega;       // P: omega_i (or 1)
+  // Numbering of the coarse unknowns in the coarse factor: coarse block b
+  // (eq. restr order) is row crow[b], row r holds block cblock[r]; null: b = r.
+  const int* crow;
+  const int* cblock;
 };
 
 // Tilde subdomain of a curve position (eq. sloc, closed form).
@@ -72,6 +81,21 @@ __host__ __device__ inline int coarse_block_of(const PartDev& pd, int p) {
   const int big = br * (bf + 1);
   const int m = o < big ? o / (bf + 1) : br + (o - big) / bf;
   return t * pd.q + m;
+}
+// First curve position and size of coarse block b.
+__host__ __device__ inline void coarse_block_range(const PartDev& pd, int b, int& start,
+                                                   int& size) {
+  const int t = b / pd.q, m = b % pd.q;
+  const int n = tilde_size(pd, t);
+  const int bf = n / pd.q, br = n % pd.q;
+  start = tilde_off(pd, t) + (m < br ? m * (bf + 1) : br * (bf + 1) + (m - br) * bf);
+  size = m < br ? bf + 1 : bf;
+}
+__device__ __forceinline__ int coarse_row(const PartDev& pd, int b) {
+  return pd.crow ? __ldg(&pd.crow[b]) : b;
+}
+__device__ __forceinline__ int coarse_block_at(const PartDev& pd, int r) {
+  return pd.cblock ? __ldg(&pd.cblock[r]) : r;
 }
 
 // Hilbert key (Sec. 3.2, Skilling's transform) of the point with lexicographic
@@ -200,7 +224,8 @@ int paper_q(long long N, int P);
 // predecessors in its own matrix.
 struct TrsvWork;
 void build_worklists(const std::vector<int>& nt, const std::vector<char>& include,
-                     std::vector<TrsvWork>& wf, std::vector<TrsvWork>& wb);
+                     const std::vector<int>& nsub, std::vector<TrsvWork>& wf,
+                     std::vector<TrsvWork>& wb);
 // Tile-skyline bookkeeping of nmat matrices from the envelope of every tile row
 // (tfirst = first nonzero column of the tile row): per-row kmin/rowoff, stored
 // tile counts, element offsets (local matrices in one buffer, coarse ones in
@@ -281,6 +306,13 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 // I > K with kmin[I] <= K over the matrices (sizes the step-K launches).
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                   void* tiles, Store st, ErrWord* err, cudaStream_t s, LaunchHook* hook);
+// Substitution form of the factors of matrices [mat0, mat0+nmat) (after
+// factor_tiles, same precision): every stored off-diagonal tile L_IK becomes
+// Lh_IK = L_IK L_KK^{-1} in place, ut receives Lh_IK^T in the same slot and
+// E_K = L_KK^{-T} L_KK^{-1} in the diagonal slot (ut has the layout of tiles).
+// max_stored = largest stored tile count of one matrix (sizes the launch).
+void unitize_tiles(const TileSetDev& ts, int mat0, int nmat, int max_stored, void* tiles, void* ut,
+                   Store st, cudaStream_t s);
 void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, cudaStream_t s);
 // Lexicographic numbering inside each local matrix: matrices [0, nmat) of ts,
 // matrix m covers the cyclic range (mstart[m], ts.n[m]) of a problem with
@@ -290,13 +322,19 @@ void local_order_lex(const TileSetDev& ts, int nmat, int max_n, const int* mstar
                      const int* mcbase, const int* lbase, long long total, const unsigned* code,
                      unsigned long long* keys, unsigned* vals, void* temp, int* lperm, int* linv,
                      cudaStream_t s);
+// rowmap (null: ts.linv of the matrix) maps an output row/column to its row in the tiles.
 void launch_unpack_dense(const TileSetDev& ts, int m, const double* tiles, double* dense,
-                         cudaStream_t s);
+                         const int* rowmap, cudaStream_t s);
+// Distinct coarse blocks adjacent to each coarse block (in eq. restr order):
+// adj[b * maxdeg + k], k < deg[b]; deg[b] = -1 if more than maxdeg.
+void launch_coarse_adjacency(const GridDev& g, const PartDev& pd, const unsigned* code,
+                             const int* invpad, int maxdeg, int* adj, int* deg, cudaStream_t s);
 
 // trsv.cu
 struct TrsvWork {
   int mat;
   int row;
+  int slab;  // rows [64 / nsub * slab, 64 / nsub * (slab + 1)) of the tile row
 };
 // Where the right-hand side of a matrix comes from and which solve it belongs to:
 // a local matrix reads rhs[rhs_base + (start + row) mod rhs_len] (a cyclic slice of
@@ -307,6 +345,7 @@ struct MatDesc {
   int start;
   int coarse;   // 1: FP64 coarse factor tiles, 0: local factor tiles
   int sub;      // index of the PCG scalars (problem) the matrix belongs to
+  int nsub;     // slabs per tile row in the substitutions (1, 2 local; 1, 4 coarse)
 };
 // Bit pattern (a signalling NaN) marking a substitution result slot as not yet
 // written in the current launch.
@@ -315,12 +354,16 @@ void launch_fill_pending(double* p, long long n, cudaStream_t s);
 struct TrsvArgs {
   TileSetDev ts;
   const MatDesc* md;           // per matrix
-  const void* ltiles;          // local factor tiles
-  const double* ctiles;        // coarse factor tiles, may be null if no coarse
+  const void* ltiles;          // local Lh tiles (unit diagonal blocks implied)
+  const void* lut;             // local Lh^T tiles, diagonal slots hold E_K
+  const double* ctiles;        // coarse Lh tiles, may be null if no coarse
+  const double* cut;           // coarse Lh^T tiles with E_K on the diagonal
   const double* rhs;           // curve-order vector the local right-hand sides are sliced from
-  const double* g0;            // coarse right-hand sides
+  const double* g0;            // coarse right-hand sides (coarse block order)
+  const int* cblock;           // coarse block of each coarse factor row (null: identity)
   double* y;                   // forward results, per matrix vbase
   double* dout;                // backward results, per matrix vbase
+  double* zc;                  // plain copy of the forward results (read by the backward)
   const TrsvWork* work;        // work list, dependency-safe order
   int nwork;
   unsigned long long* ticket;  // monotone ticket counter

@@ -3,36 +3,43 @@
 // factorization is done once in the setup phase and every application of the
 // preconditioner only runs the two triangular solves, Sec. 3.1).
 //
-// Parallel layout: one CTA per (matrix, tile row).  CTAs take tickets from a
-// monotone counter and map them through a work list in which every tile row
-// comes after the rows it depends on, so a CTA only ever waits for CTAs that
-// already started (no deadlock, whatever the residency).
-// Row results are their own ready flags: before a launch the result slots hold
-// a sentinel NaN bit pattern (the forward launch resets the backward slots of
-// its rows, the backward launch resets the forward slots of its rows after
-// reading them; setup fills both), every slot is written exactly once per
-// launch with a relaxed store, and a consumer polls the slots it needs with
-// relaxed loads until none holds the sentinel (bounded spin; a timeout sets the
-// error word and the CTA still drains its copies before it returns).
-// The diagonal slot of every tile row holds the inverse of the diagonal block,
-// so both the off-diagonal updates and the diagonal solve are GEMVs.
+// Factor form.  With D = blockdiag(L_KK) over 64 x 64 tiles the setup splits
+// L = Lh D, Lh_IK = L_IK L_KK^{-1} (unit diagonal blocks), so that
+// A = Lh (D D^T) Lh^T and
+//   forward   z_I = b_I - sum_{K<I} Lh_IK z_K
+//   backward  x_K = E_K z_K - sum_{I>K} Lh_IK^T x_I,   E_K = L_KK^{-T} L_KK^{-1}.
+// The forward reads the Lh tiles (row-major); the backward reads a second copy
+// that holds Lh_IK^T in the same slot and E_K in the diagonal slot.  Both sweeps
+// therefore stream contiguous row slabs, and the chain from one tile row to the
+// next carries a single tile GEMV (no diagonal solve on it).
 //
-// Data movement: a producer warp streams the row's tiles from HBM into a
+// Parallel layout: one CTA per work item (matrix, tile row, slab), a slab
+// being R = 64 / S consecutive rows of the tile row (S = 1, 2 or 4 per matrix:
+// splitting the rows of a long chain spreads its FP64 GEMVs over S SMs).  CTAs
+// take tickets from a monotone counter and map them through a work list in
+// which every item comes after the items it depends on, so a CTA only ever
+// waits for CTAs that already started (no deadlock, whatever the residency).
+// Row results are their own ready flags: before a launch the result slots hold
+// a sentinel NaN bit pattern, every slot is written exactly once per launch
+// with a relaxed store, and a consumer polls the slots it needs with relaxed
+// loads until none holds the sentinel (bounded spin; a timeout sets the error
+// word and the CTA still drains its copies before it returns).  The forward
+// launch resets the backward slots of its slab and also writes its results to
+// a plain buffer zc; the backward launch reads z from zc and resets the forward
+// slots of its slab (nothing reads them during the backward launch).
+//
+// Data movement: a producer warp streams the item's tile slabs from HBM into a
 // shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion
-// on mbarriers), the diagonal tile first into its own buffer; eight consumer
-// warps wait on the ring's mbarriers, apply the tiles, and free the slots.
-// Everything a row needs that does not depend on other rows (its right-hand
-// side, the diagonal tile, its tile list) is fetched before the first wait, so
-// the dependency chain between rows only carries the flag, one tile and the
-// diagonal GEMV.
+// on mbarriers), the E_K slab first into its own buffer; eight consumer warps
+// wait on the ring's mbarriers, apply the slabs, and free the stages.
 #include "sfcdd_internal.cuh"
 
 namespace sfcdd {
 
-constexpr int NCONS = 256;                 // consumer threads: 8 warps x 8 rows
+constexpr int NCONS = 256;                 // consumer threads: 8 warps
 constexpr int NTHR = NCONS + 32;           // + one producer warp
-constexpr int RING_BYTES = 64 * 1024;      // tile ring (2 FP64 / 4 FP32 / 8 BF16 tiles)
-constexpr int DIAG_BYTES = TILE2 * 8;      // diagonal tile buffer (room for FP64)
+constexpr int RING_BYTES = 64 * 1024;      // slab ring
+constexpr int DIAG_BYTES = TILE2 * 8;      // E_K slab buffer (room for a full FP64 tile)
 constexpr int MAXST = 8;
 constexpr long long SPIN_LIMIT = 1ll << 22;
 constexpr long long MBAR_LIMIT = 1ll << 26;
@@ -81,9 +88,6 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void consumers_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(NCONS) : "memory");
-}
 
 __device__ __forceinline__ double2 ld_relaxed2(const double* p) {
   unsigned long long a, b;
@@ -114,7 +118,7 @@ __device__ __forceinline__ double2 wait_pair(const double* p, ErrWord* err, int 
   return v;
 }
 
-// Two consecutive elements of a shared-memory tile row as the accumulation type.
+// Two consecutive elements of a shared-memory slab row as the accumulation type.
 __device__ __forceinline__ void sm_pair(const double* p, double& a, double& b) {
   const double2 v = *reinterpret_cast<const double2*>(p);
   a = v.x;
@@ -131,32 +135,33 @@ __device__ __forceinline__ void sm_pair(const __nv_bfloat16* p, float& a, float&
   b = __uint_as_float(u & 0xffff0000u);
 }
 
-// Sum over the 32 lanes of v[i] for the warp's 8 rows in 9 shuffles (halving
-// exchanges then a 4-lane reduction).  Every lane returns the total of row
-// `row` = (lane >> 2) & 7.
-template <class A>
-__device__ __forceinline__ A reduce8(A (&v)[8], int& row) {
+// Sums v[i] over the 32 lanes for the warp's RPW rows: log2(RPW) halving
+// exchanges (each lane keeps the half its lane bit selects) followed by a
+// butterfly over the remaining lanes.  Every lane returns the total of row
+// `row`; the 32 / RPW lanes of a group hold the same row.
+template <int RPW, class A>
+__device__ __forceinline__ A reduce_rows(A (&v)[RPW], int& row) {
   const int lane = threadIdx.x & 31;
-  A w4[4], w2[2];
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  A cur[RPW];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const A keep = h16 ? v[i + 4] : v[i];
-    const A send = h16 ? v[i] : v[i + 4];
-    w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
+  for (int i = 0; i < RPW; ++i) cur[i] = v[i];
+  row = 0;
+  int dist = 16;
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const A keep = h8 ? w4[i + 2] : w4[i];
-    const A send = h8 ? w4[i] : w4[i + 2];
-    w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  for (int width = RPW; width > 1; width >>= 1) {
+    const bool hi = (lane & dist) != 0;
+#pragma unroll
+    for (int i = 0; i < width / 2; ++i) {
+      const A keep = hi ? cur[i + width / 2] : cur[i];
+      const A send = hi ? cur[i] : cur[i + width / 2];
+      cur[i] = keep + __shfl_xor_sync(0xffffffffu, send, dist);
+    }
+    row = 2 * row + (hi ? 1 : 0);
+    dist >>= 1;
   }
-  const A keep = h4 ? w2[1] : w2[0];
-  const A send = h4 ? w2[0] : w2[1];
-  A t = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  t += __shfl_xor_sync(0xffffffffu, t, 2);
-  t += __shfl_xor_sync(0xffffffffu, t, 1);
-  row = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+  A t = cur[0];
+#pragma unroll
+  for (; dist >= 1; dist >>= 1) t += __shfl_xor_sync(0xffffffffu, t, dist);
   return t;
 }
 
@@ -166,198 +171,135 @@ struct RowSmem {
   unsigned long long* full;   // [MAXST]
   unsigned long long* empty;  // [MAXST]
   unsigned long long* dbar;
-  double* xs;                 // [TILE]
-  double* red;                // [8 * TILE]
 };
 
-template <class T>
-struct Ring {
-  static constexpr unsigned TB = TILE2 * sizeof(T);
-  static constexpr int NS = (RING_BYTES / (int)TB) < MAXST ? (RING_BYTES / (int)TB) : MAXST;
-};
-
-// Producer: the diagonal tile, then the row's tiles in consumption order.
-template <class T, class TileAt>
-__device__ void produce(const RowSmem& sm, int ntile, TileAt tile_k, const T* diag_tile,
-                        ErrWord* err) {
-  constexpr unsigned TB = Ring<T>::TB;
-  constexpr int NS = Ring<T>::NS;
-  mbar_expect_tx(sm.dbar, TB);
-  bulk_copy(sm.diag, diag_tile, TB, sm.dbar);
-  for (int t = 0; t < ntile; ++t) {
-    const int s = t % NS, k = t / NS;
-    if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, err, 10);
-    mbar_expect_tx(&sm.full[s], TB);
-    bulk_copy(sm.ring + (size_t)s * TB, tile_k(t), TB, &sm.full[s]);
-  }
-}
-
-// Forward row r of matrix m: y_r = Linv_rr (g_r - sum_{c<r} L_rc y_c).
-template <class T, class A>
-__device__ void fwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, int r,
-                        const RowSmem& sm) {
-  constexpr unsigned TB = Ring<T>::TB;
-  constexpr int NS = Ring<T>::NS;
+// One work item: rows [R s, R s + R) of tile row r of matrix m.
+//   FWD: z_r = b_r - sum_{c<r} Lh_rc z_c          (tiles lt, row list)
+//   BWD: x_r = E_r z_r - sum_{c>r} Lh_cr^T x_c     (tiles ut, column list)
+template <class T, class A, int R, bool FWD>
+__device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T* __restrict__ ut,
+                           int m, int r, int slab, const RowSmem& sm) {
+  constexpr int RPW = R / 8;                        // rows per consumer warp
+  constexpr unsigned SB = R * TILE * sizeof(T);     // slab bytes
+  constexpr int NS = (RING_BYTES / (int)SB) < MAXST ? (RING_BYTES / (int)SB) : MAXST;
   const long long tb = a.ts.tbase[m];
-  const int n = a.ts.n[m];
   const int vb = a.ts.vbase[m];
   const int fb = vb / TILE;
-  const int k0 = a.ts.kmin[fb + r];
-  const T* row0 = tiles + tb + (long long)a.ts.rowoff[fb + r] * TILE2;  // tile (r, k0)
-  const int ntile = r - k0;
+  const long long soff = (long long)R * slab * TILE;  // slab offset inside a tile
+  int ntile, k0 = 0;
+  const int* cl = nullptr;
+  const T* row0 = nullptr;
+  if (FWD) {
+    k0 = a.ts.kmin[fb + r];
+    row0 = lt + tb + (long long)a.ts.rowoff[fb + r] * TILE2 + soff;  // tile (r, k0)
+    ntile = r - k0;
+  } else {
+    // rows c > r whose envelope reaches column r (ascending), consumed from the last
+    cl = a.ts.colidx + a.ts.colptr[fb + r];
+    ntile = a.ts.colptr[fb + r + 1] - a.ts.colptr[fb + r];
+  }
   if (threadIdx.x >= NCONS) {
-    if (threadIdx.x == NCONS)
-      produce<T>(sm, ntile, [=](int t) { return row0 + (long long)t * TILE2; },
-                 row0 + (long long)ntile * TILE2, a.err);
+    if (threadIdx.x == NCONS) {
+      if (!FWD) {
+        mbar_expect_tx(sm.dbar, SB);
+        bulk_copy(sm.diag, ut + tile_at(a.ts, tb, fb, r, r) + soff, SB, sm.dbar);
+      }
+      for (int t = 0; t < ntile; ++t) {
+        const int s = t % NS, k = t / NS;
+        if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 10);
+        const T* src = FWD ? row0 + (long long)t * TILE2
+                           : ut + tile_at(a.ts, tb, fb, cl[ntile - 1 - t], r) + soff;
+        mbar_expect_tx(&sm.full[s], SB);
+        bulk_copy(sm.ring + (size_t)s * SB, src, SB, &sm.full[s]);
+      }
+    }
     return;
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  // right-hand side of this warp's rows (independent of other rows)
-  double gval = 0.0;
-  if (lane < 8) {
-    const int grow = r * TILE + 8 * w + lane;
-    if (grow < n) {
-      const MatDesc md = a.md[m];
-      if (md.coarse) {
-        gval = a.g0[md.rhs_base + grow];
-      } else {
-        int pos;
-        if (a.ts.lperm) {
-          pos = a.ts.lperm[vb + grow];
+  const int rloc = RPW * w;                 // first slab row of this warp
+  const int rbase = r * TILE + R * slab;    // first row of the slab in the matrix
+  A acc[RPW];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) acc[i] = A(0);
+  double bval = 0.0;
+  if (FWD) {
+    // right-hand side of this warp's rows (lane i < RPW holds row rloc + i)
+    if (lane < RPW) {
+      const int grow = rbase + rloc + lane;
+      if (grow < a.ts.n[m]) {
+        const MatDesc md = a.md[m];
+        if (md.coarse) {
+          bval = a.g0[md.rhs_base + (a.cblock ? a.cblock[grow] : grow)];
         } else {
-          pos = md.start + grow;
-          if (pos >= md.rhs_len) pos -= md.rhs_len;
+          int pos;
+          if (a.ts.lperm) {
+            pos = a.ts.lperm[vb + grow];
+          } else {
+            pos = md.start + grow;
+            if (pos >= md.rhs_len) pos -= md.rhs_len;
+          }
+          bval = a.rhs[md.rhs_base + pos];
         }
-        gval = a.rhs[md.rhs_base + pos];
       }
     }
-  }
-  // this row's backward slots are reset here (nobody reads them in this launch)
-  if (threadIdx.x < TILE) a.dout[vb + r * TILE + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
-  A part[8];
+    // the backward slots of this slab are reset here (nobody reads them in this launch)
+    if (threadIdx.x < R)
+      a.dout[vb + rbase + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
+  } else {
+    // z_r comes from the forward launch (a previous kernel): plain loads are coherent
+    const A z0 = A(a.zc[vb + r * TILE + 2 * lane]);
+    const A z1 = A(a.zc[vb + r * TILE + 2 * lane + 1]);
+    // the forward slots of this slab are reset for the next forward launch
+    if (threadIdx.x < R)
+      a.y[vb + rbase + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
+    mbar_wait(sm.dbar, 0, a.err, 12);
+    const T* et = reinterpret_cast<const T*>(sm.diag);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) part[i] = A(0);
+    for (int i = 0; i < RPW; ++i) {
+      A e0, e1;
+      sm_pair(et + (rloc + i) * TILE + 2 * lane, e0, e1);
+      acc[i] = fma(e1, z1, e0 * z0);
+    }
+  }
+  const double* dep = FWD ? a.y : a.dout;
   for (int t = 0; t < ntile; ++t) {
     const int s = t % NS;
-    const double2 yv = wait_pair(a.y + vb + (k0 + t) * TILE + 2 * lane, a.err, 1);
-    const A y0 = A(yv.x), y1 = A(yv.y);
+    const int c = FWD ? k0 + t : cl[ntile - 1 - t];
+    const double2 v = wait_pair(dep + vb + c * TILE + 2 * lane, a.err, FWD ? 1 : 2);
+    const A v0 = A(v.x), v1 = A(v.y);
     mbar_wait(&sm.full[s], (t / NS) & 1, a.err, 11);
-    const T* st = reinterpret_cast<const T*>(sm.ring + (size_t)s * TB);
+    const T* st = reinterpret_cast<const T*>(sm.ring + (size_t)s * SB);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < RPW; ++i) {
       A l0, l1;
-      sm_pair(st + (8 * w + i) * TILE + 2 * lane, l0, l1);
-      part[i] = fma(l0, y0, part[i]);
-      part[i] = fma(l1, y1, part[i]);
+      sm_pair(st + (rloc + i) * TILE + 2 * lane, l0, l1);
+      if (FWD) {
+        acc[i] = fma(l0, v0, acc[i]);
+        acc[i] = fma(l1, v1, acc[i]);
+      } else {
+        acc[i] = fma(-l0, v0, acc[i]);
+        acc[i] = fma(-l1, v1, acc[i]);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.empty[s]);
   }
   int row;
-  const A tot = reduce8(part, row);
-  const double gr = __shfl_sync(0xffffffffu, gval, row);  // row r's rhs sits in lane r
-  if ((lane & 3) == 0) sm.xs[8 * w + row] = double(A(gr) - tot);
-  consumers_sync();
-  // diagonal block: y_r = Linv_rr * xs
-  mbar_wait(sm.dbar, 0, a.err, 12);
-  const T* dt = reinterpret_cast<const T*>(sm.diag);
-  const A x0 = A(sm.xs[2 * lane]), x1 = A(sm.xs[2 * lane + 1]);
-  A q[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    A l0, l1;
-    sm_pair(dt + (8 * w + i) * TILE + 2 * lane, l0, l1);
-    q[i] = fma(l1, x1, l0 * x0);
-  }
-  const A yr = reduce8(q, row);
-  if ((lane & 3) == 0) st_relaxed(a.y + vb + r * TILE + 8 * w + row, double(yr));
-}
-
-// Backward row r: d_r = Linv_rr^T (y_r - sum_{c>r} L_cr^T d_c).
-template <class T, class A>
-__device__ void bwd_row(const TrsvArgs& a, const T* __restrict__ tiles, int m, int r,
-                        const RowSmem& sm) {
-  constexpr unsigned TB = Ring<T>::TB;
-  constexpr int NS = Ring<T>::NS;
-  const long long tb = a.ts.tbase[m];
-  const int vb = a.ts.vbase[m];
-  const int fb = vb / TILE;
-  // rows c > r whose envelope reaches column r (ascending), consumed from the last
-  const int* cl = a.ts.colidx + a.ts.colptr[fb + r];
-  const int ncl = a.ts.colptr[fb + r + 1] - a.ts.colptr[fb + r];
-  if (threadIdx.x >= NCONS) {
-    if (threadIdx.x == NCONS)
-      produce<T>(sm, ncl,
-                 [=](int t) { return tiles + tile_at(a.ts, tb, fb, cl[ncl - 1 - t], r); },
-                 tiles + tile_at(a.ts, tb, fb, r, r), a.err);
-    return;
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  // y_r comes from the forward launch (a previous kernel): plain loads are coherent;
-  // the slot is then reset for the next forward launch (only this CTA reads it)
-  double yown = 0.0;
-  if (threadIdx.x < TILE) {
-    yown = a.y[vb + r * TILE + threadIdx.x];
-    a.y[vb + r * TILE + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
-  }
-  A p0 = A(0), p1 = A(0);
-  for (int t = 0; t < ncl; ++t) {
-    const int s = t % NS;
-    const int c = cl[ncl - 1 - t];
-    const double* dc = a.dout + vb + c * TILE + 8 * w;
-    A dv[8];
-#pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-      const double2 v = wait_pair(dc + i, a.err, 2);
-      dv[i] = A(v.x);
-      dv[i + 1] = A(v.y);
+  const A tot = reduce_rows<RPW>(acc, row);
+  const int orow = vb + rbase + rloc + row;
+  if (FWD) {
+    const double br = __shfl_sync(0xffffffffu, bval, row);  // row i's rhs sits in lane i
+    if ((lane & (32 / RPW - 1)) == 0) {
+      const double zv = double(A(br) - tot);
+      st_relaxed(a.y + orow, zv);
+      a.zc[orow] = zv;
     }
-    mbar_wait(&sm.full[s], (t / NS) & 1, a.err, 13);
-    const T* st = reinterpret_cast<const T*>(sm.ring + (size_t)s * TB);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      A l0, l1;
-      sm_pair(st + (8 * w + i) * TILE + 2 * lane, l0, l1);
-      p0 = fma(l0, dv[i], p0);
-      p1 = fma(l1, dv[i], p1);
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&sm.empty[s]);
-  }
-  sm.red[w * TILE + 2 * lane] = double(p0);
-  sm.red[w * TILE + 2 * lane + 1] = double(p1);
-  consumers_sync();
-  if (threadIdx.x < TILE) {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) s += sm.red[k * TILE + threadIdx.x];
-    sm.xs[threadIdx.x] = double(A(yown) - A(s));
-  }
-  consumers_sync();
-  mbar_wait(sm.dbar, 0, a.err, 14);
-  const T* dt = reinterpret_cast<const T*>(sm.diag);
-  A q0 = A(0), q1 = A(0);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    A l0, l1;
-    sm_pair(dt + (8 * w + i) * TILE + 2 * lane, l0, l1);
-    const A xv = A(sm.xs[8 * w + i]);
-    q0 = fma(l0, xv, q0);
-    q1 = fma(l1, xv, q1);
-  }
-  sm.red[w * TILE + 2 * lane] = double(q0);
-  sm.red[w * TILE + 2 * lane + 1] = double(q1);
-  consumers_sync();
-  if (threadIdx.x < TILE) {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) s += sm.red[k * TILE + threadIdx.x];
-    st_relaxed(a.dout + vb + r * TILE + threadIdx.x, double(A(s)));
+  } else {
+    if ((lane & (32 / RPW - 1)) == 0) st_relaxed(a.dout + orow, double(tot));
   }
 }
 
-constexpr int SMEM_BYTES =
-    RING_BYTES + DIAG_BYTES + (2 * MAXST + 1) * 8 + TILE * 8 + 8 * TILE * 8 + 16;
+constexpr int SMEM_BYTES = RING_BYTES + DIAG_BYTES + (2 * MAXST + 1) * 8 + 16;
 
 template <class T, class A, bool FWD>
 __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
@@ -368,8 +310,6 @@ __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
   sm.full = reinterpret_cast<unsigned long long*>(sm.diag + DIAG_BYTES);
   sm.empty = sm.full + MAXST;
   sm.dbar = sm.empty + MAXST;
-  sm.xs = reinterpret_cast<double*>(sm.dbar + 1);
-  sm.red = sm.xs + TILE;
   __shared__ unsigned long long s_ticket;
   if (threadIdx.x == 0) {
     s_ticket = atomicAdd(a.ticket, 1ull);
@@ -385,16 +325,18 @@ __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
   const TrsvWork wk = a.work[t];
   const MatDesc md = a.md[wk.mat];
   if (a.sc && a.sc[md.sub].done) return;
-  if (FWD) {
-    if (md.coarse)
-      fwd_row<double, double>(a, a.ctiles, wk.mat, wk.row, sm);
+  if (md.coarse) {
+    if (md.nsub == 4)
+      sweep_item<double, double, 16, FWD>(a, a.ctiles, a.cut, wk.mat, wk.row, wk.slab, sm);
     else
-      fwd_row<T, A>(a, reinterpret_cast<const T*>(a.ltiles), wk.mat, wk.row, sm);
+      sweep_item<double, double, 64, FWD>(a, a.ctiles, a.cut, wk.mat, wk.row, 0, sm);
   } else {
-    if (md.coarse)
-      bwd_row<double, double>(a, a.ctiles, wk.mat, wk.row, sm);
+    const T* lt = reinterpret_cast<const T*>(a.ltiles);
+    const T* ut = reinterpret_cast<const T*>(a.lut);
+    if (md.nsub == 2)
+      sweep_item<T, A, 32, FWD>(a, lt, ut, wk.mat, wk.row, wk.slab, sm);
     else
-      bwd_row<T, A>(a, reinterpret_cast<const T*>(a.ltiles), wk.mat, wk.row, sm);
+      sweep_item<T, A, 64, FWD>(a, lt, ut, wk.mat, wk.row, 0, sm);
   }
 }
 

@@ -22,7 +22,7 @@ class Solver:
 
     def __init__(self, levels, P, overlap, *, precision="fp64", variant="additive",
                  weighting="omega", q=0, coeffs=None, flexible=-1, stream=None,
-                 profile=False, local_order="lex"):
+                 profile=False, local_order="lex", slabs_local=0, slabs_coarse=0):
         L = _lib.lib()
         self.levels = tuple(int(l) for l in levels)
         self.d = len(self.levels)
@@ -43,6 +43,8 @@ class Solver:
         opt.flexible = int(flexible)
         opt.profile = int(bool(profile))
         opt.local_order = {"lex": 0, "curve": 1}[local_order]
+        opt.slabs_local = int(slabs_local)
+        opt.slabs_coarse = int(slabs_coarse)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
