@@ -71,7 +71,8 @@ typedef struct {
   int slabs_local;      /* row slabs per 64-row tile row in the local substitutions (one CTA
                            each): 1 or 2; 0 (default) = 1.  Splitting shortens the FP64 GEMV on
                            the dependency chain from one tile row to the next. */
-  int slabs_coarse;     /* the same for the coarse substitutions: 1 or 4; 0 (default) = 4 */
+  int slabs_coarse;     /* the same for the coarse substitutions: 1 or 4; 0 (default) = 4.
+                           FP32 / BF16 local factors require 4 (INVALID_ARG otherwise). */
 } sfcdd_options;
 
 typedef struct {

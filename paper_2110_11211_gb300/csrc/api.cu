@@ -227,13 +227,19 @@ void rcm_order(int n, const std::vector<int>& deg, const std::vector<int>& adj, 
 }
 
 void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
-                   const std::vector<char>& is_coarse, const std::vector<int>& tfirst,
-                   SkylineHost& o) {
+                   const std::vector<char>& is_coarse, const std::vector<int>& cb,
+                   const std::vector<int>& tfirst, SkylineHost& o) {
   const int nmat = (int)nt.size();
   const int nrows = (int)tfirst.size();
   o.kmin.assign(nrows, 0);
   o.rowoff.assign(nrows, 0);
   for (int r = 0; r < nrows; ++r) o.kmin[r] = tfirst[r] / TILE;
+  // a matrix solved with cb-tile diagonal blocks keeps whole blocks in every row
+  for (int m = 0; m < nmat; ++m) {
+    const int fb = vbase[m] / TILE;
+    if (cb[m] > 1)
+      for (int I = 0; I < nt[m]; ++I) o.kmin[fb + I] = o.kmin[fb + I] / cb[m] * cb[m];
+  }
   std::vector<int> colcnt(nrows, 0);
   o.stored.assign(nmat, 0);
   o.tbase.assign(nmat, 0);
@@ -267,6 +273,22 @@ void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
     const int fb = vbase[m] / TILE;
     for (int I = 0; I < nt[m]; ++I)
       for (int K = o.kmin[fb + I]; K < I; ++K) o.colidx[pos[fb + K]++] = I;
+  }
+  // tiles the substitutions stream: forward rows skip their own diagonal block,
+  // backward rows read their block of E tiles and the column tiles below it
+  for (int m = 0; m < nmat; ++m) {
+    const int fb = vbase[m] / TILE;
+    long long f = 0, b = 0;
+    for (int I = 0; I < nt[m]; ++I) {
+      const int blk0 = I / cb[m] * cb[m];
+      const int blk1 = std::min(blk0 + cb[m], nt[m]);
+      f += std::max(0, blk0 - o.kmin[fb + I]);
+      b += blk1 - blk0;
+      for (int k = o.colptr[fb + I]; k < o.colptr[fb + I + 1]; ++k)
+        if (o.colidx[k] >= blk1) ++b;
+    }
+    (is_coarse[m] ? o.fwd_tiles_c : o.fwd_tiles_l) += f;
+    (is_coarse[m] ? o.bwd_tiles_c : o.bwd_tiles_l) += b;
   }
   o.col_max_local.assign(max_nt_l, 0);
   o.col_max_coarse.assign(max_nt_c, 0);
@@ -331,9 +353,11 @@ struct sfcdd_handle {
   void* lut = nullptr;      // Lh^T tiles, E_K on the diagonal
   double* ctiles = nullptr;
   double* cut = nullptr;
-  long long ltile_elems = 0, ctile_elems = 0, ldiag_elems = 0, cdiag_elems = 0;
+  long long ltile_elems = 0, ctile_elems = 0;
   int max_nt = 0, nt0 = 0, max_ltiles = 0, max_ctiles = 0;
   int nsub_local = 1, nsub_coarse = 4;
+  int cb_coarse = 4;  // tiles per unit diagonal block of the coarse substitution form
+  long long fwd_tiles_l = 0, bwd_tiles_l = 0, fwd_tiles_c = 0, bwd_tiles_c = 0;
   // substitution
   TrsvWork *work_f = nullptr, *work_b = nullptr;
   int nwork = 0;
@@ -593,6 +617,9 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
   if ((h->nsub_local != 1 && h->nsub_local != 2) || (h->nsub_coarse != 1 && h->nsub_coarse != 4))
     return SFCDD_ERR_INVALID_ARG;
+  // FP32 / BF16 launches size their shared memory for the local tiles: the
+  // FP64 coarse rows then run in 16-row slabs
+  if (h->precision != SFCDD_FP64 && h->nsub_coarse != 4) return SFCDD_ERR_INVALID_ARG;
   h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
   h->stream = (cudaStream_t)o.stream;
   h->profiling = o.profile != 0;
@@ -794,7 +821,9 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     dfree(h, tfirst);
     std::vector<char> is_coarse(P + 1, 0);
     is_coarse[P] = 1;
-    build_skyline(h->h_nt, h->h_vbase, is_coarse, tf, sky);
+    std::vector<int> cb(P + 1, 1);
+    cb[P] = h->cb_coarse;
+    build_skyline(h->h_nt, h->h_vbase, is_coarse, cb, tf, sky);
   }
   h->h_kmin = sky.kmin;
   h->h_rowoff = sky.rowoff;
@@ -802,11 +831,12 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   for (int m = 0; m <= P; ++m) h->h_tbase[m] = sky.tbase[m];
   h->max_ltiles = sky.max_ltiles;
   h->max_ctiles = sky.max_ctiles;
+  h->fwd_tiles_l = sky.fwd_tiles_l;
+  h->bwd_tiles_l = sky.bwd_tiles_l;
+  h->fwd_tiles_c = sky.fwd_tiles_c;
+  h->bwd_tiles_c = sky.bwd_tiles_c;
   h->ltile_elems = sky.ltiles * TILE2;
   h->ctile_elems = sky.ctiles * TILE2;
-  h->ldiag_elems = 0;
-  for (int m = 0; m < P; ++m) h->ldiag_elems += (long long)h->h_nt[m] * TILE2;
-  h->cdiag_elems = (long long)h->nt0 * TILE2;
   h->col_max_local = sky.col_max_local;
   h->col_max_coarse = sky.col_max_coarse;
   if (h->variant != SFCDD_COARSE_ONLY) {
@@ -837,6 +867,10 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   // stream so that it overlaps the local factorization (the two are independent)
   TRY(dalloc(h, &h->ctiles, h->ctile_elems));
   TRY(dalloc(h, &h->cut, h->ctile_elems));
+  double* xs = nullptr;  // inverses of the coarse diagonal blocks (scratch)
+  const int cnblk = (h->nt0 + h->cb_coarse - 1) / h->cb_coarse;
+  if (h->cb_coarse > 1)
+    TRY(dalloc(h, &xs, (size_t)cnblk * h->cb_coarse * h->cb_coarse * TILE2));
   cudaEvent_t ev_fork = nullptr, ev_coarse = nullptr;
   SFCDD_CUDA_OK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
   SFCDD_CUDA_OK(cudaEventCreateWithFlags(&ev_coarse, cudaEventDisableTiming));
@@ -855,7 +889,10 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     factor_tiles(cts, 0, 1, h->nt0, h->col_max_coarse.data(), h->ctiles, Store::F64, h->err, s2,
                  &ch);
     pf2.run(SFCDD_K_COARSE_FACTOR, [&] {
-      unitize_tiles(cts, 0, 1, h->max_ctiles, h->ctiles, h->cut, Store::F64, s2);
+      if (h->cb_coarse > 1)
+        unitize_blocks(cts, h->nt0, h->cb_coarse, h->stored[P], h->ctiles, h->cut, xs, s2);
+      else
+        unitize_tiles(cts, 0, 1, h->max_ctiles, h->ctiles, h->cut, Store::F64, s2);
     });
   }
   SFCDD_CUDA_OK(cudaEventRecord(ev_coarse, h->side_stream));
@@ -902,8 +939,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   // per-matrix right-hand-side descriptors (one problem: scalars index 0)
   {
     std::vector<MatDesc> md(P + 1);
-    for (int m = 0; m < P; ++m) md[m] = {0, h->N, h->h_start[m], 0, 0, h->nsub_local};
-    md[P] = {0, h->N0, 0, 1, 0, h->nsub_coarse};
+    for (int m = 0; m < P; ++m) md[m] = {0, h->N, h->h_start[m], 0, 0, h->nsub_local, 1};
+    md[P] = {0, h->N0, 0, 1, 0, h->nsub_coarse, h->cb_coarse};
     TRY(dalloc(h, &h->d_md, P + 1));
     SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_md, md.data(), (P + 1) * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
     SFCDD_CUDA_OK(cudaStreamSynchronize(s));
@@ -963,6 +1000,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->setup_ms = ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (xs) dfree(h, xs);
   dfree(h, keys);
   dfree(h, sort_tmp);
   int fi = 0;
@@ -1294,16 +1332,18 @@ double sfcdd_kernel_work(const sfcdd_handle* h, int kc) {
   if (!h) return 0.0;
   const double esz = h->precision == SFCDD_FP64 ? 8 : (h->precision == SFCDD_FP32 ? 4 : 2);
   const bool loc = h->variant != SFCDD_COARSE_ONLY, crs = h->variant != SFCDD_ONE_LEVEL;
-  // forward: the off-diagonal Lh tiles; backward: the Lh^T tiles and the E_K blocks
-  const double lall = loc ? (double)h->ltile_elems * esz : 0.0;
-  const double call = crs ? (double)h->ctile_elems * 8.0 : 0.0;
-  const double ldia = loc ? (double)h->ldiag_elems * esz : 0.0;
-  const double cdia = crs ? (double)h->cdiag_elems * 8.0 : 0.0;
+  // forward: the Lh tiles left of each row's diagonal block; backward: the
+  // E tiles of the row's diagonal block and the Lh^T tiles below it
+  const double t2 = (double)TILE2;
+  const double lf = loc ? (double)h->fwd_tiles_l * t2 * esz : 0.0;
+  const double lb = loc ? (double)h->bwd_tiles_l * t2 * esz : 0.0;
+  const double cf = crs ? (double)h->fwd_tiles_c * t2 * 8.0 : 0.0;
+  const double cbk = crs ? (double)h->bwd_tiles_c * t2 * 8.0 : 0.0;
   switch (kc) {
     case SFCDD_K_TRSV_FWD:
-      return (lall - ldia) + (call - cdia);
+      return lf + cf;
     case SFCDD_K_TRSV_BWD:
-      return lall + call;
+      return lb + cbk;
     case SFCDD_K_STENCIL:
       return 16.0 * (double)h->N;
     case SFCDD_K_POTRF:

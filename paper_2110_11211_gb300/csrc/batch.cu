@@ -682,7 +682,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   std::vector<int> tf(nrows);
   SFCDD_CUDA_OK(cudaMemcpyAsync(tf.data(), tfirst, nrows * sizeof(int), cudaMemcpyDeviceToHost, s));
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
-  build_skyline(b->h_nt, b->h_vbase, is_coarse, tf, b->sky);
+  build_skyline(b->h_nt, b->h_vbase, is_coarse, std::vector<int>(b->nmat, 1), tf, b->sky);
   int *d_kmin, *d_rowoff, *d_colptr, *d_colidx;
   BTRY(balloc(b, &d_kmin, nrows));
   BTRY(balloc(b, &d_rowoff, nrows));
@@ -755,17 +755,21 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
                     b->sky.ctiles * TILE2 * 8;
 
   // substitution descriptors and work lists
+  // FP32 / BF16 substitution launches run the FP64 coarse rows in 16-row slabs
+  const int cslabs = b->st == Store::F64 ? 1 : 4;
   std::vector<MatDesc> md(b->nmat);
   for (int si = 0; si < nsub; ++si) {
     const SubDesc& sd = b->hsub[si];
     for (int i = 0; i < P; ++i)
-      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)si * P + i], 0, si, 1};
-    md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si, 1};
+      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)si * P + i], 0, si, 1, 1};
+    md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si, cslabs, 1};
   }
   BTRY(balloc(b, &b->d_md, b->nmat));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_md, md.data(), b->nmat * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
   std::vector<TrsvWork> wf, wb;
-  build_worklists(b->h_nt, std::vector<char>(b->nmat, 1), std::vector<int>(b->nmat, 1), wf, wb);
+  std::vector<int> nsl(b->nmat, 1);
+  for (int si = 0; si < nsub; ++si) nsl[b->hsub[si].cmat] = cslabs;
+  build_worklists(b->h_nt, std::vector<char>(b->nmat, 1), nsl, wf, wb);
   b->nwork = (int)wf.size();
   BTRY(balloc(b, &b->work_f, b->nwork));
   BTRY(balloc(b, &b->work_b, b->nwork));

@@ -433,6 +433,150 @@ static void unitize_t(const TileSetDev& ts, int mat0, int nmat, int max_stored, 
   k_unitize<T><<<dim3(max_stored, nmat), FB, sm, s>>>(ts, mat0, tiles, ut);
 }
 
+// ---------------------------------------------------------------------------
+// Substitution form with cb-tile diagonal blocks (one matrix, FP64).  D_J is
+// the lower block-triangular cb x cb-tile diagonal block J of the factor and
+// X_J = D_J^{-1}; L = Lh blockdiag(D_J) with Lh_IK = sum_k L_{I,k} X_{k,K}
+// over the tiles k of K's block (k >= K), and E_J = X_J^T X_J.  xs holds X_J
+// as a cb x cb grid of tiles per block.
+
+// acc += P Q on 64 x 64 tiles.  p_rowmajor: the tile at p holds P row-major
+// (staged transposed, Xt[s][a] = P[a][s]); otherwise it holds P^T row-major
+// (staged as is).  Q is row-major.
+__device__ __forceinline__ void acc_product(double (&acc)[4][4], double (*Xt)[TILE + 4],
+                                            double (*Yt)[TILE + 4], const double* __restrict__ p,
+                                            bool p_rowmajor, const double* __restrict__ q,
+                                            int r0, int c0) {
+  __syncthreads();  // previous users of Xt / Yt are done
+  if (p_rowmajor) load_transposed<double>(Xt, p);  // Xt[s][a] = P[a][s]
+  else load_plain<double>(Xt, p);                  // p holds P^T: Xt[s][a] = P^T[s][a] = P[a][s]
+  load_plain<double>(Yt, q);                       // Yt[s][b] = Q[s][b]
+  __syncthreads();
+  mma_4x4_from<double>(acc, Xt, Yt, r0, c0, 0);
+}
+
+__device__ __forceinline__ long long xs_off(int cb, int J, int i, int j) {
+  return ((long long)(J * cb + i) * cb + j) * TILE2;
+}
+
+// Diagonal d of every block: X_{j+d, j} = -X_{j+d,j+d} sum_{k=j}^{j+d-1} L_{j+d,k} X_{k,j}
+// (d = 0 copies the stored inverses).  grid = (cb, number of blocks)
+__global__ void __launch_bounds__(FB) k_sb_inverse(TileSetDev ts, int cb, int d,
+                                                   const double* __restrict__ tiles,
+                                                   double* __restrict__ xs) {
+  extern __shared__ __align__(16) unsigned char dsm_sbi[];
+  double (*Xt)[TILE + 4] = reinterpret_cast<double (*)[TILE + 4]>(dsm_sbi);
+  double (*Yt)[TILE + 4] = Xt + TILE;
+  const int J = blockIdx.y, j = blockIdx.x, i = j + d;
+  const int nt = ts.nt[0];
+  const int blk0 = J * cb;
+  const int nb = min(cb, nt - blk0);
+  if (i >= nb) return;
+  const int fb = ts.vbase[0] / TILE;
+  const long long tb = ts.tbase[0];
+  double* out = xs + xs_off(cb, J, i, j);
+  if (d == 0) {
+    const double* src = tiles + tile_at(ts, tb, fb, blk0 + i, blk0 + i);
+    for (int e = threadIdx.x; e < TILE2; e += FB) out[e] = src[e];
+    return;
+  }
+  const int r0 = (threadIdx.x % 16) * 4, c0 = (threadIdx.x / 16) * 4;
+  double acc[4][4] = {};
+  for (int k = j; k < i; ++k)
+    acc_product(acc, Xt, Yt, tiles + tile_at(ts, tb, fb, blk0 + i, blk0 + k), true,
+                xs + xs_off(cb, J, k, j), r0, c0);
+  // S -> Yt, then X_ij = -X_ii S
+  __syncthreads();
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) Yt[r0 + a][c0 + b] = acc[a][b];
+  load_transposed<double>(Xt, xs + xs_off(cb, J, i, i));
+  __syncthreads();
+  double x[4][4] = {};
+  mma_4x4_from<double>(x, Xt, Yt, r0, c0, 0);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) out[(r0 + a) * TILE + c0 + b] = -x[a][b];
+}
+
+// One stored tile (I, K) per CTA.  Inside a block (I, K in block J, a >= b
+// their offsets): E_ab = sum_{k >= a} X_ka^T X_kb into ut, and E_ba = E_ab^T
+// into the tiles slot when a > b.  Below the block: Lh_IK^T into ut (the
+// tiles slot still holds L and is read by the other tiles of row I).
+__global__ void __launch_bounds__(FB) k_sb_unitize(TileSetDev ts, int cb, double* __restrict__ tiles,
+                                                   double* __restrict__ ut,
+                                                   const double* __restrict__ xs) {
+  extern __shared__ __align__(16) unsigned char dsm_sbu[];
+  double (*Xt)[TILE + 4] = reinterpret_cast<double (*)[TILE + 4]>(dsm_sbu);
+  double (*Yt)[TILE + 4] = Xt + TILE;
+  const int nt = ts.nt[0];
+  const int fb = ts.vbase[0] / TILE;
+  if ((int)blockIdx.x >= stored_tiles(ts, fb, nt)) return;
+  int I, K;
+  skyline_decode(ts, fb, nt, blockIdx.x, I, K);
+  const long long tb = ts.tbase[0];
+  const int J = K / cb, blk0 = J * cb;
+  const int nb = min(cb, nt - blk0);
+  const int b = K - blk0;
+  const int r0 = (threadIdx.x % 16) * 4, c0 = (threadIdx.x / 16) * 4;
+  double acc[4][4] = {};
+  const bool inside = I < blk0 + nb;
+  if (inside) {
+    const int aa = I - blk0;
+    // X_ka^T X_kb: Xt[s][p] = X_ka[s][p] (plain = P^T given), Yt = X_kb
+    for (int k = aa; k < nb; ++k)
+      acc_product(acc, Xt, Yt, xs + xs_off(cb, J, k, aa), false,
+                  xs + xs_off(cb, J, k, b), r0, c0);
+  } else {
+    for (int k = b; k < nb; ++k)
+      acc_product(acc, Xt, Yt, tiles + tile_at(ts, tb, fb, I, blk0 + k), true,
+                  xs + xs_off(cb, J, k, b), r0, c0);
+  }
+  __syncthreads();
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) {
+      Xt[r0 + a][c0 + q] = acc[a][q];
+      Yt[c0 + q][r0 + a] = acc[a][q];
+    }
+  __syncthreads();
+  double* uo = ut + tile_at(ts, tb, fb, I, K);
+  if (inside) {
+    for (int e = threadIdx.x; e < TILE2; e += FB) uo[e] = Xt[e / TILE][e % TILE];
+    if (I > K) {
+      double* lo = tiles + tile_at(ts, tb, fb, I, K);
+      for (int e = threadIdx.x; e < TILE2; e += FB) lo[e] = Yt[e / TILE][e % TILE];
+    }
+  } else {
+    for (int e = threadIdx.x; e < TILE2; e += FB) uo[e] = Yt[e / TILE][e % TILE];
+  }
+}
+
+// Below-block tiles: tiles(I, K) = ut(I, K)^T = Lh_IK.
+__global__ void __launch_bounds__(FB) k_sb_transpose(TileSetDev ts, int cb, double* __restrict__ tiles,
+                                                     const double* __restrict__ ut) {
+  __shared__ double t[TILE][TILE + 1];
+  const int nt = ts.nt[0];
+  const int fb = ts.vbase[0] / TILE;
+  if ((int)blockIdx.x >= stored_tiles(ts, fb, nt)) return;
+  int I, K;
+  skyline_decode(ts, fb, nt, blockIdx.x, I, K);
+  const int blk0 = K / cb * cb;
+  if (I < min(blk0 + cb, nt)) return;
+  const long long off = tile_at(ts, ts.tbase[0], fb, I, K);
+  for (int e = threadIdx.x; e < TILE2; e += FB) t[e / TILE][e % TILE] = ut[off + e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < TILE2; e += FB) tiles[off + e] = t[e % TILE][e / TILE];
+}
+
+void unitize_blocks(const TileSetDev& ts, int nt, int cb, int stored, double* tiles, double* ut,
+                    double* xs, cudaStream_t s) {
+  const int sm = 2 * TILE * (TILE + 4) * (int)sizeof(double);
+  cudaFuncSetAttribute(k_sb_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_sb_unitize, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  const int nblk = (nt + cb - 1) / cb;
+  for (int d = 0; d < cb; ++d) k_sb_inverse<<<dim3(cb - d, nblk), FB, sm, s>>>(ts, cb, d, tiles, xs);
+  k_sb_unitize<<<stored, FB, sm, s>>>(ts, cb, tiles, ut, xs);
+  k_sb_transpose<<<stored, FB, 0, s>>>(ts, cb, tiles, ut);
+}
+
 void unitize_tiles(const TileSetDev& ts, int mat0, int nmat, int max_stored, void* tiles, void* ut,
                    Store st, cudaStream_t s) {
   if (st == Store::F64)

@@ -236,10 +236,14 @@ struct SkylineHost {
   long long ltiles = 0, ctiles = 0;  // stored tiles in the local / coarse buffers
   int max_ltiles = 0, max_ctiles = 0;
   double potrf = 0, trsm = 0, syrk = 0, coarse = 0;
+  // tiles read by one forward / backward substitution (local, coarse)
+  long long fwd_tiles_l = 0, bwd_tiles_l = 0, fwd_tiles_c = 0, bwd_tiles_c = 0;
 };
+// cb[m] > 1: matrix m is solved with cb-tile diagonal blocks (its envelope is
+// widened to whole blocks).
 void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
-                   const std::vector<char>& is_coarse, const std::vector<int>& tfirst,
-                   SkylineHost& out);
+                   const std::vector<char>& is_coarse, const std::vector<int>& cb,
+                   const std::vector<int>& tfirst, SkylineHost& out);
 
 // ---------------- kernels / launchers (defined in the .cu files) ----------------
 
@@ -313,6 +317,14 @@ void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const in
 // max_stored = largest stored tile count of one matrix (sizes the launch).
 void unitize_tiles(const TileSetDev& ts, int mat0, int nmat, int max_stored, void* tiles, void* ut,
                    Store st, cudaStream_t s);
+// The same with cb-tile diagonal blocks for a one-matrix FP64 tile set (the
+// coarse factor, envelope widened to whole blocks): below-block tiles become
+// Lh_IK = sum_k L_{I,k} X_{k,K} (X_J = inverse of the block-triangular
+// diagonal block J) with Lh^T in ut; inside block J, ut(I, K) = E_J(I, K) and
+// tiles(I, K) = E_J(K, I) for I > K, E_J = X_J^T X_J.  xs: scratch of
+// ceil(nt / cb) cb^2 tiles; stored = stored tile count.
+void unitize_blocks(const TileSetDev& ts, int nt, int cb, int stored, double* tiles, double* ut,
+                    double* xs, cudaStream_t s);
 void launch_convert_f32_bf16(const float* in, __nv_bfloat16* out, long long n, cudaStream_t s);
 // Lexicographic numbering inside each local matrix: matrices [0, nmat) of ts,
 // matrix m covers the cyclic range (mstart[m], ts.n[m]) of a problem with
@@ -346,6 +358,7 @@ struct MatDesc {
   int coarse;   // 1: FP64 coarse factor tiles, 0: local factor tiles
   int sub;      // index of the PCG scalars (problem) the matrix belongs to
   int nsub;     // slabs per tile row in the substitutions (1, 2 local; 1, 4 coarse)
+  int cb;       // tiles per unit diagonal block of the substitution form (1, or 4 coarse)
 };
 // Bit pattern (a signalling NaN) marking a substitution result slot as not yet
 // written in the current launch.

@@ -3,15 +3,18 @@
 // factorization is done once in the setup phase and every application of the
 // preconditioner only runs the two triangular solves, Sec. 3.1).
 //
-// Factor form.  With D = blockdiag(L_KK) over 64 x 64 tiles the setup splits
-// L = Lh D, Lh_IK = L_IK L_KK^{-1} (unit diagonal blocks), so that
-// A = Lh (D D^T) Lh^T and
-//   forward   z_I = b_I - sum_{K<I} Lh_IK z_K
-//   backward  x_K = E_K z_K - sum_{I>K} Lh_IK^T x_I,   E_K = L_KK^{-T} L_KK^{-1}.
-// The forward reads the Lh tiles (row-major); the backward reads a second copy
-// that holds Lh_IK^T in the same slot and E_K in the diagonal slot.  Both sweeps
-// therefore stream contiguous row slabs, and the chain from one tile row to the
-// next carries a single tile GEMV (no diagonal solve on it).
+// Factor form.  With D = blockdiag(D_J), D_J the lower block-triangular
+// diagonal block of cb x cb tiles (cb = 1 for the local factors, 4 for the
+// coarse one), the setup splits L = Lh D with Lh = L D^{-1} (identity diagonal
+// blocks), so that A = Lh (D D^T) Lh^T and, for tile rows I in block J,
+//   forward   z_I = b_I - sum_{K < first row of J} Lh_IK z_K
+//   backward  x_I = sum_{K in J} E_J(I, K) z_K - sum_{K after J} Lh_KI^T x_K,
+// E_J = D_J^{-T} D_J^{-1}.  The forward reads the Lh tiles (row-major); the
+// backward reads a second copy holding Lh_KI^T in slot (K, I), and the E tiles
+// in the block's own slots (lower ones in that copy, upper ones in the first
+// array, where Lh is the identity).  Both sweeps stream contiguous row slabs;
+// all rows of a block depend only on earlier blocks, so the row-to-row chain
+// has nt / cb steps, each carrying the GEMVs with the previous block's tiles.
 //
 // Parallel layout: one CTA per work item (matrix, tile row, slab), a slab
 // being R = 64 / S consecutive rows of the tile row (S = 1, 2 or 4 per matrix:
@@ -23,26 +26,39 @@
 // a sentinel NaN bit pattern, every slot is written exactly once per launch
 // with a relaxed store, and a consumer polls the slots it needs with relaxed
 // loads until none holds the sentinel (bounded spin; a timeout sets the error
-// word and the CTA still drains its copies before it returns).  The forward
+// word and the CTA still drains its copies before it returns).  Only consumer
+// warp 0 polls; it hands the 64 values of each dependency to the other warps
+// through shared memory and a per-stage mbarrier, so one straggling lane
+// cannot hold up eight warps and the L2 sees one poller per CTA.  The forward
 // launch resets the backward slots of its slab and also writes its results to
 // a plain buffer zc; the backward launch reads z from zc and resets the forward
 // slots of its slab (nothing reads them during the backward launch).
 //
-// Data movement: a producer warp streams the item's tile slabs from HBM into a
-// shared-memory ring with bulk asynchronous copies (cp.async.bulk, completion
-// on mbarriers), the E_K slab first into its own buffer; eight consumer warps
-// wait on the ring's mbarriers, apply the slabs, and free the stages.
+// Data movement: a producer warp streams the item's tile slabs (E tiles first
+// in the backward) from HBM into a shared-memory ring with bulk asynchronous
+// copies (cp.async.bulk, completion on mbarriers); eight consumer warps wait on
+// the ring's mbarriers, apply the slabs, and free the stages.  The ring holds
+// two tiles of the launch's local precision (FP64 64 KB, FP32 32 KB, BF16
+// 16 KB), so low-precision launches keep more CTAs resident; coarse items of
+// such launches run in 16-row slabs (8 KB stages).
 #include "sfcdd_internal.cuh"
 
 namespace sfcdd {
 
 constexpr int NCONS = 256;                 // consumer threads: 8 warps
 constexpr int NTHR = NCONS + 32;           // + one producer warp
-constexpr int RING_BYTES = 64 * 1024;      // slab ring
-constexpr int DIAG_BYTES = TILE2 * 8;      // E_K slab buffer (room for a full FP64 tile)
 constexpr int MAXST = 8;
 constexpr long long SPIN_LIMIT = 1ll << 22;
 constexpr long long MBAR_LIMIT = 1ll << 26;
+constexpr long long SPIN_FAST = 1 << 12;   // polls before the poller starts to back off
+
+// Shared-memory plan of a launch whose local factors have element size ES.
+template <int ES>
+struct Plan {
+  static constexpr int RING = 2 * TILE2 * ES;  // slab ring: two local tiles
+  static constexpr int ZBUF = MAXST * TILE * 8;
+  static constexpr int BYTES = RING + ZBUF + 3 * MAXST * 8;
+};
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -107,7 +123,7 @@ __device__ __forceinline__ double2 wait_pair(const double* p, ErrWord* err, int 
   double2 v = ld_relaxed2(p);
   long long it = 0;
   while (is_pending(v.x) || is_pending(v.y)) {
-    if (++it > 32) __nanosleep(20);
+    if (++it > SPIN_FAST) __nanosleep(64);
     if ((it & 1023) == 0 &&
         (*((volatile int*)&err->code) != 0 || it > SPIN_LIMIT)) {
       if (atomicCAS(&err->code, 0, (int)SFCDD_ERR_TIMEOUT) == 0) err->index = site;
@@ -167,48 +183,66 @@ __device__ __forceinline__ A reduce_rows(A (&v)[RPW], int& row) {
 
 struct RowSmem {
   unsigned char* ring;
-  unsigned char* diag;
+  double* zbuf;               // [MAXST][TILE] dependency values of each stage
   unsigned long long* full;   // [MAXST]
   unsigned long long* empty;  // [MAXST]
-  unsigned long long* dbar;
+  unsigned long long* zbar;   // [MAXST] zbuf of the stage is filled
 };
 
 // One work item: rows [R s, R s + R) of tile row r of matrix m.
 //   FWD: z_r = b_r - sum_{c<r} Lh_rc z_c          (tiles lt, row list)
 //   BWD: x_r = E_r z_r - sum_{c>r} Lh_cr^T x_c     (tiles ut, column list)
-template <class T, class A, int R, bool FWD>
+template <class T, class A, int R, bool FWD, int RING>
 __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T* __restrict__ ut,
-                           int m, int r, int slab, const RowSmem& sm) {
+                           int m, int r, int slab, int cb, const RowSmem& sm) {
   constexpr int RPW = R / 8;                        // rows per consumer warp
   constexpr unsigned SB = R * TILE * sizeof(T);     // slab bytes
-  constexpr int NS = (RING_BYTES / (int)SB) < MAXST ? (RING_BYTES / (int)SB) : MAXST;
+  constexpr int NS = (RING / (int)SB) < MAXST ? (RING / (int)SB) : MAXST;
+  static_assert(NS >= 1, "slab larger than the ring");
   const long long tb = a.ts.tbase[m];
   const int vb = a.ts.vbase[m];
   const int fb = vb / TILE;
   const long long soff = (long long)R * slab * TILE;  // slab offset inside a tile
-  int ntile, k0 = 0;
+  // r's unit diagonal block: tile rows [blk0, blk1)
+  const int blk0 = r / cb * cb;
+  const int blk1 = min(blk0 + cb, a.ts.nt[m]);
+  // tile t of the item: forward, Lh (r, k0 + t) against z of row k0 + t, the
+  // tiles left of the block; backward, first the nE tiles E(r, blk0 + t)
+  // against z (from zc), then Lh^T (c, r) for the rows c below the block (from
+  // the last) against x_c
+  int ntile, nE = 0, ncl = 0, k0 = 0;
   const int* cl = nullptr;
   const T* row0 = nullptr;
   if (FWD) {
     k0 = a.ts.kmin[fb + r];
     row0 = lt + tb + (long long)a.ts.rowoff[fb + r] * TILE2 + soff;  // tile (r, k0)
-    ntile = r - k0;
+    ntile = blk0 > k0 ? blk0 - k0 : 0;
   } else {
-    // rows c > r whose envelope reaches column r (ascending), consumed from the last
-    cl = a.ts.colidx + a.ts.colptr[fb + r];
-    ntile = a.ts.colptr[fb + r + 1] - a.ts.colptr[fb + r];
+    cl = a.ts.colidx + a.ts.colptr[fb + r];  // rows c > r reaching column r, ascending
+    ncl = a.ts.colptr[fb + r + 1] - a.ts.colptr[fb + r];
+    int skip = 0;
+    while (skip < ncl && cl[skip] < blk1) ++skip;  // rows of r's own block
+    cl += skip;
+    ncl -= skip;
+    nE = blk1 - blk0;
+    ntile = nE + ncl;
   }
   if (threadIdx.x >= NCONS) {
     if (threadIdx.x == NCONS) {
-      if (!FWD) {
-        mbar_expect_tx(sm.dbar, SB);
-        bulk_copy(sm.diag, ut + tile_at(a.ts, tb, fb, r, r) + soff, SB, sm.dbar);
-      }
       for (int t = 0; t < ntile; ++t) {
         const int s = t % NS, k = t / NS;
         if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 10);
-        const T* src = FWD ? row0 + (long long)t * TILE2
-                           : ut + tile_at(a.ts, tb, fb, cl[ntile - 1 - t], r) + soff;
+        const T* src;
+        if (FWD) {
+          src = row0 + (long long)t * TILE2;
+        } else if (t < nE) {
+          // E(r, kp): ut holds the block's lower tiles, the tiles array its upper ones
+          const int kp = blk0 + t;
+          src = (kp <= r ? ut + tile_at(a.ts, tb, fb, r, kp) : lt + tile_at(a.ts, tb, fb, kp, r)) +
+                soff;
+        } else {
+          src = ut + tile_at(a.ts, tb, fb, cl[ncl - 1 - (t - nE)], r) + soff;
+        }
         mbar_expect_tx(&sm.full[s], SB);
         bulk_copy(sm.ring + (size_t)s * SB, src, SB, &sm.full[s]);
       }
@@ -246,40 +280,42 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
     if (threadIdx.x < R)
       a.dout[vb + rbase + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
   } else {
-    // z_r comes from the forward launch (a previous kernel): plain loads are coherent
-    const A z0 = A(a.zc[vb + r * TILE + 2 * lane]);
-    const A z1 = A(a.zc[vb + r * TILE + 2 * lane + 1]);
     // the forward slots of this slab are reset for the next forward launch
     if (threadIdx.x < R)
       a.y[vb + rbase + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
-    mbar_wait(sm.dbar, 0, a.err, 12);
-    const T* et = reinterpret_cast<const T*>(sm.diag);
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-      A e0, e1;
-      sm_pair(et + (rloc + i) * TILE + 2 * lane, e0, e1);
-      acc[i] = fma(e1, z1, e0 * z0);
-    }
   }
-  const double* dep = FWD ? a.y : a.dout;
   for (int t = 0; t < ntile; ++t) {
     const int s = t % NS;
-    const int c = FWD ? k0 + t : cl[ntile - 1 - t];
-    const double2 v = wait_pair(dep + vb + c * TILE + 2 * lane, a.err, FWD ? 1 : 2);
-    const A v0 = A(v.x), v1 = A(v.y);
-    mbar_wait(&sm.full[s], (t / NS) & 1, a.err, 11);
+    const unsigned ph = (t / NS) & 1;
+    double* zs = sm.zbuf + s * TILE;
+    double2 v;
+    if (w == 0) {
+      // every warp is done with the previous use of stage s (and of zs)
+      if (t >= NS) mbar_wait(&sm.empty[s], ph ^ 1, a.err, 13);
+      // z of the block comes from the forward launch (a previous kernel, never
+      // the sentinel), the other vectors from this launch
+      const double* dp = FWD      ? a.y + vb + (k0 + t) * TILE
+                         : t < nE ? a.zc + vb + (blk0 + t) * TILE
+                                  : a.dout + vb + cl[ncl - 1 - (t - nE)] * TILE;
+      v = wait_pair(dp + 2 * lane, a.err, FWD ? 1 : 2);
+      *reinterpret_cast<double2*>(zs + 2 * lane) = v;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.zbar[s]);
+    } else {
+      mbar_wait(&sm.zbar[s], ph, a.err, 14);
+      v = *reinterpret_cast<const double2*>(zs + 2 * lane);
+    }
+    // backward: + E z, - Lh^T x
+    const bool neg = !FWD && t >= nE;
+    const A v0 = A(neg ? -v.x : v.x), v1 = A(neg ? -v.y : v.y);
+    mbar_wait(&sm.full[s], ph, a.err, 11);
     const T* st = reinterpret_cast<const T*>(sm.ring + (size_t)s * SB);
 #pragma unroll
     for (int i = 0; i < RPW; ++i) {
       A l0, l1;
       sm_pair(st + (rloc + i) * TILE + 2 * lane, l0, l1);
-      if (FWD) {
-        acc[i] = fma(l0, v0, acc[i]);
-        acc[i] = fma(l1, v1, acc[i]);
-      } else {
-        acc[i] = fma(-l0, v0, acc[i]);
-        acc[i] = fma(-l1, v1, acc[i]);
-      }
+      acc[i] = fma(l0, v0, acc[i]);
+      acc[i] = fma(l1, v1, acc[i]);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.empty[s]);
@@ -299,25 +335,24 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
   }
 }
 
-constexpr int SMEM_BYTES = RING_BYTES + DIAG_BYTES + (2 * MAXST + 1) * 8 + 16;
-
 template <class T, class A, bool FWD>
 __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
+  using PL = Plan<(int)sizeof(T)>;
   extern __shared__ __align__(128) unsigned char dsm_trsv[];
   RowSmem sm;
   sm.ring = dsm_trsv;
-  sm.diag = dsm_trsv + RING_BYTES;
-  sm.full = reinterpret_cast<unsigned long long*>(sm.diag + DIAG_BYTES);
+  sm.zbuf = reinterpret_cast<double*>(dsm_trsv + PL::RING);
+  sm.full = reinterpret_cast<unsigned long long*>(sm.zbuf + MAXST * TILE);
   sm.empty = sm.full + MAXST;
-  sm.dbar = sm.empty + MAXST;
+  sm.zbar = sm.empty + MAXST;
   __shared__ unsigned long long s_ticket;
   if (threadIdx.x == 0) {
     s_ticket = atomicAdd(a.ticket, 1ull);
     for (int k = 0; k < MAXST; ++k) {
       mbar_init(&sm.full[k], 1);
       mbar_init(&sm.empty[k], NCONS / 32);
+      mbar_init(&sm.zbar[k], 1);
     }
-    mbar_init(sm.dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -326,17 +361,24 @@ __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
   const MatDesc md = a.md[wk.mat];
   if (a.sc && a.sc[md.sub].done) return;
   if (md.coarse) {
-    if (md.nsub == 4)
-      sweep_item<double, double, 16, FWD>(a, a.ctiles, a.cut, wk.mat, wk.row, wk.slab, sm);
-    else
-      sweep_item<double, double, 64, FWD>(a, a.ctiles, a.cut, wk.mat, wk.row, 0, sm);
+    // a full-row FP64 coarse item needs a 32 KB stage: FP64 launches only (host checks)
+    bool done = false;
+    if constexpr (sizeof(T) == 8) {
+      if (md.nsub == 1) {
+        sweep_item<double, double, 64, FWD, PL::RING>(a, a.ctiles, a.cut, wk.mat, wk.row, 0, md.cb, sm);
+        done = true;
+      }
+    }
+    if (!done)
+      sweep_item<double, double, 16, FWD, PL::RING>(a, a.ctiles, a.cut, wk.mat, wk.row, wk.slab,
+                                                     md.cb, sm);
   } else {
     const T* lt = reinterpret_cast<const T*>(a.ltiles);
     const T* ut = reinterpret_cast<const T*>(a.lut);
     if (md.nsub == 2)
-      sweep_item<T, A, 32, FWD>(a, lt, ut, wk.mat, wk.row, wk.slab, sm);
+      sweep_item<T, A, 32, FWD, PL::RING>(a, lt, ut, wk.mat, wk.row, wk.slab, md.cb, sm);
     else
-      sweep_item<T, A, 64, FWD>(a, lt, ut, wk.mat, wk.row, 0, sm);
+      sweep_item<T, A, 64, FWD, PL::RING>(a, lt, ut, wk.mat, wk.row, 0, md.cb, sm);
   }
 }
 
@@ -352,8 +394,9 @@ void launch_fill_pending(double* p, long long n, cudaStream_t s) {
 
 template <class T, class A, bool FWD>
 static void launch_k(const TrsvArgs& a, cudaStream_t s) {
-  cudaFuncSetAttribute(k_trsv<T, A, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  k_trsv<T, A, FWD><<<a.nwork, NTHR, SMEM_BYTES, s>>>(a);
+  constexpr int bytes = Plan<(int)sizeof(T)>::BYTES;
+  cudaFuncSetAttribute(k_trsv<T, A, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  k_trsv<T, A, FWD><<<a.nwork, NTHR, bytes, s>>>(a);
 }
 
 void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s) {
