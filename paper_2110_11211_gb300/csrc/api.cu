@@ -862,6 +862,9 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
 
   TRY(dalloc(h, &h->err, 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->err, 0, sizeof(ErrWord), s));
+  int* diag_cnt = nullptr;  // per tile row: updates of its diagonal tile seen (factorization)
+  TRY(dalloc(h, &diag_cnt, nrows));
+  SFCDD_CUDA_OK(cudaMemsetAsync(diag_cnt, 0, nrows * sizeof(int), s));
 
   // Algorithm 1, steps 9-10: coarse matrix and its FP64 factor, on a side
   // stream so that it overlaps the local factorization (the two are independent)
@@ -886,8 +889,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
       launch_assemble_coarse(g, pd, h->curve_code, h->invpad, cts, h->stored[P], h->ctiles, s2);
     });
     CoarseHook ch(pf2);
-    factor_tiles(cts, 0, 1, h->nt0, h->col_max_coarse.data(), h->ctiles, Store::F64, h->err, s2,
-                 &ch);
+    factor_tiles(cts, 0, 1, h->nt0, h->col_max_coarse.data(), h->ctiles, Store::F64, diag_cnt,
+                 h->err, s2, &ch, 4);
     pf2.run(SFCDD_K_COARSE_FACTOR, [&] {
       if (h->cb_coarse > 1)
         unitize_blocks(cts, h->nt0, h->cb_coarse, h->stored[P], h->ctiles, h->cut, xs, s2);
@@ -908,8 +911,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
       launch_assemble_local(g, pd, h->curve_code, h->invpad, h->ts, 0, P, h->max_ltiles,
                             work_tiles, compute_st, s);
     });
-    factor_tiles(h->ts, 0, P, h->max_nt, h->col_max_local.data(), work_tiles, compute_st, h->err,
-                 s, &pf);
+    factor_tiles(h->ts, 0, P, h->max_nt, h->col_max_local.data(), work_tiles, compute_st, diag_cnt,
+                 h->err, s, &pf, compute_st == Store::F64 ? 4 : 1);
   }
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
   void* work_ut = nullptr;
@@ -1001,6 +1004,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (xs) dfree(h, xs);
+  dfree(h, diag_cnt);
   dfree(h, keys);
   dfree(h, sort_tmp);
   int fi = 0;

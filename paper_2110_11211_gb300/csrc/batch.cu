@@ -701,6 +701,9 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   // local matrices and factors (Sec. 3.1), coarse matrices and FP64 factors (eq. csm)
   BTRY(balloc(b, &b->err, 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(b->err, 0, sizeof(ErrWord), s));
+  int* diag_cnt = nullptr;  // per tile row: updates of its diagonal tile seen (factorization)
+  BTRY(balloc(b, &diag_cnt, nrows));
+  SFCDD_CUDA_OK(cudaMemsetAsync(diag_cnt, 0, nrows * sizeof(int), s));
   const Store cst = b->st == Store::BF16 ? Store::F32 : b->st;
   const size_t esz = cst == Store::F64 ? 8 : 4;
   void* work_tiles = nullptr;
@@ -720,7 +723,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
     void after(int) override {}
   } nohook;
   factor_tiles(b->ts, 0, b->nlocal, b->max_nt_local, b->sky.col_max_local.data(), work_tiles, cst,
-               b->err, s, &nohook);
+               diag_cnt, b->err, s, &nohook);
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
   void* work_ut = nullptr;
   BTRY(balloc(b, (unsigned char**)&work_ut, b->sky.ltiles * TILE2 * esz));
@@ -747,7 +750,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
                                                                         b->ts, b->ctiles);
   }
   factor_tiles(b->ts, b->nlocal, nsub, b->max_nt_coarse, b->sky.col_max_coarse.data(), b->ctiles,
-               Store::F64, b->err, s, &nohook);
+               Store::F64, diag_cnt, b->err, s, &nohook);
   BTRY(balloc(b, &b->cut, b->sky.ctiles * TILE2));
   unitize_tiles(b->ts, b->nlocal, nsub, b->sky.max_ctiles, b->ctiles, b->cut, Store::F64, s);
   SFCDD_CUDA_OK(cudaGetLastError());

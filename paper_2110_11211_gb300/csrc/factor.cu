@@ -15,6 +15,8 @@
 // the same factor.  Per step k one launch factors the diagonal tiles (and
 // inverts the factor's diagonal block in place), one solves the panel tiles of
 // column k, one updates the trailing tiles they touch.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace sfcdd {
@@ -156,64 +158,148 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 
 // Diagonal tile k of every matrix with nt > k: Cholesky in shared memory, then
 // the inverse of the lower-triangular factor block replaces the tile.
-// Right-looking unblocked Cholesky with a 16 x 16 thread grid (each thread
-// updates rows ty + 16a, columns tx + 16b), reciprocal pivots instead of
-// divisions, then X = L^{-1} row by row with every column in parallel (four
-// threads split each dot product), which keeps the dependent FP64 chains short.
+// Blocked right-looking Cholesky with 16-column blocks.  FP64 instructions are
+// slow on this part (a warp instruction occupies a sub-partition's FP64 unit
+// for tens of cycles, masked lanes included), so the dependent work is kept
+// small and the bulk runs as dense 16-wide products on all eight warps:
+//   per block b: warps 0-3 factor the 16 x 16 diagonal block D_b (one element
+//   of its triangle per thread, reciprocal pivots, scaling applied once at the
+//   end) and invert it into X (row by row, 8 threads per dot product); then
+//   all warps form the panel L_pb = A_pb D_b^{-T} and update the trailing
+//   triangle with it.
+// The off-diagonal 16 x 16 blocks of X = L^{-1} follow by diagonals:
+// X_ab = -X_aa sum_{k=b}^{a-1} L_ak X_kb.
+constexpr int PB = 16;           // column block
+constexpr int PNB = TILE / PB;   // blocks per tile
+
+__device__ __forceinline__ void potrf_bar128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// lower-triangle index e -> (i, l), i >= l
+__device__ __forceinline__ void tri_rc(int e, int& i, int& l) {
+  int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while ((t + 1) * (t + 2) / 2 <= e) ++t;
+  while (t * (t + 1) / 2 > e) --t;
+  i = t;
+  l = e - t * (t + 1) / 2;
+}
+
+// The whole factorization + inversion of the tile at tp by one CTA (FB threads),
+// in dsm (2 (TILE + 1)^2 elements of T).  The tile is read through L2, so it
+// may have been written by other CTAs of the same launch (after a fence).
+template <class T>
+__device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m) {
+  T (*L)[TILE + 1] = reinterpret_cast<T (*)[TILE + 1]>(dsm);
+  T (*X)[TILE + 1] = L + TILE;
+  T* rinv = &X[TILE][0];  // TILE reciprocal pivots (row TILE of X, TILE + 1 entries)
+  const int tid = threadIdx.x;
+  for (int e = tid; e < TILE2; e += FB) L[e / TILE][e % TILE] = __ldcg(tp + e);
+  for (int e = tid; e < TILE2; e += FB) X[e / TILE][e % TILE] = T(0);
+  // my elements of a 16 x 16 lower triangle (136 of them; threads < 128)
+  int di0 = 0, dl0 = 0, di1 = -1, dl1 = -1;
+  if (tid < 128) {
+    tri_rc(tid, di0, dl0);
+    if (tid + 128 < PB * (PB + 1) / 2) tri_rc(tid + 128, di1, dl1);
+  }
+  __syncthreads();
+  for (int b = 0; b < PNB; ++b) {
+    const int o = PB * b;
+    if (tid < 128) {
+      // factor D_b in place (column scaling deferred): d_c -> rinv, trailing update
+      for (int c = 0; c < PB; ++c) {
+        T d = L[o + c][o + c];
+        if (!(d > T(0))) {
+          if (tid == 0 && atomicCAS(&err->code, 0, (int)SFCDD_ERR_NOT_SPD) == 0) err->index = m;
+          d = T(1);
+        }
+        const T r = rsqrt(d);
+        const T dinv = r * r;
+        if (tid == 0) rinv[o + c] = r;
+        if (dl0 > c) L[o + di0][o + dl0] -= L[o + di0][o + c] * (L[o + dl0][o + c] * dinv);
+        if (dl1 > c) L[o + di1][o + dl1] -= L[o + di1][o + c] * (L[o + dl1][o + c] * dinv);
+        potrf_bar128();
+      }
+      // deferred scaling of the strictly lower part
+      if (di0 > dl0) L[o + di0][o + dl0] *= rinv[o + dl0];
+      if (di1 > dl1) L[o + di1][o + dl1] *= rinv[o + dl1];
+      potrf_bar128();
+      // D_b^{-1}: row i needs rows < i; column c = tid / 8, eight threads per dot
+      const int c = tid >> 3, part = tid & 7;
+      for (int i = 0; i < PB; ++i) {
+        T sacc = T(0);
+        if (c < i)
+          for (int kk = c + part; kk < i; kk += 8) sacc += L[o + i][o + kk] * X[o + kk][o + c];
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+        if (part == 0 && c <= i) X[o + i][o + c] = c == i ? rinv[o + i] : -sacc * rinv[o + i];
+        potrf_bar128();
+      }
+    }
+    __syncthreads();
+    const int o2 = o + PB, rest = TILE - o2;  // rows below the block
+    if (rest > 0) {
+      // panel L_pc = sum_{k <= c} A_pk X_ck  (D^{-T} is X^T), written after all reads
+      T pv[3];
+      int np = 0;
+      for (int e = tid; e < rest * PB; e += FB, ++np) {
+        const int p = o2 + e / PB, cc = e % PB;
+        T acc = T(0);
+        for (int kk = 0; kk <= cc; ++kk) acc += L[p][o + kk] * X[o + cc][o + kk];
+        pv[np] = acc;
+      }
+      __syncthreads();
+      np = 0;
+      for (int e = tid; e < rest * PB; e += FB, ++np) L[o2 + e / PB][o + e % PB] = pv[np];
+      __syncthreads();
+      // trailing triangle A_pq -= sum_k L_pk L_qk (p >= q >= o2)
+      for (int e = tid; e < rest * (rest + 1) / 2; e += FB) {
+        int pi, qi;
+        tri_rc(e, pi, qi);
+        const int p = o2 + pi, q = o2 + qi;
+        T acc = T(0);
+#pragma unroll
+        for (int kk = 0; kk < PB; ++kk) acc += L[p][o + kk] * L[q][o + kk];
+        L[p][q] -= acc;
+      }
+      __syncthreads();
+    }
+  }
+  // off-diagonal blocks of X by diagonals d = a - b; S_ab is staged in the
+  // (zero) upper block (b, a) of X
+  for (int d = 1; d < PNB; ++d) {
+    const int nblk = PNB - d;
+    for (int e = tid; e < nblk * PB * PB; e += FB) {
+      const int bb = e / (PB * PB), a = bb + d;
+      const int i = (e / PB) % PB, j = e % PB;
+      T acc = T(0);
+      for (int k = bb; k < a; ++k)
+        for (int kk = 0; kk < PB; ++kk) acc += L[PB * a + i][PB * k + kk] * X[PB * k + kk][PB * bb + j];
+      X[PB * bb + i][PB * a + j] = acc;  // S_ab into the upper block (b, a)
+    }
+    __syncthreads();
+    for (int e = tid; e < nblk * PB * PB; e += FB) {
+      const int bb = e / (PB * PB), a = bb + d;
+      const int i = (e / PB) % PB, j = e % PB;
+      T acc = T(0);
+      for (int kk = 0; kk <= i; ++kk) acc += X[PB * a + i][PB * a + kk] * X[PB * bb + kk][PB * a + j];
+      X[PB * a + i][PB * bb + j] = -acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < TILE2; e += FB) {
+    const int r = e / TILE, c = e % TILE;
+    tp[e] = c > r ? T(0) : X[r][c];
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(FB) k_potrf(TileSetDev ts, int mat0, int k, T* __restrict__ tiles,
                                               ErrWord* err) {
   extern __shared__ __align__(16) unsigned char dsm_potrf[];
-  T (*L)[TILE + 1] = reinterpret_cast<T (*)[TILE + 1]>(dsm_potrf);
-  T (*X)[TILE + 1] = L + TILE;
-  T* rinv = &X[TILE][0];  // TILE reciprocal pivots (row TILE of X, TILE + 1 entries)
   const int m = mat0 + blockIdx.x;
   if (ts.nt[m] <= k) return;
   const int fb = ts.vbase[m] / TILE;
-  T* tp = tiles + tile_at(ts, ts.tbase[m], fb, k, k);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < TILE2; e += FB) L[e / TILE][e % TILE] = tp[e];
-  __syncthreads();
-  const int ty = tid >> 4, tx = tid & 15;
-  for (int j = 0; j < TILE; ++j) {
-    if (tid == 0) {
-      T dj = L[j][j];
-      if (!(dj > T(0))) {
-        if (atomicCAS(&err->code, 0, (int)SFCDD_ERR_NOT_SPD) == 0) err->index = m;
-        dj = T(1);
-      }
-      const T piv = sqrt(dj);
-      L[j][j] = piv;
-      rinv[j] = T(1) / piv;
-    }
-    __syncthreads();
-    if (tid > j && tid < TILE) L[tid][j] *= rinv[j];
-    __syncthreads();
-#pragma unroll
-    for (int aa = 0; aa < TILE / 16; ++aa) {
-      const int i = ty + 16 * aa;
-      if (i <= j) continue;
-      const T lij = L[i][j];
-#pragma unroll
-      for (int bb = 0; bb < TILE / 16; ++bb) {
-        const int l = tx + 16 * bb;
-        if (l > j && l <= i) L[i][l] -= lij * L[l][j];
-      }
-    }
-    __syncthreads();
-  }
-  // X = L^{-1}: row i needs rows < i; columns c <= i are independent
-  const int c = tid >> 2, part = tid & 3;
-  for (int i = 0; i < TILE; ++i) {
-    T sacc = T(0);
-    if (c < i)
-      for (int kk = c + part; kk < i; kk += 4) sacc += L[i][kk] * X[kk][c];
-    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-    sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-    if (part == 0) X[i][c] = c > i ? T(0) : ((c == i ? T(1) : T(0)) - sacc) * rinv[i];
-    __syncthreads();
-  }
-  for (int e = tid; e < TILE2; e += FB) tp[e] = X[e / TILE][e % TILE];
+  potrf_tile<T>(tiles + tile_at(ts, ts.tbase[m], fb, k, k), dsm_potrf, err, m);
 }
 
 // C = X * Y^T on 64x64 tiles (X, Y row-major in global), each thread a 4x4 block.
@@ -241,9 +327,55 @@ __device__ __forceinline__ void mma_4x4(T (&acc)[4][4], T (*Xt)[TILE + 4], T (*Y
   }
 }
 
-// Panel: L_ik = A_ik * Linv_kk^T for the stored tiles of column k below the
-// diagonal.  grid = (max panel rows, nmat)
+// Rows [r_lo, r_lo + n) of a row-major tile into columns of a transposed
+// shared array (dst[s][r] = src[r][s]).
 template <class T>
+__device__ __forceinline__ void load_rows_transposed(T (*dst)[TILE + 4], const T* __restrict__ src,
+                                                     int r_lo, int n) {
+  for (int e = threadIdx.x; e < n * TILE; e += FB) {
+    const int r = r_lo + e / TILE, c = e % TILE;
+    dst[c][r] = src[r * TILE + c];
+  }
+}
+
+// Output rows of one CTA of a tile product X Y^T: with SPLIT = 1 the whole tile,
+// each thread a 4 x 4 block; with SPLIT = 4 a 16-row slab (rows 16 slab ..),
+// each thread 1 x 4.  Splitting puts the FP64 work of one tile on four SMs.
+template <int SPLIT>
+struct SlabMap {
+  static constexpr int RA = 4 / SPLIT;  // rows per thread
+  int r0, c0;
+  __device__ SlabMap(int slab) {
+    if (SPLIT == 1) {
+      r0 = (threadIdx.x / 16) * 4;
+    } else {
+      r0 = 16 * slab + threadIdx.x / 16;
+    }
+    c0 = (threadIdx.x % 16) * 4;
+  }
+};
+
+template <class T, int RA>
+__device__ __forceinline__ void mma_rows(T (&acc)[RA][4], T (*Xt)[TILE + 4], T (*Yt)[TILE + 4],
+                                         int r0, int c0) {
+#pragma unroll 8
+  for (int s = 0; s < TILE; ++s) {
+    T xv[RA], yv[4];
+#pragma unroll
+    for (int i = 0; i < RA; ++i) xv[i] = Xt[s][r0 + i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) yv[i] = Yt[s][c0 + i];
+#pragma unroll
+    for (int i = 0; i < RA; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[i][jj] += xv[i] * yv[jj];
+  }
+}
+
+// Panel: L_ik = A_ik * Linv_kk^T for the stored tiles of column k below the
+// diagonal.  grid = (max panel rows * SPLIT, nmat); a CTA reads and writes
+// only the rows of its slab of A_ik.
+template <class T, int SPLIT>
 __global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int k, T* __restrict__ tiles) {
   extern __shared__ __align__(16) unsigned char dsm_trsm[];
   T (*At)[TILE + 4] = reinterpret_cast<T (*)[TILE + 4]>(dsm_trsm);
@@ -253,94 +385,134 @@ __global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int k, T* 
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
   const int c0p = ts.colptr[fb + k];
-  if ((int)blockIdx.x >= ts.colptr[fb + k + 1] - c0p) return;
-  const int i = ts.colidx[c0p + blockIdx.x];
+  const int tix = blockIdx.x / SPLIT, slab = blockIdx.x % SPLIT;
+  if (tix >= ts.colptr[fb + k + 1] - c0p) return;
+  const int i = ts.colidx[c0p + tix];
   const long long tb = ts.tbase[m];
   T* aik = tiles + tile_at(ts, tb, fb, i, k);
   const T* lkk = tiles + tile_at(ts, tb, fb, k, k);
-  load_transposed<T>(At, aik);
+  load_rows_transposed<T>(At, aik, (TILE / SPLIT) * slab, TILE / SPLIT);
   load_transposed<T>(Bt, lkk);
   __syncthreads();
-  const int r0 = (threadIdx.x / 16) * 4, c0 = (threadIdx.x % 16) * 4;
-  T acc[4][4];
+  const SlabMap<SPLIT> mp(slab);
+  constexpr int RA = SlabMap<SPLIT>::RA;
+  T acc[RA][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  mma_4x4<T>(acc, At, Bt, r0, c0);
+  mma_rows<T, RA>(acc, At, Bt, mp.r0, mp.c0);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) aik[(r0 + a) * TILE + c0 + b] = acc[a][b];
+    for (int b = 0; b < 4; ++b) aik[(mp.r0 + a) * TILE + mp.c0 + b] = acc[a][b];
 }
 
 // Trailing update A_ij -= L_ik L_jk^T for the stored panel tiles i >= j of
-// column k.  grid = (max pairs, nmat)
-template <class T>
-__global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* __restrict__ tiles) {
+// column k, and the factorization of diagonal tile k+1 (step k+1's potrf) as
+// soon as its last update is in: the last of the SPLIT CTAs updating tile
+// (k+1, k+1) (counted in diag_cnt[fb + k + 1], zero before the factorization)
+// factors it, or, when column k does not reach row k+1, the launch's last CTA
+// does.  grid = (max pairs * SPLIT + 1, nmat)
+template <class T, int SPLIT>
+__global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* __restrict__ tiles,
+                                             int* __restrict__ diag_cnt, ErrWord* err) {
   extern __shared__ __align__(16) unsigned char dsm_syrk[];
   T (*Xt)[TILE + 4] = reinterpret_cast<T (*)[TILE + 4]>(dsm_syrk);
   T (*Yt)[TILE + 4] = Xt + TILE;
+  __shared__ int s_last;
   const int m = mat0 + blockIdx.y;
   const int nt = ts.nt[m];
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
   const int c0p = ts.colptr[fb + k];
   const int cnt = ts.colptr[fb + k + 1] - c0p;
-  if ((int)blockIdx.x >= cnt * (cnt + 1) / 2) return;
-  int ii, jj;
-  tri_decode(blockIdx.x, ii, jj);
-  const int i = ts.colidx[c0p + ii], j = ts.colidx[c0p + jj];
   const long long tb = ts.tbase[m];
+  if ((int)blockIdx.x == (int)gridDim.x - 1) {
+    // column k does not reach row k+1: tile (k+1, k+1) is final already
+    if (k + 1 < nt && ts.kmin[fb + k + 1] > k)
+      potrf_tile<T>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_syrk, err, m);
+    return;
+  }
+  const int tix = blockIdx.x / SPLIT, slab = blockIdx.x % SPLIT;
+  if (tix >= cnt * (cnt + 1) / 2) return;
+  int ii, jj;
+  tri_decode(tix, ii, jj);
+  const int i = ts.colidx[c0p + ii], j = ts.colidx[c0p + jj];
   const T* lik = tiles + tile_at(ts, tb, fb, i, k);
   const T* ljk = tiles + tile_at(ts, tb, fb, j, k);
   T* aij = tiles + tile_at(ts, tb, fb, i, j);
-  load_transposed<T>(Xt, lik);
+  load_rows_transposed<T>(Xt, lik, (TILE / SPLIT) * slab, TILE / SPLIT);
   load_transposed<T>(Yt, ljk);
   __syncthreads();
-  const int r0 = (threadIdx.x / 16) * 4, c0 = (threadIdx.x % 16) * 4;
-  T acc[4][4];
+  const SlabMap<SPLIT> mp(slab);
+  constexpr int RA = SlabMap<SPLIT>::RA;
+  T acc[RA][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  mma_4x4<T>(acc, Xt, Yt, r0, c0);
+  mma_rows<T, RA>(acc, Xt, Yt, mp.r0, mp.c0);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) aij[(r0 + a) * TILE + c0 + b] -= acc[a][b];
+    for (int b = 0; b < 4; ++b) aij[(mp.r0 + a) * TILE + mp.c0 + b] -= acc[a][b];
+  if (i == k + 1 && j == k + 1) {
+    __threadfence();
+    __syncthreads();  // every slab row of this CTA is written (and the smem reads done)
+    if (threadIdx.x == 0) s_last = atomicAdd(&diag_cnt[fb + k + 1], 1) == SPLIT - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      potrf_tile<T>(aij, dsm_syrk, err, m);
+    }
+  }
 }
 
-template <class T>
+template <class T, int SPLIT>
 static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
-                           T* tiles, ErrWord* err, cudaStream_t s, LaunchHook* hook) {
+                           T* tiles, int* diag_cnt, ErrWord* err, cudaStream_t s, LaunchHook* hook) {
   const int sm_potrf = (2 * TILE + 1) * (TILE + 1) * (int)sizeof(T);
-  const int sm_gemm = 2 * TILE * (TILE + 4) * (int)sizeof(T);
+  const int sm_gemm = std::max(2 * TILE * (TILE + 4), (2 * TILE + 1) * (TILE + 1)) * (int)sizeof(T);
   cudaFuncSetAttribute(k_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_potrf);
-  cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_gemm);
-  cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_gemm);
+  cudaFuncSetAttribute(k_trsm<T, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_gemm);
+  cudaFuncSetAttribute(k_syrk<T, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_gemm);
+  // step k: panel (trsm), then trailing update fused with the factorization of
+  // diagonal tile k+1; only step 0 and steps without a panel launch potrf alone
+  hook->before(SFCDD_K_POTRF);
+  k_potrf<T><<<nmat, FB, sm_potrf, s>>>(ts, mat0, 0, tiles, err);
+  hook->after(SFCDD_K_POTRF);
   for (int k = 0; k < max_nt; ++k) {
-    hook->before(SFCDD_K_POTRF);
-    k_potrf<T><<<nmat, FB, sm_potrf, s>>>(ts, mat0, k, tiles, err);
-    hook->after(SFCDD_K_POTRF);
     const int rows = col_max[k];
     if (rows > 0) {
       hook->before(SFCDD_K_TRSM);
-      k_trsm<T><<<dim3(rows, nmat), FB, sm_gemm, s>>>(ts, mat0, k, tiles);
+      k_trsm<T, SPLIT><<<dim3(rows * SPLIT, nmat), FB, sm_gemm, s>>>(ts, mat0, k, tiles);
       hook->after(SFCDD_K_TRSM);
       hook->before(SFCDD_K_SYRK);
-      k_syrk<T><<<dim3(rows * (rows + 1) / 2, nmat), FB, sm_gemm, s>>>(ts, mat0, k, tiles);
+      k_syrk<T, SPLIT><<<dim3(rows * (rows + 1) / 2 * SPLIT + 1, nmat), FB, sm_gemm, s>>>(
+          ts, mat0, k, tiles, diag_cnt, err);
       hook->after(SFCDD_K_SYRK);
+    } else if (k + 1 < max_nt) {
+      hook->before(SFCDD_K_POTRF);
+      k_potrf<T><<<nmat, FB, sm_potrf, s>>>(ts, mat0, k + 1, tiles, err);
+      hook->after(SFCDD_K_POTRF);
     }
   }
 }
 
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
-                  void* tiles, Store st, ErrWord* err, cudaStream_t s, LaunchHook* hook) {
-  if (st == Store::F64)
-    factor_tiles_t<double>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, err, s, hook);
-  else
-    factor_tiles_t<float>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, err, s, hook);
+                  void* tiles, Store st, int* diag_cnt, ErrWord* err, cudaStream_t s,
+                  LaunchHook* hook, int split) {
+  if (st == Store::F64) {
+    if (split == 4)
+      factor_tiles_t<double, 4>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, diag_cnt, err, s,
+                                hook);
+    else
+      factor_tiles_t<double, 1>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, diag_cnt, err, s,
+                                hook);
+  } else {
+    factor_tiles_t<float, 1>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, diag_cnt, err, s, hook);
+  }
 }
 
 // A 64 x 64 row-major tile into a padded shared array, rows kept as rows.

@@ -308,8 +308,13 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 // in place, over the stored tiles only; diagonal slots end up holding the
 // inverse of the factor's diagonal block.  col_max[K] = largest number of rows
 // I > K with kmin[I] <= K over the matrices (sizes the step-K launches).
+// split = 4 (FP64 only) computes every panel and trailing tile product as four
+// 16-row slabs on four CTAs (for few, long factorizations such as the coarse one).
+// diag_cnt: one int per tile row of ts (indexed fb + I), zero on entry; the
+// trailing update of step k factors diagonal tile k+1 once its last update is in.
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
-                  void* tiles, Store st, ErrWord* err, cudaStream_t s, LaunchHook* hook);
+                  void* tiles, Store st, int* diag_cnt, ErrWord* err, cudaStream_t s,
+                  LaunchHook* hook, int split = 1);
 // Substitution form of the factors of matrices [mat0, mat0+nmat) (after
 // factor_tiles, same precision): every stored off-diagonal tile L_IK becomes
 // Lh_IK = L_IK L_KK^{-1} in place, ut receives Lh_IK^T in the same slot and
