@@ -319,11 +319,11 @@ def run_ours(args):
             e2e_ms.append(1e3 * (t1 - t0))
     e2e = max_over_ranks(world, statistics.mean(e2e_ms))
 
-    # mixed-precision variants of the same workload
+    # mixed-precision variants of the same workload, and the balanced operator
     variants = {}
     if not args.no_variants and rank == 0:
-        for vp in ("fp32", "bf16"):
-            if vp == prec:
+        for vp, var in (("fp32", "additive"), ("bf16", "additive"), (prec, "balanced")):
+            if vp == prec and var == "additive":
                 continue
             times = []
             for k in range(3):
@@ -331,7 +331,7 @@ def run_ours(args):
                 a0 = torch.cuda.Event(enable_timing=True)
                 a1 = torch.cuda.Event(enable_timing=True)
                 a0.record(stream)
-                s = Solver(levels, P, gamma, precision=vp, coeffs=coeffs)
+                s = Solver(levels, P, gamma, precision=vp, coeffs=coeffs, variant=var)
                 uv, stv = s.solve(f, rtol=args.rtol)
                 s.close()
                 a1.record(stream)
@@ -339,7 +339,8 @@ def run_ours(args):
                 if k >= 1:
                     times.append(a0.elapsed_time(a1))
             err = float(torch.linalg.norm(uv - u64) / torch.linalg.norm(u64))
-            variants[vp] = {"ms": round(statistics.mean(times), 2), "iters": stv.iters,
+            key = vp if var == "additive" else f"{var}_{vp}"
+            variants[key] = {"ms": round(statistics.mean(times), 2), "iters": stv.iters,
                             "setup_ms": round(stv.setup_ms, 2), "solve_ms": round(stv.solve_ms, 2),
                             "applies_per_s": round(stv.iters / (stv.solve_ms / 1e3), 1),
                             "rel_diff_vs_fp64_solution": err, "true_rel_res": stv.true_rel_res}

@@ -358,11 +358,16 @@ struct sfcdd_handle {
   int nsub_local = 1, nsub_coarse = 4;
   int cb_coarse = 4;  // tiles per unit diagonal block of the coarse substitution form
   long long fwd_tiles_l = 0, bwd_tiles_l = 0, fwd_tiles_c = 0, bwd_tiles_c = 0;
-  // substitution
-  TrsvWork *work_f = nullptr, *work_b = nullptr;
-  int nwork = 0;
-  unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
+  // substitution work lists (each with its own ticket counters: the items of a
+  // launch map to tickets modulo the list length): the variant's matrices, and
+  // for the balanced variant the local matrices and the coarse matrix alone
+  struct WorkList {
+    TrsvWork *f = nullptr, *b = nullptr;
+    int n = 0;
+    unsigned long long *tf = nullptr, *tb = nullptr;
+  } lists[3];
   double *ybuf = nullptr, *dbuf = nullptr, *zcbuf = nullptr;
+  double* bal[4] = {nullptr, nullptr, nullptr, nullptr};  // balanced apply: w, g - A w, t, v
   long long vtotal = 0;
   // PCG
   double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *qv = nullptr, *z = nullptr,
@@ -466,7 +471,10 @@ struct CoarseHook : LaunchHook {
   void after(int) override { p.after(SFCDD_K_COARSE_FACTOR); }
 };
 
-TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalars* sc) {
+enum { LIST_MAIN = 0, LIST_LOCAL = 1, LIST_COARSE = 2 };
+
+TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalars* sc,
+                   int list = LIST_MAIN) {
   TrsvArgs a{};
   a.ts = h->ts;
   a.md = h->d_md;
@@ -480,9 +488,10 @@ TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalar
   a.y = h->ybuf;
   a.dout = h->dbuf;
   a.zc = h->zcbuf;
-  a.work = fwd ? h->work_f : h->work_b;
-  a.nwork = h->nwork;
-  a.ticket = fwd ? h->ticket_f : h->ticket_b;
+  const auto& wl = h->lists[list];
+  a.work = fwd ? wl.f : wl.b;
+  a.nwork = wl.n;
+  a.ticket = fwd ? wl.tf : wl.tb;
   a.err = h->err;
   a.sc = sc;
   return a;
@@ -516,24 +525,60 @@ int prolong_mode(const sfcdd_handle* h) {
   return 0;
 }
 
+// One substitution pair (forward, backward) over a work list; local right-hand
+// sides sliced from g, the coarse one from g0.
+void enqueue_solves(sfcdd_handle* h, Prof& pf, const double* g, PcgScalars* sc, int list) {
+  cudaStream_t s = pf.s;
+  TrsvArgs af = trsv_args(h, true, g, sc, list);
+  TrsvArgs ab = trsv_args(h, false, g, sc, list);
+  pf.run(SFCDD_K_TRSV_FWD, [&] { launch_trsv_fwd(af, h->st, s); });
+  pf.run(SFCDD_K_TRSV_BWD, [&] { launch_trsv_bwd(ab, h->st, s); });
+}
+
+// w = F g = R_0^T A_0^{-1} R_0 g
+void enqueue_coarse_correction(sfcdd_handle* h, Prof& pf, const double* g, double* w,
+                               PcgScalars* sc) {
+  cudaStream_t s = pf.s;
+  pf.run(SFCDD_K_RESTRICT, [&] { launch_restrict(h->pd, g, h->g0, sc, s); });
+  enqueue_solves(h, pf, g, sc, LIST_COARSE);
+  pf.run(SFCDD_K_PROLONG,
+         [&] { launch_prolong(h->pd, h->ts, 2, h->dbuf, g, w, sc, h->ws, s, false); });
+}
+
+// Balanced variant (eq. balSW): z = G^T C_(1) G g + F g with G = I - A F and
+// G^T = I - F A (A, F symmetric), C_(1) the weighted one-level operator:
+//   w = F g,  t = C_(1) (g - A w),  v = F A t,  z = t - v + w.
+void enqueue_apply_balanced(sfcdd_handle* h, Prof& pf, const double* g, double* z,
+                            PcgScalars* sc) {
+  cudaStream_t s = pf.s;
+  double *w = h->bal[0], *gg = h->bal[1], *t = h->bal[2], *v = h->bal[3];
+  enqueue_coarse_correction(h, pf, g, w, sc);
+  pf.run(SFCDD_K_STENCIL,
+         [&] { launch_residual(h->g, h->curve_code, h->invpad, g, w, gg, sc, h->ws, s); });
+  enqueue_solves(h, pf, gg, sc, LIST_LOCAL);
+  pf.run(SFCDD_K_PROLONG,
+         [&] { launch_prolong(h->pd, h->ts, 1, h->dbuf, gg, t, sc, h->ws, s, false); });
+  pf.run(SFCDD_K_STENCIL,
+         [&] { launch_stencil(h->g, h->curve_code, h->invpad, t, h->tmp2, 0, sc, h->ws, s); });
+  enqueue_coarse_correction(h, pf, h->tmp2, v, sc);
+  pf.run(SFCDD_K_VECTOR, [&] { launch_combine_bal(h->N, t, v, w, g, z, sc, h->ws, s); });
+}
+
 // z = C^{-1} g in curve order.  With sc != null the prolongation finalizes r^T z
 // (PCG) and every kernel returns early once the solve has converged.
 void enqueue_apply(sfcdd_handle* h, Prof& pf, const double* g, double* z, PcgScalars* sc) {
   cudaStream_t s = pf.s;
+  if (h->variant == SFCDD_BALANCED) {
+    enqueue_apply_balanced(h, pf, g, z, sc);
+    return;
+  }
   const bool coarse = h->variant != SFCDD_ONE_LEVEL;
   if (coarse) pf.run(SFCDD_K_RESTRICT, [&] { launch_restrict(h->pd, g, h->g0, sc, s); });
-  TrsvArgs af = trsv_args(h, true, g, sc);
-  TrsvArgs ab = trsv_args(h, false, g, sc);
-  pf.run(SFCDD_K_TRSV_FWD, [&] { launch_trsv_fwd(af, h->st, s); });
-  pf.run(SFCDD_K_TRSV_BWD, [&] { launch_trsv_bwd(ab, h->st, s); });
+  enqueue_solves(h, pf, g, sc, LIST_MAIN);
   pf.run(SFCDD_K_PROLONG, [&] {
     launch_prolong(h->pd, h->ts, prolong_mode(h), h->dbuf, g, z, sc, h->ws, s);
   });
 }
-
-// Balanced variant (eq. balSW): z = (I - F A) C1 (g - A F g) + F g, with
-// F = R_0^T A_0^{-1} R_0 and C1 the weighted one-level operator.
-// Not part of the graph-captured additive path; built on the same kernels.
 
 void enqueue_iteration(sfcdd_handle* h, Prof& pf) {
   cudaStream_t s = pf.s;
@@ -612,7 +657,6 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   if (h->precision < 0 || h->precision > 2 || h->variant < 0 || h->variant > 3 ||
       h->weighting < 0 || h->weighting > 1)
     return SFCDD_ERR_INVALID_ARG;
-  if (h->variant == SFCDD_BALANCED) return SFCDD_ERR_UNSUPPORTED;
   h->nsub_local = o.slabs_local == 0 ? 1 : o.slabs_local;
   h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
   if ((h->nsub_local != 1 && h->nsub_local != 2) || (h->nsub_coarse != 1 && h->nsub_coarse != 4))
@@ -950,25 +994,38 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   }
 
   // substitution work lists: tile rows in dependency-safe order
-  std::vector<TrsvWork> wf, wb;
   {
-    std::vector<char> include(P + 1, 1);
-    if (h->variant == SFCDD_COARSE_ONLY)
-      for (int m = 0; m < P; ++m) include[m] = 0;
-    if (h->variant == SFCDD_ONE_LEVEL) include[P] = 0;
     std::vector<int> nsub(P + 1, h->nsub_local);
     nsub[P] = h->nsub_coarse;
-    build_worklists(h->h_nt, include, nsub, wf, wb);
+    for (int li = 0; li < 3; ++li) {
+      std::vector<char> include(P + 1, 1);
+      if (li == LIST_MAIN) {
+        if (h->variant == SFCDD_COARSE_ONLY)
+          for (int m = 0; m < P; ++m) include[m] = 0;
+        if (h->variant == SFCDD_ONE_LEVEL) include[P] = 0;
+      } else {
+        if (h->variant != SFCDD_BALANCED) continue;
+        if (li == LIST_LOCAL) include[P] = 0;
+        else
+          for (int m = 0; m < P; ++m) include[m] = 0;
+      }
+      std::vector<TrsvWork> wf, wb;
+      build_worklists(h->h_nt, include, nsub, wf, wb);
+      auto& wl = h->lists[li];
+      wl.n = (int)wf.size();
+      TRY(dalloc(h, &wl.f, wl.n));
+      TRY(dalloc(h, &wl.b, wl.n));
+      SFCDD_CUDA_OK(cudaMemcpyAsync(wl.f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+      SFCDD_CUDA_OK(cudaMemcpyAsync(wl.b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+      TRY(dalloc(h, &wl.tf, 1));
+      TRY(dalloc(h, &wl.tb, 1));
+      SFCDD_CUDA_OK(cudaMemsetAsync(wl.tf, 0, sizeof(unsigned long long), s));
+      SFCDD_CUDA_OK(cudaMemsetAsync(wl.tb, 0, sizeof(unsigned long long), s));
+      SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
+    }
   }
-  h->nwork = (int)wf.size();
-  TRY(dalloc(h, &h->work_f, h->nwork));
-  TRY(dalloc(h, &h->work_b, h->nwork));
-  SFCDD_CUDA_OK(cudaMemcpyAsync(h->work_f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-  SFCDD_CUDA_OK(cudaMemcpyAsync(h->work_b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-  TRY(dalloc(h, &h->ticket_f, 1));
-  TRY(dalloc(h, &h->ticket_b, 1));
-  SFCDD_CUDA_OK(cudaMemsetAsync(h->ticket_f, 0, sizeof(unsigned long long), s));
-  SFCDD_CUDA_OK(cudaMemsetAsync(h->ticket_b, 0, sizeof(unsigned long long), s));
+  if (h->variant == SFCDD_BALANCED)
+    for (int k = 0; k < 4; ++k) TRY(dalloc(h, &h->bal[k], N));
   TRY(dalloc(h, &h->ybuf, h->vtotal));
   TRY(dalloc(h, &h->dbuf, h->vtotal));
   TRY(dalloc(h, &h->zcbuf, h->vtotal));

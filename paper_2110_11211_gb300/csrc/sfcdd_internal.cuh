@@ -267,8 +267,17 @@ void launch_update_xr(int n, double* x, double* r, const double* p, const double
                       PcgScalars* sc, ReduceWs ws, cudaStream_t s);
 void launch_restrict(const PartDev& pd, const double* r, double* g0, const PcgScalars* sc,
                      cudaStream_t s);
+// mode 0 additive, 1 one level, 2 coarse only.  With sc and dot: fused r^T z
+// PCG finalize; with sc and !dot: only the early return after convergence.
 void launch_prolong(const PartDev& pd, const TileSetDev& ts, int mode, const double* dvec,
-                    const double* r, double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
+                    const double* r, double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s,
+                    bool dot = true);
+// y = b - A x (sc: early return after convergence)
+void launch_residual(const GridDev& g, const unsigned* code, const int* invpad, const double* b,
+                     const double* x, double* y, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
+// z = t - v + w (eq. balSW from its parts), with sc: fused r^T z PCG finalize
+void launch_combine_bal(int n, const double* t, const double* v, const double* w, const double* r,
+                        double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
 void launch_update_p(int n, const double* z, double* p, const PcgScalars* sc, cudaStream_t s);
 void launch_init_pcg(int n, const double* b, double* x, double* r, PcgScalars* sc, ReduceWs ws,
                      double rtol, int flexible, cudaStream_t s);

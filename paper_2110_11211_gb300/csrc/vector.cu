@@ -74,7 +74,8 @@ __device__ __forceinline__ void reduce_finalize(double (&v)[K], ReduceWs ws, Fin
 // Stencil y = A x in curve order.  Neighbours: the point's packed code gives
 // its coordinates; code +- 2^{off_j} is the axis-j neighbour, whose curve
 // position comes from invpad.  MODE 0: y = A x; 1: also p^T A p -> alpha;
-// 2: y = b - A x and ||y|| -> true relative residual.
+// 2: y = b - A x and ||y|| -> true relative residual; 3: y = b - A x.  MODE 0
+// and 3 with sc != null return once the solve has converged.
 template <int D, int MODE>
 __global__ void __launch_bounds__(VB) k_stencil(GridDev g, const unsigned* __restrict__ code,
                                                 const int* __restrict__ invpad,
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(VB) k_stencil(GridDev g, const unsigned* __res
                                                 double* __restrict__ y,
                                                 const double* __restrict__ b, PcgScalars* sc,
                                                 ReduceWs ws) {
-  if (MODE == 1 && sc->done) return;
+  if ((MODE == 1 || ((MODE == 0 || MODE == 3) && sc)) && sc->done) return;
   double acc = 0.0;
   const int stride = gridDim.x * VB;
   for (int p = blockIdx.x * VB + threadIdx.x; p < g.N; p += stride) {
@@ -91,6 +92,8 @@ __global__ void __launch_bounds__(VB) k_stencil(GridDev g, const unsigned* __res
     if (MODE == 2) {
       v = b[p] - v;
       acc += v * v;
+    } else if (MODE == 3) {
+      v = b[p] - v;
     } else if (MODE == 1) {
       acc += xc * v;
     }
@@ -133,6 +136,11 @@ void launch_stencil(const GridDev& g, const unsigned* code, const int* invpad, c
     stencil_dispatch<1>(g, code, invpad, x, y, nullptr, sc, ws, s);
   else
     stencil_dispatch<0>(g, code, invpad, x, y, nullptr, sc, ws, s);
+}
+
+void launch_residual(const GridDev& g, const unsigned* code, const int* invpad, const double* b,
+                     const double* x, double* y, PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
+  stencil_dispatch<3>(g, code, invpad, x, y, b, sc, ws, s);
 }
 
 void launch_true_residual(const GridDev& g, const unsigned* code, const int* invpad,
@@ -209,13 +217,29 @@ void launch_restrict(const PartDev& pd, const double* r, double* g0, const PcgSc
 // per curve position from the (at most min(2g+3, P)) subdomains whose range can
 // contain it; fused with r^T z (and r^T z_old for the flexible beta).
 // mode: 0 additive two-level, 1 one level, 2 coarse only.  DOT: PCG finalize.
+// The PCG finalize of r^T z: beta (Hestenes-Stiefel, or Polak-Ribiere for the
+// flexible variant) from t = {r^T z_new, r^T z_old}.
+__device__ __forceinline__ void finalize_rz(PcgScalars* sc, const double* t) {
+  const double rz_new = t[0];
+  if (sc->iter == 0) {
+    sc->beta = 0.0;
+  } else if (sc->flexible) {
+    sc->beta = (rz_new - t[1]) / sc->rz;
+  } else {
+    sc->beta = rz_new / sc->rz;
+  }
+  sc->rz_old = t[1];
+  sc->rz = rz_new;
+}
+
+// sc != null without DOT: only the early return once the solve has converged.
 template <bool DOT>
 __global__ void __launch_bounds__(VB) k_prolong(PartDev pd, TileSetDev ts, int mode,
                                                 const double* __restrict__ dvec,
                                                 const double* __restrict__ r,
                                                 double* __restrict__ z, PcgScalars* sc,
                                                 ReduceWs ws) {
-  if (DOT && sc->done) return;
+  if (sc && sc->done) return;
   double acc[2] = {0.0, 0.0};
   const int stride = gridDim.x * VB;
   const int coarse_base = mode != 1 ? __ldg(&ts.vbase[pd.P]) : 0;
@@ -229,28 +253,49 @@ __global__ void __launch_bounds__(VB) k_prolong(PartDev pd, TileSetDev ts, int m
     }
     z[p] = v;
   }
-  if (DOT) {
-    reduce_finalize<2>(acc, ws, [&](double* t) {
-      const double rz_new = t[0];
-      if (sc->iter == 0) {
-        sc->beta = 0.0;
-      } else if (sc->flexible) {
-        sc->beta = (rz_new - t[1]) / sc->rz;
-      } else {
-        sc->beta = rz_new / sc->rz;
-      }
-      sc->rz_old = t[1];
-      sc->rz = rz_new;
-    });
-  }
+  if (DOT) reduce_finalize<2>(acc, ws, [&](double* t) { finalize_rz(sc, t); });
 }
 
 void launch_prolong(const PartDev& pd, const TileSetDev& ts, int mode, const double* dvec,
-                    const double* r, double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
-  if (sc)
+                    const double* r, double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s,
+                    bool dot) {
+  if (sc && dot)
     k_prolong<true><<<vec_blocks(pd.N), VB, 0, s>>>(pd, ts, mode, dvec, r, z, sc, ws);
   else
     k_prolong<false><<<vec_blocks(pd.N), VB, 0, s>>>(pd, ts, mode, dvec, r, z, sc, ws);
+}
+
+// Balanced operator (eq. balSW) from its parts: z = t - v + w with w = F g,
+// t = C_(1) (g - A w), v = F A t; with sc: the PCG finalize of r^T z as in the
+// prolongation.
+template <bool DOT>
+__global__ void __launch_bounds__(VB) k_combine_bal(int n, const double* __restrict__ t,
+                                                    const double* __restrict__ v,
+                                                    const double* __restrict__ w,
+                                                    const double* __restrict__ r,
+                                                    double* __restrict__ z, PcgScalars* sc,
+                                                    ReduceWs ws) {
+  if (DOT && sc->done) return;
+  double acc[2] = {0.0, 0.0};
+  const int stride = gridDim.x * VB;
+  for (int p = blockIdx.x * VB + threadIdx.x; p < n; p += stride) {
+    const double zp = (t[p] - v[p]) + w[p];
+    if (DOT) {
+      const double rp = r[p];
+      acc[0] += rp * zp;
+      acc[1] += rp * z[p];
+    }
+    z[p] = zp;
+  }
+  if (DOT) reduce_finalize<2>(acc, ws, [&](double* tt) { finalize_rz(sc, tt); });
+}
+
+void launch_combine_bal(int n, const double* t, const double* v, const double* w, const double* r,
+                        double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
+  if (sc)
+    k_combine_bal<true><<<vec_blocks(n), VB, 0, s>>>(n, t, v, w, r, z, sc, ws);
+  else
+    k_combine_bal<false><<<vec_blocks(n), VB, 0, s>>>(n, t, v, w, r, z, sc, ws);
 }
 
 // p = z + beta p

@@ -94,7 +94,7 @@ def test_local_and_coarse_matrices(levels, P, gamma):
 
 
 @pytest.mark.parametrize("levels,P,gamma", SMALL)
-@pytest.mark.parametrize("variant", ["additive", "one_level", "coarse_only"])
+@pytest.mark.parametrize("variant", ["additive", "one_level", "coarse_only", "balanced"])
 def test_preconditioner_apply_fp64(levels, P, gamma, variant):
     S = schwarz.Schwarz(levels, P, gamma)
     g = inputs.uniform(9, S.N)
@@ -104,9 +104,33 @@ def test_preconditioner_apply_fp64(levels, P, gamma, variant):
         ref = S.apply(g)
     elif variant == "one_level":
         ref = S.one_level(g)
+    elif variant == "balanced":
+        ref = S.apply_balanced(g)
     else:
         ref = S.coarse_correction(g)
     assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("levels,P,gamma", [((6, 6), 8, 0.5), ((3, 3, 3), 5, 1.0),
+                                            ((3, 2, 3, 2), 8, 0.5), ((7, 4), 16, 0.5)])
+def test_solve_balanced(levels, P, gamma):
+    """PCG with the balanced operator (eq. balSW) against the oracle's PCG with
+    the same operator: iteration counts within +-1, solutions within 1e-8; it
+    needs no more iterations than the additive operator (Sec. 4.1)."""
+    S = schwarz.Schwarz(levels, P, gamma)
+    f = inputs.uniform(15, S.N)
+    with make(levels, P, gamma, variant="balanced") as s:
+        u, st = s.solve(torch.tensor(f, device="cuda"), rtol=1e-10)
+        u = u.cpu().numpy()
+    with make(levels, P, gamma) as s2:
+        _, st_add = s2.solve(torch.tensor(f, device="cuda"), rtol=1e-10)
+    ue = exact.solve(levels, f)
+    xo, its, _ = krylov.pcg(lambda v: S.A @ v, S.apply_balanced, f, rtol=1e-10)
+    assert st.true_rel_res <= 2e-10
+    assert abs(st.iters - its) <= 1, (st.iters, its)
+    assert np.linalg.norm(u - ue) <= 1e-8 * np.linalg.norm(ue)
+    assert np.linalg.norm(u - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert st.iters <= st_add.iters
 
 
 @pytest.mark.parametrize("levels,P,gamma", SMALL)
