@@ -356,14 +356,22 @@ def run_ours(args):
     timed = {k: v for k, v in agg.items() if v[0] > 0}
     dom = max(timed, key=lambda k: timed[k][0])
     dom_ms, dom_n = timed[dom]
-    if dom in ("trsv_fwd", "trsv_bwd"):
+    d = len(levels)
+    if dom in ("trsv_fwd", "trsv_bwd") and prec == "fp64":
+        # one FMA per 8-byte factor element: 0.25 FMA/B needs 1.7 T FMA/s at full
+        # HBM rate, GB300 has 0.63 -> FP64-ALU bound; flops = 2 per element
+        per_launch = 2.0 * work[dom] / 8.0
+        achieved = per_launch / (dom_ms / dom_n * 1e-3) / 1e12
+        roof = {"bound": "alu", "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    elif dom in ("trsv_fwd", "trsv_bwd"):
         per_launch = work[dom]
         achieved = per_launch / (dom_ms / dom_n * 1e-3) / 1e9
         roof = {"bound": "hbm", "peak": hbm_peak, "unit": "GB/s"}
     elif dom == "stencil":
-        per_launch = work[dom]
-        achieved = per_launch / (dom_ms / dom_n * 1e-3) / 1e9
-        roof = {"bound": "hbm", "peak": hbm_peak, "unit": "GB/s"}
+        # 1 + 3 d FP64 flops per point against 16 bytes: FP64-ALU bound on GB300
+        per_launch = (1 + 3 * d) * N
+        achieved = per_launch / (dom_ms / dom_n * 1e-3) / 1e12
+        roof = {"bound": "alu", "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
     else:
         # factorization classes: operations per setup / device time per setup
         launches_per_setup = dom_n / steps
@@ -385,9 +393,14 @@ def run_ours(args):
             gbs = work[k] / (ms / n * 1e-3) / 1e9
             trsv[k] = {"GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
                        "bytes_per_launch": work[k], "avg_launch_ms": round(ms / n, 4)}
+            if prec == "fp64":
+                tf = 2.0 * work[k] / 8.0 / (ms / n * 1e-3) / 1e12
+                trsv[k].update({"fp64_TFLOPs": round(tf, 3), "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4)})
     if "stencil" in timed:
         ms, n = timed["stencil"]
+        tf = (1 + 3 * d) * N / (ms / n * 1e-3) / 1e12
         trsv["stencil"] = {"GB/s_algorithmic": round(work["stencil"] / (ms / n * 1e-3) / 1e9, 1),
+                           "fp64_TFLOPs": round(tf, 3), "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4),
                            "avg_launch_ms": round(ms / n, 4)}
     launches = nlaunch / args.steps
     it = statistics.mean(iters)
@@ -451,10 +464,17 @@ def run_stencil(args):
     ms = statistics.median(times)
     hbm, _, src = load_peaks()
     gbs = 16.0 * N / (ms * 1e-3) / 1e9
+    # 1 + 3 d FP64 flops per 16 bytes: above GB300's FP64/HBM balance (1.25 TF /
+    # 6.8 TB/s = 0.18 flop/B), so the FP64 ALU is the roofline
+    tf = (1 + 3 * len(levels)) * N / (ms * 1e-3) / 1e12
     print(json.dumps({"kernel": "stencil", "levels": list(levels), "N": N,
                       "vector_bytes": 8 * N, "ms_per_launch": round(ms, 4),
+                      "roofline": {"bound": "alu", "achieved": round(tf, 3),
+                                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": round(tf / FP64_PEAK_TFLOPS, 4),
+                                   "peak_source": "nominal (unit counts x clock)"},
                       "algorithmic_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
-                      "dram_bytes_per_point_min": 20, "peak_source": src}), flush=True)
+                      "peak_source": src}), flush=True)
     s.close()
 
 
