@@ -138,6 +138,25 @@ int sfcdd_solve_host(sfcdd_handle* h, const double* f_host, double* u_host, doub
 int sfcdd_solve_backward(sfcdd_handle* h, const double* u_dev, const double* gu_dev, double* gf_dev,
                          double* gc_host, double rtol, int maxit, sfcdd_stats* stats);
 
+/* Estimates of the extreme eigenvalues lambda_min, lambda_max of C^{-1} A (the
+ * numbers that give the optimal Richardson damping of eq. redrate): Ritz
+ * values of the Lanczos tridiagonal formed from the coefficients of a PCG run
+ * on f (at most `steps` iterations, to relative residual 1e-14).  They lie
+ * inside [lambda_min, lambda_max] and converge to its ends as steps grows.
+ * f_dev: device, length N, lexicographic (not modified).  Synchronises the
+ * stream.  Errors: INVALID_ARG (also f = 0), NAN, TIMEOUT, CUDA. */
+int sfcdd_estimate_spectrum(sfcdd_handle* h, const double* f_dev, int steps, double* lmin,
+                            double* lmax);
+
+/* Algorithm 3: the preconditioned damped linear (Richardson) iteration
+ * x^{k+1} = x^k + xi C^{-1} (f - A x^k), x^0 = 0, with the handle's
+ * preconditioner (additive, balanced, ...), until ||f - A x^k|| <= rtol ||f||
+ * (recomputed every step) or maxit updates.  xi > 0; the optimal damping is
+ * xi* = 2 / (lambda_min + lambda_max) (eq. redrate).  stats->iters = number of
+ * updates.  Synchronises the stream.  Errors as sfcdd_solve. */
+int sfcdd_richardson(sfcdd_handle* h, const double* f_dev, double* u_dev, double xi, double rtol,
+                     int maxit, sfcdd_stats* stats);
+
 /* ---- Batched solves: many independent subgrid problems ----
  * The subproblems of the sparse-grid combination technique (Sec. 2: one
  * anisotropic full grid per level vector l, solved independently), all with the

@@ -2,6 +2,7 @@
 // additive Schwarz preconditioner (Algorithm 2, eq. addSW; Sec. 3.3), adjoint,
 // and introspection for parity checks.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -1244,6 +1245,146 @@ int sfcdd_solve_backward(sfcdd_handle* h, const double* u_dev, const double* gu_
     for (int j = 0; j < h->d; ++j) gc_host[j] = h->sc_host->grad[j];
   }
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+namespace {
+// Number of eigenvalues below x of the symmetric tridiagonal (d, e), e[j]
+// coupling j-1 and j (Sturm sequence of the LDL^T pivots).
+int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t j = 0; j < d.size(); ++j) {
+    const double off = j ? e[j] * e[j] / q : 0.0;
+    q = d[j] - x - off;
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+// The idx-th smallest eigenvalue by bisection inside the Gershgorin interval.
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, int idx) {
+  double lo = 1e300, hi = -1e300;
+  for (size_t j = 0; j < d.size(); ++j) {
+    const double r = (j ? std::fabs(e[j]) : 0.0) + (j + 1 < d.size() ? std::fabs(e[j + 1]) : 0.0);
+    lo = std::min(lo, d[j] - r);
+    hi = std::max(hi, d[j] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(d, e, mid) > idx) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+}  // namespace
+
+int sfcdd_estimate_spectrum(sfcdd_handle* h, const double* f_dev, int steps, double* lmin,
+                            double* lmax) {
+  if (!h || !f_dev || steps < 1 || !lmin || !lmax) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  double* hist = nullptr;
+  SFCDD_CUDA_OK(cudaMalloc(&hist, 2 * (size_t)steps * sizeof(double)));
+  double* ha = hist;
+  double* hb = hist + steps;
+  const PcgScalars* sc = h->sc;
+  SFCDD_CUDA_OK(cudaMemcpyAsync((char*)h->sc + offsetof(PcgScalars, hist_alpha), &ha, sizeof(ha),
+                                cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync((char*)h->sc + offsetof(PcgScalars, hist_beta), &hb, sizeof(hb),
+                                cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync((char*)h->sc + offsetof(PcgScalars, hist_cap), &steps, sizeof(int),
+                                cudaMemcpyHostToDevice, s));
+  (void)sc;
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_lex_to_curve(h->g, h->curve_code, f_dev, h->b, s);
+  sfcdd_stats st{};
+  int rc = pcg_impl(h, 1e-14, steps, &st);
+  std::vector<double> a(steps), b(steps);
+  SFCDD_CUDA_OK(cudaMemcpyAsync(a.data(), ha, steps * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b.data(), hb, steps * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const double* nul = nullptr;
+  const int zero = 0;
+  SFCDD_CUDA_OK(cudaMemcpyAsync((char*)h->sc + offsetof(PcgScalars, hist_alpha), &nul, sizeof(nul),
+                                cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync((char*)h->sc + offsetof(PcgScalars, hist_beta), &nul, sizeof(nul),
+                                cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync((char*)h->sc + offsetof(PcgScalars, hist_cap), &zero, sizeof(int),
+                                cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  cudaFree(hist);
+  if (rc != SFCDD_OK && rc != SFCDD_ERR_MAXIT) return rc;
+  const int k = std::min(st.iters, steps);
+  if (k < 1) return SFCDD_ERR_INVALID_ARG;
+  // Lanczos tridiagonal of C^{-1} A from the PCG coefficients:
+  // T_00 = 1/a_0, T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_{j-1,j} = sqrt(b_{j-1})/a_{j-1}
+  std::vector<double> d(k), e(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    d[j] = 1.0 / a[j] + (j ? b[j - 1] / a[j - 1] : 0.0);
+    if (j) e[j] = std::sqrt(std::max(b[j - 1], 0.0)) / a[j - 1];
+  }
+  *lmin = tridiag_eig(d, e, 0);
+  *lmax = tridiag_eig(d, e, k - 1);
+  return SFCDD_OK;
+}
+
+int sfcdd_richardson(sfcdd_handle* h, const double* f_dev, double* u_dev, double xi, double rtol,
+                     int maxit, sfcdd_stats* stats) {
+  if (!h || !f_dev || !u_dev || !(xi > 0) || !(rtol >= 0) || maxit < 0)
+    return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_lex_to_curve(h->g, h->curve_code, f_dev, h->b, s);
+  SFCDD_CUDA_OK(cudaEventRecord(e0, s));
+  Prof pf(h, s);
+  pf.run(SFCDD_K_VECTOR,
+         [&] { launch_init_pcg(h->N, h->b, h->x, h->r, h->sc, h->ws, rtol, 0, s); });
+  int k = 0;
+  int rc = SFCDD_OK;
+  for (;;) {
+    // r = b - A x and ||r|| / ||b||
+    pf.run(SFCDD_K_STENCIL, [&] {
+      launch_true_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, h->sc, h->ws, s);
+    });
+    TRY(read_scalars(h));
+    const double rel = h->sc_host->bb > 0 ? h->sc_host->true_rel : 0.0;
+    if (!(rel == rel)) {
+      rc = SFCDD_ERR_NAN;
+      break;
+    }
+    if (rel <= rtol) break;
+    if (k >= maxit) {
+      rc = SFCDD_ERR_MAXIT;
+      break;
+    }
+    enqueue_apply(h, pf, h->tmp, h->z, nullptr);  // h = C^{-1} r
+    pf.run(SFCDD_K_UPDATE, [&] { launch_axpby(h->N, 1.0, h->x, xi, h->z, h->x, s); });
+    ++k;
+  }
+  SFCDD_CUDA_OK(cudaEventRecord(e1, s));
+  SFCDD_CUDA_OK(cudaEventSynchronize(e1));
+  pf.collect();
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int fi = 0;
+  const int ec = check_err(h, &fi);
+  if (ec != 0) rc = ec;
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_curve_to_lex(h->g, h->curve_code, h->x, u_dev, s);
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  if (stats) {
+    stats->iters = k;
+    stats->status = rc;
+    stats->fail_index = fi;
+    stats->rel_res = h->sc_host->true_rel;
+    stats->true_rel_res = h->sc_host->true_rel;
+    stats->setup_ms = h->setup_ms;
+    stats->solve_ms = ms;
+  }
   return rc;
 }
 

@@ -195,6 +195,11 @@ struct PcgScalars {
   int done;
   int status;
   int flexible;
+  // optional record of the PCG coefficients (Lanczos estimate of the spectrum):
+  // hist_alpha[k] = alpha_k, hist_beta[k] = beta_k for k < hist_cap
+  double* hist_alpha;
+  double* hist_beta;
+  int hist_cap;
 };
 
 // Reduction workspace: per-block partials + arrival counter.

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(VB) k_stencil(GridDev g, const unsigned* __res
     reduce_finalize<1>(vv, ws, [&](double* t) {
       sc->pq = t[0];
       sc->alpha = sc->rz / t[0];
+      if (sc->hist_alpha && sc->iter < sc->hist_cap) sc->hist_alpha[sc->iter] = sc->alpha;
     });
   } else if (MODE == 2) {
     double vv[1] = {acc};
@@ -230,6 +231,9 @@ __device__ __forceinline__ void finalize_rz(PcgScalars* sc, const double* t) {
   }
   sc->rz_old = t[1];
   sc->rz = rz_new;
+  // beta_k (p_{k+1} = z_{k+1} + beta_k p_k) after update k (iter = k + 1)
+  if (sc->hist_beta && sc->iter >= 1 && sc->iter - 1 < sc->hist_cap)
+    sc->hist_beta[sc->iter - 1] = sc->beta;
 }
 
 // sc != null without DOT: only the early return once the solve has converged.

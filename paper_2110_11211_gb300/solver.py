@@ -109,6 +109,25 @@ class Solver:
         check("sfcdd_solve_backward", rc)
         return gf, [gc[j] for j in range(self.d)], st
 
+    def estimate_spectrum(self, f: torch.Tensor, steps=200):
+        """(lambda_min, lambda_max) estimates of C^{-1} A from a PCG run on f."""
+        lo, hi = C.c_double(), C.c_double()
+        check("sfcdd_estimate_spectrum",
+              self._L.sfcdd_estimate_spectrum(self._h, _dev_ptr(f.reshape(-1).contiguous()),
+                                              int(steps), C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
+
+    def richardson(self, f: torch.Tensor, xi, rtol=1e-8, maxit=100000, check_status=True):
+        """Algorithm 3: damped preconditioned Richardson iteration from x = 0."""
+        f = f.reshape(-1).contiguous()
+        u = torch.empty_like(f)
+        st = Stats()
+        rc = self._L.sfcdd_richardson(self._h, _dev_ptr(f), _dev_ptr(u), float(xi), float(rtol),
+                                      int(maxit), C.byref(st))
+        if check_status:
+            check("sfcdd_richardson", rc)
+        return u, st
+
     def apply_operator(self, x: torch.Tensor, curve_order=False):
         y = torch.empty_like(x)
         check("sfcdd_apply_operator",
