@@ -50,6 +50,7 @@ enum sfcdd_status {
 enum sfcdd_precision { SFCDD_FP64 = 0, SFCDD_FP32 = 1, SFCDD_BF16 = 2 };
 enum sfcdd_variant { SFCDD_ADDITIVE = 0, SFCDD_BALANCED = 1, SFCDD_ONE_LEVEL = 2, SFCDD_COARSE_ONLY = 3 };
 enum sfcdd_weighting { SFCDD_WEIGHT_NONE = 0, SFCDD_WEIGHT_OMEGA = 1 };
+enum sfcdd_method { SFCDD_METHOD_PCG = 0, SFCDD_METHOD_RICHARDSON = 1 };
 
 typedef struct {
   const double* coeffs; /* host, length d: per-axis c_j; NULL = all ones */
@@ -156,6 +157,26 @@ int sfcdd_estimate_spectrum(sfcdd_handle* h, const double* f_dev, int steps, dou
  * updates.  Synchronises the stream.  Errors as sfcdd_solve. */
 int sfcdd_richardson(sfcdd_handle* h, const double* f_dev, double* u_dev, double xi, double rtol,
                      int maxit, sfcdd_stats* stats);
+
+/* The convergence protocol of Sec. 4: the homogeneous problem A x = 0 (f = 0,
+ * solution 0), so every iterate x^k is its own error, measured in the energy
+ * norm ||x^k||_A = sqrt(x^k^T A x^k).  Starts from x0_dev (device, length N,
+ * lexicographic, not modified; the paper draws it from U[-1,1] and rescales to
+ * ||x^0||_A = 1, which this relative test makes unnecessary) and iterates until
+ * ||x^K||_A <= tol ||x^0||_A or maxit updates.
+ *   method SFCDD_METHOD_PCG:        preconditioned CG with the handle's
+ *     preconditioner; the energy norm comes from the recurrence residual,
+ *     ||x^k||_A^2 = -x^k^T r^k (r^k = -A x^k), fused into the update.
+ *   method SFCDD_METHOD_RICHARDSON: Algorithm 3 with damping xi > 0 (xi is
+ *     ignored for PCG); the energy norm is recomputed from A x^k every step.
+ * u_dev (device, length N, lexicographic) receives x^K.  stats->iters = K
+ * (updates of x), stats->rel_res = ||x^K||_A / ||x^0||_A as the stopping test
+ * saw it, stats->true_rel_res = the same ratio recomputed from A x^K.
+ * x^0 = 0 returns at once with K = 0.  Synchronises the stream.
+ * Errors: INVALID_ARG (null pointers, tol < 0, maxit < 0, unknown method,
+ * xi <= 0 for Richardson), MAXIT, NAN, TIMEOUT, CUDA. */
+int sfcdd_solve_homogeneous(sfcdd_handle* h, const double* x0_dev, double* u_dev, int method,
+                            double xi, double tol, int maxit, sfcdd_stats* stats);
 
 /* ---- Batched solves: many independent subgrid problems ----
  * The subproblems of the sparse-grid combination technique (Sec. 2: one

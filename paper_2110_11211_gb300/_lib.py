@@ -31,7 +31,7 @@ EXPORTS = [
     "sfcdd_set_profiling", "sfcdd_get_kernel_stats", "sfcdd_kernel_work", "sfcdd_destroy",
     "sfcdd_status_string", "sfcdd_curve_order_noalloc", "sfcdd_batch_setup",
     "sfcdd_batch_offsets", "sfcdd_batch_solve", "sfcdd_batch_info", "sfcdd_batch_destroy",
-    "sfcdd_estimate_spectrum", "sfcdd_richardson",
+    "sfcdd_estimate_spectrum", "sfcdd_richardson", "sfcdd_solve_homogeneous",
 ]
 
 
@@ -113,6 +113,8 @@ def lib() -> C.CDLL:
     L.sfcdd_estimate_spectrum.argtypes = [H, P, C.c_int, C.POINTER(C.c_double),
                                           C.POINTER(C.c_double)]
     L.sfcdd_richardson.argtypes = [H, P, P, C.c_double, C.c_double, C.c_int, C.POINTER(Stats)]
+    L.sfcdd_solve_homogeneous.argtypes = [H, P, P, C.c_int, C.c_double, C.c_double, C.c_int,
+                                          C.POINTER(Stats)]
     for name in EXPORTS:
         if name not in ("sfcdd_default_options", "sfcdd_kernel_work", "sfcdd_status_string"):
             getattr(L, name).restype = C.c_int

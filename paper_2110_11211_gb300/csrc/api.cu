@@ -1089,7 +1089,10 @@ int read_scalars(sfcdd_handle* h) {
 }
 
 // PCG on the curve-order right-hand side already in h->b; solution in h->x.
-int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats) {
+// homogeneous: b = 0 and h->x holds x_0; the iteration stops on the energy
+// norm ||x_k||_A <= rtol ||x_0||_A (Sec. 4) instead of the residual.
+int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats,
+             bool homogeneous = false) {
   if (!(rtol >= 0) || maxit < 0) return SFCDD_ERR_INVALID_ARG;
   cudaStream_t s = h->stream;
   TRY(build_graph(h));
@@ -1098,7 +1101,17 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats) {
   SFCDD_CUDA_OK(cudaEventCreate(&e1));
   SFCDD_CUDA_OK(cudaEventRecord(e0, s));
   Prof pf(h, s);
-  pf.run(SFCDD_K_VECTOR, [&] { launch_init_pcg(h->N, h->b, h->x, h->r, h->sc, h->ws, rtol, h->flexible, s); });
+  if (homogeneous) {
+    // r_0 = -A x_0, ||x_0||_A^2 = -x_0^T r_0
+    pf.run(SFCDD_K_STENCIL, [&] {
+      launch_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->r, nullptr, h->ws, s);
+    });
+    pf.run(SFCDD_K_VECTOR, [&] {
+      launch_energy(h->N, h->x, h->r, h->sc, h->ws, rtol, h->flexible, 1, s);
+    });
+  } else {
+    pf.run(SFCDD_K_VECTOR, [&] { launch_init_pcg(h->N, h->b, h->x, h->r, h->sc, h->ws, rtol, h->flexible, s); });
+  }
   SFCDD_CUDA_OK(cudaMemsetAsync(h->p, 0, (size_t)h->N * sizeof(double), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->z, 0, (size_t)h->N * sizeof(double), s));
   enqueue_apply(h, pf, h->r, h->z, h->sc);   // z_0 = C^{-1} r_0, rz, beta = 0
@@ -1123,10 +1136,19 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats) {
     chunk = std::min(chunk * 2, 16);
   }
   SFCDD_CUDA_OK(cudaEventRecord(e1, s));
-  // true residual ||b - A x|| / ||b||
-  pf.run(SFCDD_K_STENCIL, [&] {
-    launch_true_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, h->sc, h->ws, s);
-  });
+  if (homogeneous) {
+    // energy norm recomputed from A x (not the recurrence residual)
+    pf.run(SFCDD_K_STENCIL, [&] {
+      launch_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, nullptr, h->ws, s);
+    });
+    pf.run(SFCDD_K_VECTOR,
+           [&] { launch_energy(h->N, h->x, h->tmp, h->sc, h->ws, rtol, h->flexible, 0, s); });
+  } else {
+    // true residual ||b - A x|| / ||b||
+    pf.run(SFCDD_K_STENCIL, [&] {
+      launch_true_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, h->sc, h->ws, s);
+    });
+  }
   TRY(read_scalars(h));
   pf.collect();
   float ms = 0.f;
@@ -1146,6 +1168,77 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats) {
     stats->fail_index = fi;
     stats->rel_res = sc.rel;
     stats->true_rel_res = sc.true_rel;
+    stats->setup_ms = h->setup_ms;
+    stats->solve_ms = ms;
+  }
+  return rc;
+}
+
+// Algorithm 3 on the curve-order right-hand side in h->b: x <- x + xi C^{-1}(b - A x),
+// result written to u_dev (lexicographic).  homogeneous: b = 0, h->x holds x_0 and
+// the stop is ||x_k||_A <= rtol ||x_0||_A (Sec. 4); otherwise x_0 = 0 and the stop
+// is the true relative residual.  Every step reads the stopping quantity back.
+int richardson_impl(sfcdd_handle* h, double* u_dev, double xi, double rtol, int maxit,
+                    sfcdd_stats* stats, bool homogeneous) {
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  SFCDD_CUDA_OK(cudaEventRecord(e0, s));
+  Prof pf(h, s);
+  if (!homogeneous)
+    pf.run(SFCDD_K_VECTOR,
+           [&] { launch_init_pcg(h->N, h->b, h->x, h->r, h->sc, h->ws, rtol, 0, s); });
+  int k = 0;
+  int rc = SFCDD_OK;
+  for (;;) {
+    if (homogeneous) {
+      // tmp = -A x; ||x||_A^2 = -x^T tmp (the first pass records ||x_0||_A)
+      pf.run(SFCDD_K_STENCIL, [&] {
+        launch_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, nullptr, h->ws, s);
+      });
+      pf.run(SFCDD_K_VECTOR,
+             [&] { launch_energy(h->N, h->x, h->tmp, h->sc, h->ws, rtol, 0, k == 0, s); });
+    } else {
+      // tmp = b - A x and ||tmp|| / ||b||
+      pf.run(SFCDD_K_STENCIL, [&] {
+        launch_true_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, h->sc, h->ws, s);
+      });
+    }
+    TRY(read_scalars(h));
+    const double rel = (homogeneous || h->sc_host->bb > 0) ? h->sc_host->true_rel : 0.0;
+    if (!(rel == rel)) {
+      rc = SFCDD_ERR_NAN;
+      break;
+    }
+    if (rel <= rtol) break;
+    if (k >= maxit) {
+      rc = SFCDD_ERR_MAXIT;
+      break;
+    }
+    enqueue_apply(h, pf, h->tmp, h->z, nullptr);  // z = C^{-1} (b - A x)
+    pf.run(SFCDD_K_UPDATE, [&] { launch_axpby(h->N, 1.0, h->x, xi, h->z, h->x, s); });
+    ++k;
+  }
+  SFCDD_CUDA_OK(cudaEventRecord(e1, s));
+  SFCDD_CUDA_OK(cudaEventSynchronize(e1));
+  pf.collect();
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int fi = 0;
+  const int ec = check_err(h, &fi);
+  if (ec != 0) rc = ec;
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_curve_to_lex(h->g, h->curve_code, h->x, u_dev, s);
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  if (stats) {
+    stats->iters = k;
+    stats->status = rc;
+    stats->fail_index = fi;
+    stats->rel_res = h->sc_host->true_rel;
+    stats->true_rel_res = h->sc_host->true_rel;
     stats->setup_ms = h->setup_ms;
     stats->solve_ms = ms;
   }
@@ -1331,60 +1424,27 @@ int sfcdd_richardson(sfcdd_handle* h, const double* f_dev, double* u_dev, double
                      int maxit, sfcdd_stats* stats) {
   if (!h || !f_dev || !u_dev || !(xi > 0) || !(rtol >= 0) || maxit < 0)
     return SFCDD_ERR_INVALID_ARG;
-  cudaStream_t s = h->stream;
-  cudaEvent_t e0, e1;
-  SFCDD_CUDA_OK(cudaEventCreate(&e0));
-  SFCDD_CUDA_OK(cudaEventCreate(&e1));
   h->launches[SFCDD_K_VECTOR] += 1;
-  launch_lex_to_curve(h->g, h->curve_code, f_dev, h->b, s);
-  SFCDD_CUDA_OK(cudaEventRecord(e0, s));
-  Prof pf(h, s);
-  pf.run(SFCDD_K_VECTOR,
-         [&] { launch_init_pcg(h->N, h->b, h->x, h->r, h->sc, h->ws, rtol, 0, s); });
-  int k = 0;
-  int rc = SFCDD_OK;
-  for (;;) {
-    // r = b - A x and ||r|| / ||b||
-    pf.run(SFCDD_K_STENCIL, [&] {
-      launch_true_residual(h->g, h->curve_code, h->invpad, h->b, h->x, h->tmp, h->sc, h->ws, s);
-    });
-    TRY(read_scalars(h));
-    const double rel = h->sc_host->bb > 0 ? h->sc_host->true_rel : 0.0;
-    if (!(rel == rel)) {
-      rc = SFCDD_ERR_NAN;
-      break;
-    }
-    if (rel <= rtol) break;
-    if (k >= maxit) {
-      rc = SFCDD_ERR_MAXIT;
-      break;
-    }
-    enqueue_apply(h, pf, h->tmp, h->z, nullptr);  // h = C^{-1} r
-    pf.run(SFCDD_K_UPDATE, [&] { launch_axpby(h->N, 1.0, h->x, xi, h->z, h->x, s); });
-    ++k;
-  }
-  SFCDD_CUDA_OK(cudaEventRecord(e1, s));
-  SFCDD_CUDA_OK(cudaEventSynchronize(e1));
-  pf.collect();
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  int fi = 0;
-  const int ec = check_err(h, &fi);
-  if (ec != 0) rc = ec;
+  launch_lex_to_curve(h->g, h->curve_code, f_dev, h->b, h->stream);
+  return richardson_impl(h, u_dev, xi, rtol, maxit, stats, false);
+}
+
+int sfcdd_solve_homogeneous(sfcdd_handle* h, const double* x0_dev, double* u_dev, int method,
+                            double xi, double tol, int maxit, sfcdd_stats* stats) {
+  if (!h || !x0_dev || !u_dev || !(tol >= 0) || maxit < 0) return SFCDD_ERR_INVALID_ARG;
+  if (method != SFCDD_METHOD_PCG && method != SFCDD_METHOD_RICHARDSON)
+    return SFCDD_ERR_INVALID_ARG;
+  if (method == SFCDD_METHOD_RICHARDSON && !(xi > 0)) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->b, 0, (size_t)h->N * sizeof(double), s));
+  h->launches[SFCDD_K_VECTOR] += 1;
+  launch_lex_to_curve(h->g, h->curve_code, x0_dev, h->x, s);
+  if (method == SFCDD_METHOD_RICHARDSON)
+    return richardson_impl(h, u_dev, xi, tol, maxit, stats, true);
+  const int rc = pcg_impl(h, tol, maxit, stats, true);
   h->launches[SFCDD_K_VECTOR] += 1;
   launch_curve_to_lex(h->g, h->curve_code, h->x, u_dev, s);
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
-  if (stats) {
-    stats->iters = k;
-    stats->status = rc;
-    stats->fail_index = fi;
-    stats->rel_res = h->sc_host->true_rel;
-    stats->true_rel_res = h->sc_host->true_rel;
-    stats->setup_ms = h->setup_ms;
-    stats->solve_ms = ms;
-  }
   return rc;
 }
 

@@ -200,6 +200,10 @@ struct PcgScalars {
   double* hist_alpha;
   double* hist_beta;
   int hist_cap;
+  // energy-norm stopping for the homogeneous problem (f = 0, solution 0):
+  // ||x||_A^2 = -x^T r, converged when it falls below rtol^2 ||x_0||_A^2 = rtol^2 esq0
+  int energy;
+  double esq0;
 };
 
 // Reduction workspace: per-block partials + arrival counter.
@@ -286,6 +290,8 @@ void launch_combine_bal(int n, const double* t, const double* v, const double* w
 void launch_update_p(int n, const double* z, double* p, const PcgScalars* sc, cudaStream_t s);
 void launch_init_pcg(int n, const double* b, double* x, double* r, PcgScalars* sc, ReduceWs ws,
                      double rtol, int flexible, cudaStream_t s);
+void launch_energy(int n, const double* x, const double* r, PcgScalars* sc, ReduceWs ws,
+                   double rtol, int flexible, int init, cudaStream_t s);
 void launch_true_residual(const GridDev& g, const unsigned* code, const int* invpad,
                           const double* b, const double* x, double* tmp, PcgScalars* sc,
                           ReduceWs ws, cudaStream_t s);

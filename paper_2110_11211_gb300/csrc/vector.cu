@@ -159,18 +159,20 @@ __global__ void __launch_bounds__(VB) k_update_xr(int n, double* __restrict__ x,
                                                   ReduceWs ws) {
   if (sc->done) return;
   const double alpha = sc->alpha;
-  double acc = 0.0;
+  double acc[2] = {0.0, 0.0};
   const int stride = gridDim.x * VB;
   for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) {
-    x[i] += alpha * p[i];
+    const double xi = x[i] + alpha * p[i];
+    x[i] = xi;
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
-    acc += ri * ri;
+    acc[0] += ri * ri;
+    acc[1] += xi * ri;
   }
-  double vv[1] = {acc};
-  reduce_finalize<1>(vv, ws, [&](double* t) {
+  reduce_finalize<2>(acc, ws, [&](double* t) {
     sc->rr = t[0];
-    const double rel = sqrt(t[0] / sc->bb);
+    // energy mode (f = 0): ||x||_A / ||x_0||_A with ||x||_A^2 = -x^T r
+    const double rel = sc->energy ? sqrt(fmax(-t[1], 0.0) / sc->esq0) : sqrt(t[0] / sc->bb);
     sc->rel = rel;
     sc->iter += 1;
     if (!(rel == rel) || isinf(rel) || !(sc->alpha == sc->alpha) || isinf(sc->alpha)) {
@@ -185,6 +187,45 @@ __global__ void __launch_bounds__(VB) k_update_xr(int n, double* __restrict__ x,
 void launch_update_xr(int n, double* x, double* r, const double* p, const double* q,
                       PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
   k_update_xr<<<vec_blocks(n), VB, 0, s>>>(n, x, r, p, q, sc, ws);
+}
+
+// Energy-norm protocol (f = 0): r = -A x is given; init = 1 resets the PCG
+// scalars with ||x_0||_A^2 = -x^T r, otherwise sc->true_rel = ||x||_A / ||x_0||_A.
+__global__ void __launch_bounds__(VB) k_energy(int n, const double* __restrict__ x,
+                                               const double* __restrict__ r, PcgScalars* sc,
+                                               ReduceWs ws, double rtol, int flexible, int init) {
+  double acc = 0.0;
+  const int stride = gridDim.x * VB;
+  for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) acc += x[i] * r[i];
+  double vv[1] = {acc};
+  reduce_finalize<1>(vv, ws, [&](double* t) {
+    const double esq = fmax(-t[0], 0.0);
+    if (init) {
+      sc->esq0 = esq;
+      sc->energy = 1;
+      sc->bb = 1.0;
+      sc->rr = 0.0;
+      sc->rel = esq > 0.0 ? 1.0 : 0.0;
+      sc->true_rel = sc->rel;
+      sc->rz = 0.0;
+      sc->rz_old = 0.0;
+      sc->pq = 0.0;
+      sc->alpha = 0.0;
+      sc->beta = 0.0;
+      sc->iter = 0;
+      sc->status = 0;
+      sc->rtol = rtol;
+      sc->flexible = flexible;
+      sc->done = esq > 0.0 ? 0 : 1;
+    } else {
+      sc->true_rel = sc->esq0 > 0.0 ? sqrt(esq / sc->esq0) : 0.0;
+    }
+  });
+}
+
+void launch_energy(int n, const double* x, const double* r, PcgScalars* sc, ReduceWs ws,
+                   double rtol, int flexible, int init, cudaStream_t s) {
+  k_energy<<<vec_blocks(n), VB, 0, s>>>(n, x, r, sc, ws, rtol, flexible, init);
 }
 
 // ---------------------------------------------------------------------------
@@ -330,6 +371,7 @@ __global__ void __launch_bounds__(VB) k_init_pcg(int n, const double* __restrict
   }
   double vv[1] = {acc};
   reduce_finalize<1>(vv, ws, [&](double* t) {
+    sc->energy = 0;
     sc->bb = t[0];
     sc->rr = t[0];
     sc->rel = t[0] > 0.0 ? 1.0 : 0.0;

@@ -128,6 +128,20 @@ class Solver:
             check("sfcdd_richardson", rc)
         return u, st
 
+    def solve_homogeneous(self, x0: torch.Tensor, method="pcg", xi=0.0, tol=1e-8, maxit=100000,
+                          check_status=True):
+        """Sec. 4 protocol: A x = 0 from x0, until ||x_K||_A <= tol ||x0||_A.
+        method 'pcg' or 'richardson' (damping xi).  Returns (x_K, stats)."""
+        m = {"pcg": 0, "richardson": 1}[method]
+        x0 = x0.reshape(-1).contiguous()
+        u = torch.empty_like(x0)
+        st = Stats()
+        rc = self._L.sfcdd_solve_homogeneous(self._h, _dev_ptr(x0), _dev_ptr(u), m, float(xi),
+                                             float(tol), int(maxit), C.byref(st))
+        if check_status:
+            check("sfcdd_solve_homogeneous", rc)
+        return u, st
+
     def apply_operator(self, x: torch.Tensor, curve_order=False):
         y = torch.empty_like(x)
         check("sfcdd_apply_operator",
