@@ -5,11 +5,15 @@ there are C(L + d - 2 - i, d - 1) of them.  Each gets P = P_hat * 2^{d-1-i}
 subdomains (eq. Pchoice).  The total number of subdomains is
     P_hat / (d-1)! * sum_{k=0}^{d-1} 2^{d-1-k} prod_{i=1}^{d-1} (L + d - 1 - k - i)
 (Sec. 2, the formula before Table 1).  eq. (combi) combines the subgrid
-solutions with the weights (-1)^i C(d-1, i).
+solutions with the weights (-1)^i C(d-1, i); the combined function is the
+weighted sum of the subgrids' piecewise multilinear interpolants, evaluated
+here at arbitrary points.
 """
 from __future__ import annotations
 
 from math import comb, factorial
+
+import numpy as np
 
 
 def layer_levels(d: int, L: int, i: int):
@@ -54,3 +58,52 @@ def total_subdomains_closed_form(d: int, L: int, P_hat: int) -> int:
 def combination_weights(d: int):
     """eq. (combi): weight of layer i is (-1)^i C(d-1, i)."""
     return [(-1) ** i * comb(d - 1, i) for i in range(d)]
+
+
+def full_layer_set(d: int, L: int):
+    """(level vector, combination weight) of every subproblem of eq. (combi):
+    layers i = 0..d-1, weight (-1)^i C(d-1, i)."""
+    w = combination_weights(d)
+    return [(lv, w[i]) for i in range(d) for lv in layer_levels(d, L, i)]
+
+
+def interpolate(levels, values_lex, points):
+    """Piecewise multilinear interpolant of a grid function with zero Dirichlet
+    data (the nodal basis of Sec. 2's full grids), evaluated at points (n, d) in
+    [0, 1]^d.  Node k_j of axis j sits at k_j 2^{-l_j}, k_j = 0..2^{l_j}; the
+    boundary nodes k_j = 0 and k_j = 2^{l_j} carry 0, the interior ones the
+    lexicographic values (last axis fastest)."""
+    levels = [int(l) for l in levels]
+    d = len(levels)
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, d)
+    sizes = [(1 << l) - 1 for l in levels]
+    U = np.zeros([s + 2 for s in sizes])
+    U[tuple(slice(1, s + 1) for s in sizes)] = np.asarray(values_lex).reshape(sizes)
+    out = np.zeros(pts.shape[0])
+    for p in range(pts.shape[0]):
+        base, frac = [], []
+        for j in range(d):
+            t = pts[p, j] * (1 << levels[j])
+            k = min(int(np.floor(t)), (1 << levels[j]) - 1)
+            base.append(k)
+            frac.append(t - k)
+        acc = 0.0
+        for corner in range(1 << d):
+            wgt = 1.0
+            idx = []
+            for j in range(d):
+                bit = (corner >> j) & 1
+                wgt *= frac[j] if bit else 1.0 - frac[j]
+                idx.append(base[j] + bit)
+            acc += wgt * U[tuple(idx)]
+        out[p] = acc
+    return out
+
+
+def combine(d: int, L: int, solutions, points):
+    """eq. (combi): sum over the full layer set of weight x interpolant of the
+    subproblem's solution.  solutions: dict level vector -> lexicographic values."""
+    out = np.zeros(np.asarray(points).reshape(-1, d).shape[0])
+    for lv, w in full_layer_set(d, L):
+        out += w * interpolate(lv, solutions[lv], points)
+    return out

@@ -129,3 +129,36 @@ def combi_levels(d: int, norms) -> list[tuple[int, ...]]:
     for s in sorted(norms):
         rec([], s, d)
     return out
+
+
+def unit_points(seed: int, n: int, d: int) -> np.ndarray:
+    """n points uniformly distributed in [0, 1)^d, shape (n, d)."""
+    return unit_doubles(seed, n * d).reshape(n, d)
+
+
+def ct_exact(points) -> np.ndarray:
+    """The solution of the Poisson test problem of the combination-technique
+    study (Sec. 4.3): u(x) = ||x||_2 prod_i sin(pi x_i), zero on the boundary
+    of [0, 1]^d.  points: (n, d)."""
+    x = np.asarray(points, dtype=np.float64)
+    return np.linalg.norm(x, axis=1) * np.prod(np.sin(np.pi * x), axis=1)
+
+
+def ct_rhs(levels) -> np.ndarray:
+    """f = -Laplace(u) of that solution at the interior grid points
+    x_j = k_j 2^{-l_j}, lexicographic (last axis fastest).  With r = ||x||_2 and
+    s = prod_i sin(pi x_i):  Laplace(u) = s (d-1)/r + 2 (x/r) . grad(s) - d pi^2 r s,
+    grad(s)_i = pi cos(pi x_i) prod_{j != i} sin(pi x_j)."""
+    levels = [int(l) for l in levels]
+    d = len(levels)
+    axes = [np.arange(1, 1 << l, dtype=np.float64) / float(1 << l) for l in levels]
+    X = np.stack([g.reshape(-1) for g in np.meshgrid(*axes, indexing="ij")], axis=1)
+    r = np.linalg.norm(X, axis=1)
+    S = np.sin(np.pi * X)
+    s = np.prod(S, axis=1)
+    grad_dot = np.zeros(X.shape[0])
+    for i in range(d):
+        others = np.prod(np.delete(S, i, axis=1), axis=1) if d > 1 else np.ones(X.shape[0])
+        grad_dot += X[:, i] * np.pi * np.cos(np.pi * X[:, i]) * others
+    lap = s * (d - 1) / r + 2.0 * grad_dot / r - d * np.pi ** 2 * r * s
+    return -lap
