@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--gamma", type=float, default=None, help="custom overlap")
     ap.add_argument("--stencil-levels", default=None,
                     help="time only the curve-order stencil on this grid (e.g. 9,9,9)")
+    ap.add_argument("--ct", default=None,
+                    help="time the combination technique d,L,P_hat (e.g. 4,10,4): batched "
+                         "solve of the full layer set + eq. combi at 2^16 points")
     return ap.parse_args()
 
 
@@ -383,6 +386,10 @@ def run_ours(args):
             "true_rel_res": str_.true_rel_res,
             "rel_diff_vs_pcg_solution": float(torch.linalg.norm(ur - u64) / torch.linalg.norm(u64))}
 
+    # the combination technique around the batched solver (eq. combi, Sec. 4.3 problem)
+    if not args.no_variants and rank == 0:
+        variants["combination_d4_L10_Phat4_fp32"] = ct_measure(4, 10, 4, "fp32", 2)
+
     hbm_peak, bf16_peak, peak_src = load_peaks()
     steps = prof_steps
     kernels = {}
@@ -517,6 +524,62 @@ def run_stencil(args):
     s.close()
 
 
+def ct_measure(d, L, P_hat, prec, steps, rtol=1e-8, npts=1 << 16):
+    """Combination technique on the Sec. 4.3 Poisson test problem: batched setup
+    and one-graph solve of every subgrid of the full layer set (eq. Pchoice
+    subdomain counts), then eq. combi at npts seeded points; error against the
+    closed-form solution.  Times are CUDA-event device times (mean of `steps`)."""
+    import numpy as np
+    import torch
+    from paper_2110_11211_gb300.combination import Combination
+    stream = torch.cuda.current_stream()
+    pts = torch.tensor(inputs.unit_points(44, npts, d), device="cuda")
+    ue = inputs.ct_exact(pts.cpu().numpy())
+    rows = []
+    for k in range(steps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        ct = Combination(d, L, P_hat, precision=prec)
+        ev[1].record(stream)
+        ct.solve(rtol=rtol)
+        ev[2].record(stream)
+        out = ct.evaluate(pts)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        tot, per = ct.stats
+        it = [p.iters for p in per]
+        nsub, ntot = len(ct.levels), ct.batch.N
+        corners = sum(2 ** sum(1 for l in lv if l > 1) for lv in ct.levels)
+        ct.close()
+        if k == 0:
+            continue  # first pass warms the library and the allocator
+        rows.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                     ev[2].elapsed_time(ev[3])])
+    m = np.mean(np.array(rows), axis=0)
+    err = float(np.abs(out.cpu().numpy() - ue).max())
+    return {"d": d, "L": L, "P_hat": P_hat, "precision": prec, "subgrids": nsub,
+            "N_total": ntot, "rtol": rtol, "setup_ms": round(float(m[0]), 2),
+            "solve_ms": round(float(m[1]), 2), "combine_ms": round(float(m[2]), 3),
+            "points": npts, "interior_corner_loads_per_point_max": corners,
+            "iters": {"min": int(min(it)), "max": int(max(it)),
+                      "mean": round(float(np.mean(it)), 2)},
+            "max_abs_error_vs_exact": err, "timing": "CUDA events, mean of %d" % steps}
+
+
+def run_ct_bench(args):
+    import torch
+    torch.cuda.set_device(0)
+    d, L, P_hat = (int(v) for v in args.ct.split(","))
+    prec = args.precision or "fp32"
+    r = ct_measure(d, L, P_hat, prec, max(args.steps, 1))
+    print(json.dumps({"metric": "combination technique: setup + solve + combine (ms)",
+                      "value": round(r["setup_ms"] + r["solve_ms"] + r["combine_ms"], 2),
+                      "unit": "ms", "higher_is_better": False, "data": "synthetic",
+                      "config": {"workload": f"combination_d{d}_L{L}_Phat{P_hat}"}, **r}),
+          flush=True)
+
+
 def run_batch_bench(args):
     """Combination-technique set (all d = 4 level vectors with |l|_1 in {12, 13},
     385 subgrids, P = 64 each, gamma = 1/2): batched setup + one-graph solve of
@@ -599,6 +662,9 @@ def main():
         return
     if args.stencil_levels:
         run_stencil(args)
+        return
+    if args.ct and args.impl == "ours":
+        run_ct_bench(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -195,6 +195,11 @@ int sfcdd_solve_homogeneous(sfcdd_handle* h, const double* x0_dev, double* u_dev
 typedef struct sfcdd_batch sfcdd_batch;
 int sfcdd_batch_setup(const int* levels, int nsub, int d, int P, double overlap,
                       const sfcdd_options* opt, sfcdd_batch** out);
+/* As sfcdd_batch_setup with a subdomain count per subgrid: P (host, nsub
+ * entries, each >= 2 and <= that subgrid's N), e.g. eq. Pchoice,
+ * P = P_hat 2^{d-1-i} for the subgrids of layer i of eq. combi. */
+int sfcdd_batch_setup_each(const int* levels, const int* P, int nsub, int d, double overlap,
+                           const sfcdd_options* opt, sfcdd_batch** out);
 int sfcdd_batch_offsets(const sfcdd_batch* b, long long* offsets_host);
 int sfcdd_batch_solve(sfcdd_batch* b, const double* f_dev, double* u_dev, double rtol, int maxit,
                       sfcdd_stats* per_sub, sfcdd_stats* total);
@@ -202,6 +207,20 @@ int sfcdd_batch_solve(sfcdd_batch* b, const double* f_dev, double* u_dev, double
 int sfcdd_batch_info(const sfcdd_batch* b, long long* n_total, long long* factor_bytes,
                      double* setup_ms);
 int sfcdd_batch_destroy(sfcdd_batch* b);
+
+/* The combination formula eq. combi evaluated at points: for every point x_p
+ *   out[p] = sum_s coef[s] * (I_s u_s)(x_p),
+ * where u_s is subgrid s's solution (device, the concatenated lexicographic
+ * vectors of sfcdd_batch_solve, offsets from sfcdd_batch_offsets) and I_s the
+ * piecewise multilinear interpolant on its grid (nodes k_j 2^{-l_j},
+ * k_j = 0..2^{l_j}, zero on the boundary nodes).  coef (host, nsub): the
+ * combination coefficient of each subgrid, (-1)^i C(d-1, i) for layer i.
+ * points (device, npts x d, row-major, coordinates clamped to [0, 1]);
+ * out (device, npts).  One warp per point, a fixed summation order: repeated
+ * calls give identical results.  Synchronises the batch's stream.
+ * Errors: INVALID_ARG (null pointers, npts < 0, NaN coefficient), CUDA. */
+int sfcdd_batch_combine(sfcdd_batch* b, const double* coef_host, const double* u_dev,
+                        const double* points_dev, long long npts, double* out_dev);
 
 /* y = A x (the matrix-free stencil, Sec. 4).  curve_order = 0: x, y
  * lexicographic; 1: x, y in curve order (no permutation, the hot-path form). */

@@ -32,6 +32,7 @@ EXPORTS = [
     "sfcdd_status_string", "sfcdd_curve_order_noalloc", "sfcdd_batch_setup",
     "sfcdd_batch_offsets", "sfcdd_batch_solve", "sfcdd_batch_info", "sfcdd_batch_destroy",
     "sfcdd_estimate_spectrum", "sfcdd_richardson", "sfcdd_solve_homogeneous",
+    "sfcdd_batch_setup_each", "sfcdd_batch_combine",
 ]
 
 
@@ -104,6 +105,9 @@ def lib() -> C.CDLL:
     L.sfcdd_curve_order_noalloc.argtypes = [C.POINTER(C.c_int), C.c_int, P, P, C.c_void_p]
     L.sfcdd_batch_setup.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_double,
                                     C.POINTER(Options), C.POINTER(H)]
+    L.sfcdd_batch_setup_each.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
+                                         C.c_int, C.c_double, C.POINTER(Options), C.POINTER(H)]
+    L.sfcdd_batch_combine.argtypes = [H, C.POINTER(C.c_double), P, P, C.c_longlong, P]
     L.sfcdd_batch_offsets.argtypes = [H, C.POINTER(C.c_longlong)]
     L.sfcdd_batch_solve.argtypes = [H, P, P, C.c_double, C.c_int, C.POINTER(Stats),
                                     C.POINTER(Stats)]

@@ -1,7 +1,8 @@
 // Batched solve of many independent subgrid problems: the subproblems of the
 // sparse-grid combination technique (Sec. 2: every level vector l of the
 // layers |l|_1 = L + d - 1 - i gets its own anisotropic full grid, solved
-// independently), each with P subdomains of the two-level SFC Schwarz method.
+// independently), each with its own number P_s of subdomains of the two-level
+// SFC Schwarz method (eq. Pchoice: P = P_hat 2^{d-1-i} on layer i).
 //
 // One setup builds every subgrid into batch-wide arrays: a single radix sort of
 // (subgrid, Hilbert key), per-subgrid descriptors, one tile-skyline set of all
@@ -25,8 +26,17 @@ namespace sfcdd {
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 }
 
+// One subgrid of the combination: vector offset, levels, lexicographic strides
+// and the coefficient (-1)^i C(d-1, i) of its layer.
+struct CombSub {
+  int base;
+  int lev[MAXD];
+  int stride[MAXD];
+  double coef;
+};
+
 struct sfcdd_batch {
-  int nsub = 0, d = 0, P = 0, precision = 0, weighting = 1, flexible = 0;
+  int nsub = 0, d = 0, precision = 0, weighting = 1, flexible = 0;
   double gamma = 0;
   Store st = Store::F64;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
@@ -38,6 +48,9 @@ struct sfcdd_batch {
   int* invpad = nullptr;
   int *d_start = nullptr, *d_len = nullptr;
   double* d_omega = nullptr;
+  int* d_msub = nullptr;  // subgrid of every local matrix
+  CombSub* d_comb = nullptr;  // interpolation table of eq. combi (nsub)
+  std::vector<CombSub> h_comb;
   TileSetDev ts{};
   MatDesc* d_md = nullptr;
   void* ltiles = nullptr;  // Lh tiles (unit diagonal blocks implied)
@@ -111,6 +124,63 @@ __device__ __forceinline__ int lex_id_of(const GridDev& g, unsigned c) {
 }
 
 // ---------------------------------------------------------------------------
+// eq. combi: u_c(x) = sum_s c_s I_s u_s (x), I_s the piecewise multilinear
+// interpolant of subgrid s's nodal values (zero Dirichlet data on the
+// boundary nodes).  One warp per point; lane t sums the subgrids t, t + 32, ...
+// in order and the warp adds the 32 partial sums in a fixed tree, so the result
+// does not depend on timing.  Coordinates are clamped to [0, 1].  Corners on the
+// boundary are skipped before their weight is formed (a level-1 axis has one
+// interior node, so it halves the corners of its subgrid).
+template <int D>
+__global__ void __launch_bounds__(256) k_combine(const CombSub* __restrict__ cs, int nsub,
+                                                 const double* __restrict__ u,
+                                                 const double* __restrict__ pts, long long npts,
+                                                 double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < npts;
+       p += nwarps) {
+    double x[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) x[j] = fmin(fmax(pts[p * D + j], 0.0), 1.0);
+    double acc = 0.0;
+    for (int t = lane; t < nsub; t += 32) {
+      const CombSub& c = cs[t];
+      int k[D];
+      double fr[D];
+      unsigned lo_out = 0u, hi_out = 0u;  // axes whose lower / upper node is a boundary node
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int n = 1 << c.lev[j];
+        const double tt = x[j] * (double)n;
+        const int kk = min((int)floor(tt), n - 1);
+        k[j] = kk;
+        fr[j] = tt - (double)kk;
+        if (kk == 0) lo_out |= 1u << j;
+        if (kk + 1 == n) hi_out |= 1u << j;
+      }
+      double v = 0.0;
+      for (unsigned corner = 0; corner < (1u << D); ++corner) {
+        if ((~corner & lo_out) | (corner & hi_out)) continue;
+        double w = 1.0;
+        int id = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const int bit = (corner >> j) & 1;
+          w *= bit ? fr[j] : 1.0 - fr[j];
+          id += (k[j] + bit - 1) * c.stride[j];
+        }
+        v += w * u[(long long)c.base + id];
+      }
+      acc += c.coef * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[p] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Setup kernels.  grid.y = subgrid (or matrix), positions local to the subgrid.
 template <int D>
 __global__ void k_b_keygen(const SubDesc* __restrict__ sub, int kbits,
@@ -132,11 +202,12 @@ __global__ void k_b_invpad(const SubDesc* __restrict__ sub, const unsigned* __re
     invpad[sd.ibase + code[sd.base + p]] = p;
 }
 
-__global__ void k_b_env_local(const SubDesc* __restrict__ sub, int P, const unsigned* __restrict__ code,
-                              const int* __restrict__ invpad, TileSetDev ts, int* tfirst) {
+__global__ void k_b_env_local(const SubDesc* __restrict__ sub, const int* __restrict__ msub,
+                              const unsigned* __restrict__ code, const int* __restrict__ invpad,
+                              TileSetDev ts, int* tfirst) {
   const int m = blockIdx.y;
-  const SubDesc& sd = sub[m / P];
-  const int i = m % P;
+  const SubDesc& sd = sub[msub[m]];
+  const int i = m - sd.mat0;
   const int n = ts.n[m];
   const int fb = ts.vbase[m] / TILE;
   const int start = sd.pd.start[i];
@@ -168,13 +239,14 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_b_assemble_local(const SubDesc* __restrict__ sub, int P,
+__global__ void __launch_bounds__(256) k_b_assemble_local(const SubDesc* __restrict__ sub,
+                                                          const int* __restrict__ msub,
                                                           const unsigned* __restrict__ code,
                                                           const int* __restrict__ invpad,
                                                           TileSetDev ts, T* __restrict__ tiles) {
   __shared__ double sm[TILE2];
   const int m = blockIdx.y;
-  const SubDesc& sd = sub[m / P];
+  const SubDesc& sd = sub[msub[m]];
   const int nt = ts.nt[m];
   const int fb = ts.vbase[m] / TILE;
   const int idx = blockIdx.x;
@@ -185,7 +257,7 @@ __global__ void __launch_bounds__(256) k_b_assemble_local(const SubDesc* __restr
   __syncthreads();
   const int vb = ts.vbase[m];
   const LocalOrder lo{ts.lperm ? ts.lperm + vb : nullptr, ts.linv ? ts.linv + vb : nullptr};
-  assemble_local_tile(sd.g, code + sd.base, invpad + sd.ibase, sd.pd.start[m % P], ts.n[m], lo, a,
+  assemble_local_tile(sd.g, code + sd.base, invpad + sd.ibase, sd.pd.start[m - sd.mat0], ts.n[m], lo, a,
                       bb, sm);
   __syncthreads();
   T* out = tiles + ts.tbase[m] + (long long)idx * TILE2;
@@ -486,10 +558,12 @@ int build_graph(sfcdd_batch* b, int maxit) {
   return SFCDD_OK;
 }
 
-int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, double overlap,
-                     const sfcdd_options* opt) {
-  if (!levels || nsub < 1 || d < 1 || d > MAXD || P < 2 || !(overlap > 0))
+int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const int* Ps,
+                     double overlap, const sfcdd_options* opt) {
+  if (!levels || !Ps || nsub < 1 || d < 1 || d > MAXD || !(overlap > 0))
     return SFCDD_ERR_INVALID_ARG;
+  for (int si = 0; si < nsub; ++si)
+    if (Ps[si] < 2) return SFCDD_ERR_INVALID_ARG;
   sfcdd_options o;
   sfcdd_default_options(&o);
   if (opt) o = *opt;
@@ -498,7 +572,6 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
     return o.variant != SFCDD_ADDITIVE ? SFCDD_ERR_UNSUPPORTED : SFCDD_ERR_INVALID_ARG;
   b->nsub = nsub;
   b->d = d;
-  b->P = P;
   b->gamma = overlap;
   b->precision = o.precision;
   b->weighting = o.weighting;
@@ -520,12 +593,15 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   std::vector<int> N0s(nsub);
   long long ibase = 0, base = 0;
   int kbits = 0;
+  std::vector<int> pofs(nsub + 1, 0);  // first local matrix of every subgrid
   for (int si = 0; si < nsub; ++si) {
     SubDesc& sd = b->hsub[si];
+    const int P = Ps[si];
     long long N;
     int B;
     BTRY(make_grid(levels + (size_t)si * d, d, o.coeffs, sd.g, N, B));
     if (P > N) return SFCDD_ERR_INVALID_ARG;
+    pofs[si + 1] = pofs[si] + P;
     std::vector<int> st, ln;
     std::vector<double> om;
     int gf;
@@ -557,15 +633,20 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   while ((1 << sbits) < nsub) ++sbits;
   if (kbits + sbits > 64) return SFCDD_ERR_KEY_OVERFLOW;
   b->Ntot = (int)base;
-  BTRY(balloc(b, &b->d_start, (size_t)nsub * P));
-  BTRY(balloc(b, &b->d_len, (size_t)nsub * P));
-  BTRY(balloc(b, &b->d_omega, (size_t)nsub * P));
+  b->nlocal = pofs[nsub];
+  BTRY(balloc(b, &b->d_start, b->nlocal));
+  BTRY(balloc(b, &b->d_len, b->nlocal));
+  BTRY(balloc(b, &b->d_omega, b->nlocal));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_start, start_all.data(), start_all.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_len, len_all.data(), len_all.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_omega, omega_all.data(), omega_all.size() * sizeof(double), cudaMemcpyHostToDevice, s));
 
-  // matrices: locals s * P + i, coarse nsub * P + s
-  b->nlocal = nsub * P;
+  // matrices: locals pofs[s] + i, coarse nlocal + s
+  std::vector<int> hmsub(b->nlocal);
+  for (int si = 0; si < nsub; ++si)
+    for (int m = pofs[si]; m < pofs[si + 1]; ++m) hmsub[m] = si;
+  BTRY(balloc(b, &b->d_msub, b->nlocal));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_msub, hmsub.data(), b->nlocal * sizeof(int), cudaMemcpyHostToDevice, s));
   b->nmat = b->nlocal + nsub;
   std::vector<int> h_n(b->nmat);
   b->h_nt.assign(b->nmat, 0);
@@ -592,16 +673,26 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   long long g0base = 0;
   for (int si = 0; si < nsub; ++si) {
     SubDesc& sd = b->hsub[si];
-    sd.pd.start = b->d_start + (size_t)si * P;
-    sd.pd.len = b->d_len + (size_t)si * P;
-    sd.pd.omega = b->d_omega + (size_t)si * P;
-    sd.mat0 = si * P;
+    sd.pd.start = b->d_start + pofs[si];
+    sd.pd.len = b->d_len + pofs[si];
+    sd.pd.omega = b->d_omega + pofs[si];
+    sd.mat0 = pofs[si];
     sd.cmat = b->nlocal + si;
     sd.g0base = (int)g0base;
     g0base += (long long)b->h_nt[sd.cmat] * TILE;
   }
   BTRY(balloc(b, &b->dsub, nsub));
   SFCDD_CUDA_OK(cudaMemcpyAsync(b->dsub, b->hsub.data(), nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
+  BTRY(balloc(b, &b->d_comb, nsub));
+  b->h_comb.assign(nsub, CombSub{});
+  for (int si = 0; si < nsub; ++si) {
+    CombSub& c = b->h_comb[si];
+    c.base = b->hsub[si].base;
+    for (int j = 0; j < MAXD; ++j) {
+      c.lev[j] = j < d ? b->hsub[si].g.lev[j] : 0;
+      c.stride[j] = j < d ? b->hsub[si].g.stride[j] : 0;
+    }
+  }
 
   // curve order of every subgrid: one sort of (subgrid, key)
   unsigned long long* keys;
@@ -640,7 +731,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
     std::vector<int> mstart(b->nlocal), mN(b->nlocal), mcb(b->nlocal), lb(b->nlocal);
     long long tot = 0;
     for (int m = 0; m < b->nlocal; ++m) {
-      const SubDesc& sd = b->hsub[m / P];
+      const SubDesc& sd = b->hsub[hmsub[m]];
       mstart[m] = start_all[m];
       mN[m] = sd.pd.N;
       mcb[m] = sd.base;
@@ -676,8 +767,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
     b->ts.linv = linv;
   }
   launch_envelope_init(b->ts, b->nmat, max_nt_all, tfirst, s);
-  k_b_env_local<<<dim3((max_nl + 255) / 256, b->nlocal), 256, 0, s>>>(b->dsub, P, b->code,
-                                                                      b->invpad, b->ts, tfirst);
+  k_b_env_local<<<dim3((max_nl + 255) / 256, b->nlocal), 256, 0, s>>>(
+      b->dsub, b->d_msub, b->code, b->invpad, b->ts, tfirst);
   k_b_env_coarse<<<gsub, 256, 0, s>>>(b->dsub, b->code, b->invpad, b->ts, tfirst);
   std::vector<int> tf(nrows);
   SFCDD_CUDA_OK(cudaMemcpyAsync(tf.data(), tfirst, nrows * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -711,11 +802,11 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   switch (cst) {
     case Store::F64:
       k_b_assemble_local<double><<<dim3(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
-          b->dsub, P, b->code, b->invpad, b->ts, (double*)work_tiles);
+          b->dsub, b->d_msub, b->code, b->invpad, b->ts, (double*)work_tiles);
       break;
     default:
       k_b_assemble_local<float><<<dim3(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
-          b->dsub, P, b->code, b->invpad, b->ts, (float*)work_tiles);
+          b->dsub, b->d_msub, b->code, b->invpad, b->ts, (float*)work_tiles);
       break;
   }
   struct NoHook : LaunchHook {
@@ -763,8 +854,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, int P, 
   std::vector<MatDesc> md(b->nmat);
   for (int si = 0; si < nsub; ++si) {
     const SubDesc& sd = b->hsub[si];
-    for (int i = 0; i < P; ++i)
-      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)si * P + i], 0, si, 1, 1};
+    for (int i = 0; i < sd.pd.P; ++i)
+      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)sd.mat0 + i], 0, si, 1, 1};
     md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si, cslabs, 1};
   }
   BTRY(balloc(b, &b->d_md, b->nmat));
@@ -833,8 +924,8 @@ void batch_destroy(sfcdd_batch* b) {
 
 extern "C" {
 
-int sfcdd_batch_setup(const int* levels, int nsub, int d, int P, double overlap,
-                      const sfcdd_options* opt, sfcdd_batch** out) {
+int sfcdd_batch_setup_each(const int* levels, const int* P, int nsub, int d, double overlap,
+                           const sfcdd_options* opt, sfcdd_batch** out) {
   if (!out) return SFCDD_ERR_INVALID_ARG;
   *out = nullptr;
   sfcdd_batch* b = new (std::nothrow) sfcdd_batch();
@@ -847,6 +938,37 @@ int sfcdd_batch_setup(const int* levels, int nsub, int d, int P, double overlap,
     return rc;
   }
   *out = b;
+  return SFCDD_OK;
+}
+
+int sfcdd_batch_setup(const int* levels, int nsub, int d, int P, double overlap,
+                      const sfcdd_options* opt, sfcdd_batch** out) {
+  if (!out) return SFCDD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nsub < 1) return SFCDD_ERR_INVALID_ARG;
+  const std::vector<int> Ps(nsub, P);
+  return sfcdd_batch_setup_each(levels, Ps.data(), nsub, d, overlap, opt, out);
+}
+
+int sfcdd_batch_combine(sfcdd_batch* b, const double* coef_host, const double* u_dev,
+                        const double* points_dev, long long npts, double* out_dev) {
+  if (!b || !coef_host || !u_dev || npts < 0 || (npts > 0 && (!points_dev || !out_dev)))
+    return SFCDD_ERR_INVALID_ARG;
+  if (npts == 0) return SFCDD_OK;
+  for (int si = 0; si < b->nsub; ++si) {
+    if (!(coef_host[si] == coef_host[si])) return SFCDD_ERR_INVALID_ARG;
+    b->h_comb[si].coef = coef_host[si];
+  }
+  cudaStream_t s = b->stream;
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_comb, b->h_comb.data(), b->nsub * sizeof(CombSub),
+                                cudaMemcpyHostToDevice, s));
+  const long long warps_per_block = 256 / 32;
+  const long long blocks = std::min<long long>((npts + warps_per_block - 1) / warps_per_block,
+                                               152LL * 64);
+  SFCDD_DISPATCH_D(k_combine, b->d, (unsigned)blocks, 256, 0, s, b->d_comb, b->nsub, u_dev,
+                   points_dev, npts, out_dev);
+  SFCDD_CUDA_OK(cudaGetLastError());
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
   return SFCDD_OK;
 }
 

@@ -4,6 +4,7 @@ from __future__ import annotations
 
 import ctypes as C
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -205,9 +206,10 @@ class Solver:
 
 
 class BatchSolver:
-    """Many independent subgrid problems (same d, P, overlap, options), set up
-    together and solved in one CUDA-graph launch (sfcdd_batch_*).  Vectors are
-    the concatenation of the subgrids' lexicographic vectors at `offsets`."""
+    """Many independent subgrid problems (same d, overlap, options; P shared or
+    one per subgrid), set up together and solved in one CUDA-graph launch
+    (sfcdd_batch_*).  Vectors are the concatenation of the subgrids'
+    lexicographic vectors at `offsets`."""
 
     def __init__(self, levels_list, P, overlap, *, precision="fp64", weighting="omega", q=0,
                  coeffs=None, flexible=-1, stream=None, local_order="lex"):
@@ -234,8 +236,17 @@ class BatchSolver:
         opt.stream = C.c_void_p(stream.cuda_stream)
         flat = (C.c_int * (self.nsub * self.d))(*[l for lv in self.levels for l in lv])
         h = C.c_void_p()
-        check("sfcdd_batch_setup", L.sfcdd_batch_setup(flat, self.nsub, self.d, int(P),
-                                                       float(overlap), C.byref(opt), C.byref(h)))
+        if isinstance(P, (int, np.integer)):
+            check("sfcdd_batch_setup", L.sfcdd_batch_setup(flat, self.nsub, self.d, int(P),
+                                                           float(overlap), C.byref(opt),
+                                                           C.byref(h)))
+        else:
+            if len(P) != self.nsub:
+                raise ValueError("one subdomain count per subgrid")
+            Ps = (C.c_int * self.nsub)(*[int(p) for p in P])
+            check("sfcdd_batch_setup_each",
+                  L.sfcdd_batch_setup_each(flat, Ps, self.nsub, self.d, float(overlap),
+                                           C.byref(opt), C.byref(h)))
         self._h = h
         self._L = L
         offs = (C.c_longlong * (self.nsub + 1))()
@@ -261,6 +272,16 @@ class BatchSolver:
         if check_status:
             check("sfcdd_batch_solve", rc)
         return u, tot, [per[i] for i in range(self.nsub)]
+
+    def combine(self, coef, u: torch.Tensor, points: torch.Tensor):
+        """eq. combi at points (npts x d, device): sum_s coef[s] I_s u_s."""
+        cf = (C.c_double * self.nsub)(*[float(c) for c in coef])
+        pts = points.reshape(-1, self.d).contiguous()
+        out = torch.empty(pts.shape[0], dtype=torch.float64, device=pts.device)
+        check("sfcdd_batch_combine",
+              self._L.sfcdd_batch_combine(self._h, cf, _dev_ptr(u.contiguous()), _dev_ptr(pts),
+                                          int(pts.shape[0]), _dev_ptr(out)))
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
