@@ -70,10 +70,11 @@ typedef struct {
                            the factor's envelope shrinks to a band), 1 ascending curve position.
                            A_i^{-1} and therefore the preconditioner are the same either way. */
   int slabs_local;      /* row slabs per 64-row tile row in the local substitutions (one CTA
-                           each): 1 or 2; 0 (default) = 1.  Splitting shortens the FP64 GEMV on
-                           the dependency chain from one tile row to the next. */
-  int slabs_coarse;     /* the same for the coarse substitutions: 1 or 4; 0 (default) = 4.
-                           FP32 / BF16 local factors require 4 (INVALID_ARG otherwise). */
+                           each): 1, 2 or 4 (rows of 64, 32, 16); 0 (default) = 1.  Splitting
+                           shortens the GEMV on the dependency chain from one tile row to the
+                           next.  sfcdd_autotune picks it by measurement. */
+  int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 4.
+                           FP32 / BF16 local factors require 2 or 4 (INVALID_ARG otherwise). */
 } sfcdd_options;
 
 typedef struct {
@@ -188,7 +189,8 @@ int sfcdd_solve_homogeneous(sfcdd_handle* h, const double* x0_dev, double* u_dev
  * Vectors: the concatenation of the subgrids' vectors, each lexicographic, at
  * the offsets returned by sfcdd_batch_offsets (nsub + 1 entries, last = total).
  * Supported options: precision, weighting, q (<= 0: per-subgrid rule), flexible,
- * coeffs (shared), stream; variant must be SFCDD_ADDITIVE (else UNSUPPORTED).
+ * coeffs (shared), stream, slabs_local / slabs_coarse (defaults 1 and 1 for FP64,
+ * 1 and 4 otherwise); variant must be SFCDD_ADDITIVE (else UNSUPPORTED).
  * Errors as sfcdd_setup_ex / sfcdd_solve; per_sub (nsub entries) and total may
  * be NULL; total->iters is the largest iteration count, total->fail_index the
  * number of subgrids that did not converge. */
@@ -231,6 +233,26 @@ int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, in
  * eq. balSW adds the two coarse corrections and stencil applies of G).
  * curve_order as in sfcdd_apply_operator. */
 int sfcdd_apply_precond(sfcdd_handle* h, const double* g_dev, double* z_dev, int curve_order);
+
+/* Autotuner of the substitution tile shapes (the row slab a work item of the
+ * batched triangular solves covers: 64, 32 or 16 rows, for the local and the
+ * coarse factors).  Times `reps` preconditioner applies (device time, CUDA
+ * events, after two warm-up applies) for every admissible (slabs_local,
+ * slabs_coarse) pair, keeps the fastest in the handle and reports it.  The
+ * preconditioner's values do not depend on the choice.  Drops the captured
+ * iteration graph (rebuilt by the next solve).  Synchronises the stream.
+ * Errors: INVALID_ARG (reps < 1), TIMEOUT, CUDA. */
+typedef struct {
+  int slabs_local;      /* chosen slab count of the local substitutions */
+  int slabs_coarse;     /* chosen slab count of the coarse substitutions */
+  double apply_ms;      /* mean device time of one apply with the choice */
+  int candidates;       /* configurations timed */
+} sfcdd_tuning;
+int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out);
+/* The same for a batch (declared below): times `reps` pairs of batched forward
+ * and backward substitutions over every subgrid for each slab pair and keeps
+ * the fastest; drops the captured solve graph.  Errors as sfcdd_autotune. */
+int sfcdd_batch_autotune(sfcdd_batch* b, int reps, sfcdd_tuning* out);
 
 /* Introspection for parity checks (all synchronise the stream). */
 int sfcdd_get_info(const sfcdd_handle* h, sfcdd_info* info);

@@ -32,8 +32,13 @@ EXPORTS = [
     "sfcdd_status_string", "sfcdd_curve_order_noalloc", "sfcdd_batch_setup",
     "sfcdd_batch_offsets", "sfcdd_batch_solve", "sfcdd_batch_info", "sfcdd_batch_destroy",
     "sfcdd_estimate_spectrum", "sfcdd_richardson", "sfcdd_solve_homogeneous",
-    "sfcdd_batch_setup_each", "sfcdd_batch_combine",
+    "sfcdd_batch_setup_each", "sfcdd_batch_combine", "sfcdd_autotune", "sfcdd_batch_autotune",
 ]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("slabs_local", C.c_int), ("slabs_coarse", C.c_int), ("apply_ms", C.c_double),
+                ("candidates", C.c_int)]
 
 
 class Options(C.Structure):
@@ -108,6 +113,8 @@ def lib() -> C.CDLL:
     L.sfcdd_batch_setup_each.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
                                          C.c_int, C.c_double, C.POINTER(Options), C.POINTER(H)]
     L.sfcdd_batch_combine.argtypes = [H, C.POINTER(C.c_double), P, P, C.c_longlong, P]
+    L.sfcdd_autotune.argtypes = [H, C.c_int, C.POINTER(Tuning)]
+    L.sfcdd_batch_autotune.argtypes = [H, C.c_int, C.POINTER(Tuning)]
     L.sfcdd_batch_offsets.argtypes = [H, C.POINTER(C.c_longlong)]
     L.sfcdd_batch_solve.argtypes = [H, P, P, C.c_double, C.c_int, C.POINTER(Stats),
                                     C.POINTER(Stats)]

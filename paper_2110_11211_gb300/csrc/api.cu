@@ -405,6 +405,15 @@ int dalloc(sfcdd_handle* h, T** p, size_t count) {
   return SFCDD_OK;
 }
 
+// Slab counts the substitution kernel is built for: local rows of 64, 32 or 16,
+// coarse rows of 64, 32 or 16.  FP32 / BF16 launches size their shared memory
+// for the local tiles, so a full 64-row FP64 coarse stage needs an FP64 launch.
+bool valid_slabs(int precision, int nsub_local, int nsub_coarse) {
+  const bool l = nsub_local == 1 || nsub_local == 2 || nsub_local == 4;
+  const bool c = nsub_coarse == 1 || nsub_coarse == 2 || nsub_coarse == 4;
+  return l && c && (precision == SFCDD_FP64 || nsub_coarse != 1);
+}
+
 void dfree(sfcdd_handle* h, void* p) {
   if (!p) return;
   for (auto& a : h->allocs)
@@ -590,6 +599,58 @@ void enqueue_iteration(sfcdd_handle* h, Prof& pf) {
   pf.run(SFCDD_K_VECTOR, [&] { launch_update_p(h->N, h->z, h->p, h->sc, s); });
 }
 
+// Substitution work items: the per-matrix descriptors (slab counts: local rows
+// of 64 / nsub_local, coarse rows of 64 / nsub_coarse) and the work lists of
+// tile-row slabs in dependency-safe order.  Re-running it with other slab
+// counts replaces both and drops the captured iteration graph.
+int configure_substitution(sfcdd_handle* h, int nsub_local, int nsub_coarse) {
+  const int P = h->P;
+  cudaStream_t s = h->stream;
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  if (h->iter_graph) {
+    cudaGraphExecDestroy(h->iter_graph);
+    h->iter_graph = nullptr;
+  }
+  h->nsub_local = nsub_local;
+  h->nsub_coarse = nsub_coarse;
+  std::vector<MatDesc> md(P + 1);
+  for (int m = 0; m < P; ++m) md[m] = {0, h->N, h->h_start[m], 0, 0, nsub_local, 1};
+  md[P] = {0, h->N0, 0, 1, 0, nsub_coarse, h->cb_coarse};
+  if (!h->d_md) TRY(dalloc(h, &h->d_md, P + 1));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_md, md.data(), (P + 1) * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
+  std::vector<int> nsub(P + 1, nsub_local);
+  nsub[P] = nsub_coarse;
+  for (int li = 0; li < 3; ++li) {
+    std::vector<char> include(P + 1, 1);
+    if (li == LIST_MAIN) {
+      if (h->variant == SFCDD_COARSE_ONLY)
+        for (int m = 0; m < P; ++m) include[m] = 0;
+      if (h->variant == SFCDD_ONE_LEVEL) include[P] = 0;
+    } else {
+      if (h->variant != SFCDD_BALANCED) continue;
+      if (li == LIST_LOCAL) include[P] = 0;
+      else
+        for (int m = 0; m < P; ++m) include[m] = 0;
+    }
+    std::vector<TrsvWork> wf, wb;
+    build_worklists(h->h_nt, include, nsub, wf, wb);
+    auto& wl = h->lists[li];
+    dfree(h, wl.f);
+    dfree(h, wl.b);
+    wl.n = (int)wf.size();
+    TRY(dalloc(h, &wl.f, wl.n));
+    TRY(dalloc(h, &wl.b, wl.n));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(wl.f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(wl.b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+    if (!wl.tf) TRY(dalloc(h, &wl.tf, 1));
+    if (!wl.tb) TRY(dalloc(h, &wl.tb, 1));
+    SFCDD_CUDA_OK(cudaMemsetAsync(wl.tf, 0, sizeof(unsigned long long), s));
+    SFCDD_CUDA_OK(cudaMemsetAsync(wl.tb, 0, sizeof(unsigned long long), s));
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
+  }
+  return SFCDD_OK;
+}
+
 int build_graph(sfcdd_handle* h) {
   if (h->iter_graph) return SFCDD_OK;
   long long before[SFCDD_K_COUNT];
@@ -660,11 +721,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     return SFCDD_ERR_INVALID_ARG;
   h->nsub_local = o.slabs_local == 0 ? 1 : o.slabs_local;
   h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
-  if ((h->nsub_local != 1 && h->nsub_local != 2) || (h->nsub_coarse != 1 && h->nsub_coarse != 4))
-    return SFCDD_ERR_INVALID_ARG;
-  // FP32 / BF16 launches size their shared memory for the local tiles: the
-  // FP64 coarse rows then run in 16-row slabs
-  if (h->precision != SFCDD_FP64 && h->nsub_coarse != 4) return SFCDD_ERR_INVALID_ARG;
+  if (!valid_slabs(h->precision, h->nsub_local, h->nsub_coarse)) return SFCDD_ERR_INVALID_ARG;
   h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
   h->stream = (cudaStream_t)o.stream;
   h->profiling = o.profile != 0;
@@ -984,47 +1041,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   cudaEventDestroy(ev_coarse);
   SFCDD_CUDA_OK(cudaGetLastError());
 
-  // per-matrix right-hand-side descriptors (one problem: scalars index 0)
-  {
-    std::vector<MatDesc> md(P + 1);
-    for (int m = 0; m < P; ++m) md[m] = {0, h->N, h->h_start[m], 0, 0, h->nsub_local, 1};
-    md[P] = {0, h->N0, 0, 1, 0, h->nsub_coarse, h->cb_coarse};
-    TRY(dalloc(h, &h->d_md, P + 1));
-    SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_md, md.data(), (P + 1) * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
-    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
-  }
-
-  // substitution work lists: tile rows in dependency-safe order
-  {
-    std::vector<int> nsub(P + 1, h->nsub_local);
-    nsub[P] = h->nsub_coarse;
-    for (int li = 0; li < 3; ++li) {
-      std::vector<char> include(P + 1, 1);
-      if (li == LIST_MAIN) {
-        if (h->variant == SFCDD_COARSE_ONLY)
-          for (int m = 0; m < P; ++m) include[m] = 0;
-        if (h->variant == SFCDD_ONE_LEVEL) include[P] = 0;
-      } else {
-        if (h->variant != SFCDD_BALANCED) continue;
-        if (li == LIST_LOCAL) include[P] = 0;
-        else
-          for (int m = 0; m < P; ++m) include[m] = 0;
-      }
-      std::vector<TrsvWork> wf, wb;
-      build_worklists(h->h_nt, include, nsub, wf, wb);
-      auto& wl = h->lists[li];
-      wl.n = (int)wf.size();
-      TRY(dalloc(h, &wl.f, wl.n));
-      TRY(dalloc(h, &wl.b, wl.n));
-      SFCDD_CUDA_OK(cudaMemcpyAsync(wl.f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-      SFCDD_CUDA_OK(cudaMemcpyAsync(wl.b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-      TRY(dalloc(h, &wl.tf, 1));
-      TRY(dalloc(h, &wl.tb, 1));
-      SFCDD_CUDA_OK(cudaMemsetAsync(wl.tf, 0, sizeof(unsigned long long), s));
-      SFCDD_CUDA_OK(cudaMemsetAsync(wl.tb, 0, sizeof(unsigned long long), s));
-      SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
-    }
-  }
+  TRY(configure_substitution(h, h->nsub_local, h->nsub_coarse));
   if (h->variant == SFCDD_BALANCED)
     for (int k = 0; k < 4; ++k) TRY(dalloc(h, &h->bal[k], N));
   TRY(dalloc(h, &h->ybuf, h->vtotal));
@@ -1462,6 +1479,65 @@ int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, in
   }
   SFCDD_CUDA_OK(cudaGetLastError());
   pf.collect();
+  return SFCDD_OK;
+}
+
+int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out) {
+  if (!h || reps < 1) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  const bool prof = h->profiling;
+  long long saved[SFCDD_K_COUNT];
+  memcpy(saved, h->launches, sizeof(saved));
+  h->profiling = false;
+  // the timed applies read a zero vector: the substitution streams the same
+  // tiles whatever the values
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->tmp, 0, (size_t)h->N * sizeof(double), s));
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  int best_l = h->nsub_local, best_c = h->nsub_coarse, cand = 0;
+  float best = -1.f;
+  int rc = SFCDD_OK;
+  const int opts[3] = {1, 2, 4};
+  for (int il = 0; il < 3 && rc == SFCDD_OK; ++il)
+    for (int ic = 0; ic < 3 && rc == SFCDD_OK; ++ic) {
+      const int sl = opts[il], sc = opts[ic];
+      if (!valid_slabs(h->precision, sl, sc)) continue;
+      rc = configure_substitution(h, sl, sc);
+      if (rc != SFCDD_OK) break;
+      Prof pf(h, s);
+      for (int k = 0; k < 2; ++k) enqueue_apply(h, pf, h->tmp, h->z, nullptr);
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < reps; ++k) enqueue_apply(h, pf, h->tmp, h->z, nullptr);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = SFCDD_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ++cand;
+      if (best < 0.f || ms < best) {
+        best = ms;
+        best_l = sl;
+        best_c = sc;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  memcpy(h->launches, saved, sizeof(saved));
+  h->profiling = prof;
+  if (rc != SFCDD_OK) return rc;
+  int fi = 0;
+  const int ec = check_err(h, &fi);
+  if (ec != 0) return ec;
+  TRY(configure_substitution(h, best_l, best_c));
+  if (out) {
+    out->slabs_local = best_l;
+    out->slabs_coarse = best_c;
+    out->apply_ms = best / reps;
+    out->candidates = cand;
+  }
   return SFCDD_OK;
 }
 

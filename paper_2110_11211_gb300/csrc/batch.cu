@@ -51,6 +51,8 @@ struct sfcdd_batch {
   int* d_msub = nullptr;  // subgrid of every local matrix
   CombSub* d_comb = nullptr;  // interpolation table of eq. combi (nsub)
   std::vector<CombSub> h_comb;
+  std::vector<int> h_start;   // first curve position of every local matrix
+  int nsub_local = 1, nsub_coarse = 1;
   TileSetDev ts{};
   MatDesc* d_md = nullptr;
   void* ltiles = nullptr;  // Lh tiles (unit diagonal blocks implied)
@@ -100,6 +102,55 @@ int balloc(sfcdd_batch* b, T** p, size_t count) {
     int _rc = (x);                   \
     if (_rc != SFCDD_OK) return _rc; \
   } while (0)
+
+void bfree(sfcdd_batch* b, void* p) {
+  if (!p) return;
+  for (auto& a : b->allocs)
+    if (a == p) {
+      cudaFree(p);
+      a = nullptr;
+    }
+}
+
+// Per-matrix substitution descriptors and the work lists of (matrix, tile row,
+// slab) items for the given slab counts; drops the captured solve graph.
+int batch_configure(sfcdd_batch* b, int nsub_local, int nsub_coarse) {
+  cudaStream_t s = b->stream;
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_maxit = -1;
+  }
+  b->nsub_local = nsub_local;
+  b->nsub_coarse = nsub_coarse;
+  std::vector<MatDesc> md(b->nmat);
+  std::vector<int> nsl(b->nmat, nsub_local);
+  for (int si = 0; si < b->nsub; ++si) {
+    const SubDesc& sd = b->hsub[si];
+    for (int i = 0; i < sd.pd.P; ++i)
+      md[sd.mat0 + i] = {sd.base, sd.pd.N, b->h_start[(size_t)sd.mat0 + i], 0, si, nsub_local, 1};
+    md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si, nsub_coarse, 1};
+    nsl[sd.cmat] = nsub_coarse;
+  }
+  if (!b->d_md) BTRY(balloc(b, &b->d_md, b->nmat));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_md, md.data(), b->nmat * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
+  std::vector<TrsvWork> wf, wb;
+  build_worklists(b->h_nt, std::vector<char>(b->nmat, 1), nsl, wf, wb);
+  bfree(b, b->work_f);
+  bfree(b, b->work_b);
+  b->nwork = (int)wf.size();
+  BTRY(balloc(b, &b->work_f, b->nwork));
+  BTRY(balloc(b, &b->work_b, b->nwork));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+  if (!b->ticket_f) BTRY(balloc(b, &b->ticket_f, 1));
+  if (!b->ticket_b) BTRY(balloc(b, &b->ticket_b, 1));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_f, 0, sizeof(unsigned long long), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_b, 0, sizeof(unsigned long long), s));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
+  return SFCDD_OK;
+}
 
 // Deterministic block sum over BT threads; every thread gets the total.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -848,31 +899,17 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   b->factor_bytes = b->sky.ltiles * TILE2 * (b->precision == 0 ? 8 : b->precision == 1 ? 4 : 2) +
                     b->sky.ctiles * TILE2 * 8;
 
-  // substitution descriptors and work lists
-  // FP32 / BF16 substitution launches run the FP64 coarse rows in 16-row slabs
-  const int cslabs = b->st == Store::F64 ? 1 : 4;
-  std::vector<MatDesc> md(b->nmat);
-  for (int si = 0; si < nsub; ++si) {
-    const SubDesc& sd = b->hsub[si];
-    for (int i = 0; i < sd.pd.P; ++i)
-      md[sd.mat0 + i] = {sd.base, sd.pd.N, start_all[(size_t)sd.mat0 + i], 0, si, 1, 1};
-    md[sd.cmat] = {sd.g0base, sd.N0, 0, 1, si, cslabs, 1};
+  // substitution descriptors and work lists (FP32 / BF16 launches run the FP64
+  // coarse rows in 16-row slabs; sfcdd_batch_autotune may change both counts)
+  b->h_start = start_all;
+  {
+    const int sl = o.slabs_local == 0 ? 1 : o.slabs_local;
+    const int sc = o.slabs_coarse == 0 ? (b->st == Store::F64 ? 1 : 4) : o.slabs_coarse;
+    const bool ok = (sl == 1 || sl == 2 || sl == 4) && (sc == 1 || sc == 2 || sc == 4) &&
+                    (b->st == Store::F64 || sc != 1);
+    if (!ok) return SFCDD_ERR_INVALID_ARG;
+    BTRY(batch_configure(b, sl, sc));
   }
-  BTRY(balloc(b, &b->d_md, b->nmat));
-  SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_md, md.data(), b->nmat * sizeof(MatDesc), cudaMemcpyHostToDevice, s));
-  std::vector<TrsvWork> wf, wb;
-  std::vector<int> nsl(b->nmat, 1);
-  for (int si = 0; si < nsub; ++si) nsl[b->hsub[si].cmat] = cslabs;
-  build_worklists(b->h_nt, std::vector<char>(b->nmat, 1), nsl, wf, wb);
-  b->nwork = (int)wf.size();
-  BTRY(balloc(b, &b->work_f, b->nwork));
-  BTRY(balloc(b, &b->work_b, b->nwork));
-  SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_f, wf.data(), wf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-  SFCDD_CUDA_OK(cudaMemcpyAsync(b->work_b, wb.data(), wb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
-  BTRY(balloc(b, &b->ticket_f, 1));
-  BTRY(balloc(b, &b->ticket_b, 1));
-  SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_f, 0, sizeof(unsigned long long), s));
-  SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_b, 0, sizeof(unsigned long long), s));
   BTRY(balloc(b, &b->ybuf, vb));
   BTRY(balloc(b, &b->dbuf, vb));
   BTRY(balloc(b, &b->zcbuf, vb));
@@ -1039,6 +1076,65 @@ int sfcdd_batch_solve(sfcdd_batch* b, const double* f_dev, double* u_dev, double
     total->solve_ms = ms;
   }
   return rc;
+}
+
+int sfcdd_batch_autotune(sfcdd_batch* b, int reps, sfcdd_tuning* out) {
+  if (!b || reps < 1) return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = b->stream;
+  // a substitution pair over every subgrid: the batched triangular solves of
+  // one PCG iteration, without the converged-subgrid early exit
+  auto pair = [&]() {
+    TrsvArgs af = batch_trsv_args(b, true), ab = batch_trsv_args(b, false);
+    af.sc = nullptr;
+    ab.sc = nullptr;
+    launch_trsv_fwd(af, b->st, s);
+    launch_trsv_bwd(ab, b->st, s);
+  };
+  SFCDD_CUDA_OK(cudaMemsetAsync(b->r, 0, (size_t)b->Ntot * sizeof(double), s));
+  cudaEvent_t e0, e1;
+  SFCDD_CUDA_OK(cudaEventCreate(&e0));
+  SFCDD_CUDA_OK(cudaEventCreate(&e1));
+  const int opts[3] = {1, 2, 4};
+  int best_l = b->nsub_local, best_c = b->nsub_coarse, cand = 0, rc = SFCDD_OK;
+  float best = -1.f;
+  for (int il = 0; il < 3 && rc == SFCDD_OK; ++il)
+    for (int ic = 0; ic < 3 && rc == SFCDD_OK; ++ic) {
+      const int sl = opts[il], sc = opts[ic];
+      if (b->st != Store::F64 && sc == 1) continue;  // 64-row FP64 stage: FP64 launches only
+      rc = batch_configure(b, sl, sc);
+      if (rc != SFCDD_OK) break;
+      for (int k = 0; k < 2; ++k) pair();
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < reps; ++k) pair();
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = SFCDD_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ++cand;
+      if (best < 0.f || ms < best) {
+        best = ms;
+        best_l = sl;
+        best_c = sc;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SFCDD_OK) return rc;
+  ErrWord e{};
+  SFCDD_CUDA_OK(cudaMemcpyAsync(&e, b->err, sizeof(ErrWord), cudaMemcpyDeviceToHost, s));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  if (e.code != 0) return e.code;
+  BTRY(batch_configure(b, best_l, best_c));
+  if (out) {
+    out->slabs_local = best_l;
+    out->slabs_coarse = best_c;
+    out->apply_ms = best / reps;
+    out->candidates = cand;
+  }
+  return SFCDD_OK;
 }
 
 int sfcdd_batch_info(const sfcdd_batch* b, long long* n_total, long long* factor_bytes,

@@ -369,14 +369,21 @@ __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
         done = true;
       }
     }
-    if (!done)
-      sweep_item<double, double, 16, FWD, PL::RING>(a, a.ctiles, a.cut, wk.mat, wk.row, wk.slab,
-                                                     md.cb, sm);
+    if (!done) {
+      if (md.nsub == 2)
+        sweep_item<double, double, 32, FWD, PL::RING>(a, a.ctiles, a.cut, wk.mat, wk.row, wk.slab,
+                                                       md.cb, sm);
+      else
+        sweep_item<double, double, 16, FWD, PL::RING>(a, a.ctiles, a.cut, wk.mat, wk.row, wk.slab,
+                                                       md.cb, sm);
+    }
   } else {
     const T* lt = reinterpret_cast<const T*>(a.ltiles);
     const T* ut = reinterpret_cast<const T*>(a.lut);
     if (md.nsub == 2)
       sweep_item<T, A, 32, FWD, PL::RING>(a, lt, ut, wk.mat, wk.row, wk.slab, md.cb, sm);
+    else if (md.nsub == 4)
+      sweep_item<T, A, 16, FWD, PL::RING>(a, lt, ut, wk.mat, wk.row, wk.slab, md.cb, sm);
     else
       sweep_item<T, A, 64, FWD, PL::RING>(a, lt, ut, wk.mat, wk.row, 0, md.cb, sm);
   }

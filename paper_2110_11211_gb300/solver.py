@@ -8,7 +8,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import Info, Options, Stats, check
+from ._lib import Info, Options, Stats, Tuning, check
 
 
 def _dev_ptr(t: torch.Tensor, dtype=torch.float64) -> int:
@@ -143,6 +143,13 @@ class Solver:
             check("sfcdd_solve_homogeneous", rc)
         return u, st
 
+    def autotune(self, reps=5):
+        """Pick the substitution slab shapes by timing preconditioner applies."""
+        t = Tuning()
+        check("sfcdd_autotune", self._L.sfcdd_autotune(self._h, int(reps), C.byref(t)))
+        return {"slabs_local": t.slabs_local, "slabs_coarse": t.slabs_coarse,
+                "apply_ms": t.apply_ms, "candidates": t.candidates}
+
     def apply_operator(self, x: torch.Tensor, curve_order=False):
         y = torch.empty_like(x)
         check("sfcdd_apply_operator",
@@ -212,7 +219,8 @@ class BatchSolver:
     lexicographic vectors at `offsets`."""
 
     def __init__(self, levels_list, P, overlap, *, precision="fp64", weighting="omega", q=0,
-                 coeffs=None, flexible=-1, stream=None, local_order="lex"):
+                 coeffs=None, flexible=-1, stream=None, local_order="lex", slabs_local=0,
+                 slabs_coarse=0):
         L = _lib.lib()
         self.levels = [tuple(int(l) for l in lv) for lv in levels_list]
         self.nsub = len(self.levels)
@@ -230,6 +238,8 @@ class BatchSolver:
         opt.precision = _lib.PRECISION[precision]
         opt.flexible = int(flexible)
         opt.local_order = {"lex": 0, "curve": 1}[local_order]
+        opt.slabs_local = int(slabs_local)
+        opt.slabs_coarse = int(slabs_coarse)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -272,6 +282,13 @@ class BatchSolver:
         if check_status:
             check("sfcdd_batch_solve", rc)
         return u, tot, [per[i] for i in range(self.nsub)]
+
+    def autotune(self, reps=3):
+        """Pick the substitution slab shapes by timing batched substitution pairs."""
+        t = Tuning()
+        check("sfcdd_batch_autotune", self._L.sfcdd_batch_autotune(self._h, int(reps), C.byref(t)))
+        return {"slabs_local": t.slabs_local, "slabs_coarse": t.slabs_coarse,
+                "apply_ms": t.apply_ms, "candidates": t.candidates}
 
     def combine(self, coef, u: torch.Tensor, points: torch.Tensor):
         """eq. combi at points (npts x d, device): sum_s coef[s] I_s u_s."""

@@ -1,0 +1,93 @@
+"""Autotuner of the substitution tile shapes (sfcdd_autotune, sfcdd_batch_autotune).
+
+Every slab shape runs the same arithmetic per row (the same tiles in the same
+order, only the rows a CTA covers change), so the preconditioner may differ by
+rounding at most (bar: relative 1e-14 in FP64); after tuning, solves equal the
+untuned ones to the solve tolerance and the oracle's iteration counts.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import exact
+from paper_2110_11211_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2110_11211_gb300.build import build
+    build()
+
+
+SHAPES = [(sl, sc) for sl in (1, 2, 4) for sc in (1, 2, 4)]
+
+
+@pytest.mark.parametrize("precision,variant", [("fp64", "additive"), ("fp64", "balanced"),
+                                               ("fp32", "additive"), ("bf16", "additive")])
+def test_every_slab_shape_gives_the_same_preconditioner(precision, variant):
+    from paper_2110_11211_gb300.solver import Solver
+    levels, P, gamma = (7, 5, 4), 24, 0.5
+    g = torch.tensor(inputs.uniform(61, inputs.grid_size(levels)), device="cuda")
+    ref = None
+    for sl, sc in SHAPES:
+        if precision != "fp64" and sc == 1:
+            continue
+        with Solver(levels, P, gamma, precision=precision, variant=variant, slabs_local=sl,
+                    slabs_coarse=sc) as s:
+            z = s.apply_precond(g)
+        if ref is None:
+            ref = z
+        tol = 1e-14 if precision == "fp64" else 1e-6
+        assert float(torch.linalg.norm(z - ref) / torch.linalg.norm(ref)) <= tol, (sl, sc)
+
+
+def test_autotune_keeps_the_solution():
+    from paper_2110_11211_gb300.solver import Solver
+    levels, P, gamma = (9, 5, 3), 64, 1.0
+    f_np = inputs.uniform(62, inputs.grid_size(levels))
+    f = torch.tensor(f_np, device="cuda")
+    with Solver(levels, P, gamma) as s:
+        u0, st0 = s.solve(f, rtol=1e-10)
+        t = s.autotune(reps=3)
+        assert t["slabs_local"] in (1, 2, 4) and t["slabs_coarse"] in (1, 2, 4)
+        assert t["candidates"] == 9 and t["apply_ms"] > 0
+        u1, st1 = s.solve(f, rtol=1e-10)
+    assert abs(st1.iters - st0.iters) <= 1
+    assert float(torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)) <= 1e-9
+    ue = exact.solve(levels, f_np)
+    assert np.linalg.norm(u1.cpu().numpy() - ue) <= 1e-8 * np.linalg.norm(ue)
+
+
+def test_autotune_low_precision_skips_full_coarse_rows():
+    from paper_2110_11211_gb300.solver import Solver
+    with Solver((8, 4, 3), 32, 0.5, precision="bf16") as s:
+        t = s.autotune(reps=2)
+    assert t["candidates"] == 6 and t["slabs_coarse"] in (2, 4)
+
+
+def test_invalid_slab_options_are_rejected():
+    from paper_2110_11211_gb300._lib import SfcddError
+    from paper_2110_11211_gb300.solver import Solver
+    for kw in (dict(slabs_local=3), dict(slabs_coarse=8),
+               dict(precision="fp32", slabs_coarse=1)):
+        with pytest.raises(SfcddError):
+            Solver((6, 4), 8, 0.5, **kw)
+
+
+def test_batch_autotune_keeps_the_solutions():
+    from paper_2110_11211_gb300.solver import BatchSolver
+    levels = inputs.combi_levels(3, (9,))
+    f = torch.tensor(inputs.uniform(63, sum(inputs.grid_size(lv) for lv in levels)),
+                     device="cuda")
+    with BatchSolver(levels, 16, 0.5, precision="fp32") as b:
+        u0, tot0, per0 = b.solve(f, rtol=1e-10)
+        t = b.autotune(reps=2)
+        assert t["candidates"] == 6
+        u1, tot1, per1 = b.solve(f, rtol=1e-10)
+    assert tot1.fail_index == 0
+    assert all(abs(p.iters - q.iters) <= 1 for p, q in zip(per0, per1))
+    assert float(torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)) <= 1e-9
