@@ -75,6 +75,11 @@ typedef struct {
                            next.  sfcdd_autotune picks it by measurement. */
   int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 4.
                            FP32 / BF16 local factors require 2 or 4 (INVALID_ARG otherwise). */
+  int tensor_cores;     /* FP32 / BF16 local factors: the panel and trailing-update tile
+                           products of the factorization on the tensor cores (tcgen05, TF32
+                           operands with the hi/lo split, FP32 accumulation: FP32-accurate)
+                           when 1 or -1 (default), on CUDA cores when 0.  FP64 factors: the
+                           tile products stay on the FP64 units (1 is UNSUPPORTED). */
 } sfcdd_options;
 
 typedef struct {

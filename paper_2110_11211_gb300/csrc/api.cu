@@ -357,6 +357,7 @@ struct sfcdd_handle {
   long long ltile_elems = 0, ctile_elems = 0;
   int max_nt = 0, nt0 = 0, max_ltiles = 0, max_ctiles = 0;
   int nsub_local = 1, nsub_coarse = 4;
+  bool tensor_cores = false;  // FP32 factorization tile products on tcgen05
   int cb_coarse = 4;  // tiles per unit diagonal block of the coarse substitution form
   long long fwd_tiles_l = 0, bwd_tiles_l = 0, fwd_tiles_c = 0, bwd_tiles_c = 0;
   // substitution work lists (each with its own ticket counters: the items of a
@@ -722,6 +723,9 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->nsub_local = o.slabs_local == 0 ? 1 : o.slabs_local;
   h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
   if (!valid_slabs(h->precision, h->nsub_local, h->nsub_coarse)) return SFCDD_ERR_INVALID_ARG;
+  if (o.tensor_cores < -1 || o.tensor_cores > 1) return SFCDD_ERR_INVALID_ARG;
+  if (h->precision == SFCDD_FP64 && o.tensor_cores == 1) return SFCDD_ERR_UNSUPPORTED;
+  h->tensor_cores = h->precision != SFCDD_FP64 && o.tensor_cores != 0;
   h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
   h->stream = (cudaStream_t)o.stream;
   h->profiling = o.profile != 0;
@@ -1014,7 +1018,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
                             work_tiles, compute_st, s);
     });
     factor_tiles(h->ts, 0, P, h->max_nt, h->col_max_local.data(), work_tiles, compute_st, diag_cnt,
-                 h->err, s, &pf, compute_st == Store::F64 ? 4 : 1);
+                 h->err, s, &pf, compute_st == Store::F64 ? 4 : 1, h->tensor_cores);
   }
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
   void* work_ut = nullptr;
@@ -1280,6 +1284,7 @@ void sfcdd_default_options(sfcdd_options* opt) {
   opt->local_order = 0;
   opt->slabs_local = 0;
   opt->slabs_coarse = 0;
+  opt->tensor_cores = -1;
 }
 
 int sfcdd_setup_ex(const int* levels, int d, int P, double overlap, const sfcdd_options* opt,

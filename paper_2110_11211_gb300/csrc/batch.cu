@@ -618,8 +618,9 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   sfcdd_options o;
   sfcdd_default_options(&o);
   if (opt) o = *opt;
+  if (o.precision == SFCDD_FP64 && o.tensor_cores == 1) return SFCDD_ERR_UNSUPPORTED;
   if (o.variant != SFCDD_ADDITIVE || o.precision < 0 || o.precision > 2 || o.weighting < 0 ||
-      o.weighting > 1)
+      o.weighting > 1 || o.tensor_cores < -1 || o.tensor_cores > 1)
     return o.variant != SFCDD_ADDITIVE ? SFCDD_ERR_UNSUPPORTED : SFCDD_ERR_INVALID_ARG;
   b->nsub = nsub;
   b->d = d;
@@ -865,7 +866,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
     void after(int) override {}
   } nohook;
   factor_tiles(b->ts, 0, b->nlocal, b->max_nt_local, b->sky.col_max_local.data(), work_tiles, cst,
-               diag_cnt, b->err, s, &nohook);
+               diag_cnt, b->err, s, &nohook, 1, cst != Store::F64 && o.tensor_cores != 0);
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
   void* work_ut = nullptr;
   BTRY(balloc(b, (unsigned char**)&work_ut, b->sky.ltiles * TILE2 * esz));

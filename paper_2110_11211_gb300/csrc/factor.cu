@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "tc_tile.cuh"
 
 namespace sfcdd {
 
@@ -469,6 +470,180 @@ __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 panel and trailing update on the tensor cores (tcgen05, TF32 operands
+// with the error-compensated hi/lo split, FP32 accumulation in tensor memory;
+// see tc_tile.cuh).  One CTA computes two tile products that share their right
+// operand as one M = 128 MMA chain: rows 0-63 of A are the first tile, rows
+// 64-127 the second (or the first again when there is no second).
+
+// Stage, multiply, and hand each thread its 32 accumulator columns; returns
+// false (error word set) when the MMA completion wait ran out.
+__device__ __forceinline__ bool tc_product(unsigned char* dsm, const float* a0, const float* a1,
+                                           const float* b, float (&v)[32], int& row, int& col0,
+                                           uint32_t& tmem, ErrWord* err, int m) {
+  using namespace tc;
+  unsigned char* ahi = dsm;
+  unsigned char* alo = dsm + A_BYTES;
+  unsigned char* bhi = dsm + 2 * A_BYTES;
+  unsigned char* blo = bhi + B_BYTES;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(blo + B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  if (threadIdx.x < 32) tmem_alloc(tslot);
+  if (threadIdx.x == 0) {
+    mbar_init1(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  stage_tile(ahi, alo, a0, 0);
+  stage_tile(ahi, alo, a1, 64);
+  stage_tile(bhi, blo, b, 0);
+  fence_proxy_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  tmem = *tslot;
+  if (threadIdx.x == 0) {
+    issue_product(tmem, ahi, alo, bhi, blo);
+    mma_commit(bar);
+  }
+  const bool ok = mbar_wait_bounded(bar, 0, 1ll << 24);
+  fence_after_sync();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  row = 32 * (w & 3) + lane;
+  col0 = 32 * (w >> 2);
+  if (ok) {
+    tmem_ld32(tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)col0, v);
+  } else if (lane == 0 && atomicCAS(&err->code, 0, (int)SFCDD_ERR_TIMEOUT) == 0) {
+    err->index = m;
+  }
+  return ok;
+}
+
+// Every thread is done with its tensor-memory reads: release the columns.
+__device__ __forceinline__ void tc_release(uint32_t tmem) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tmem);
+}
+
+// Panel L_ik = A_ik Linv_kk^T, two stored tiles of column k per CTA.
+// grid = (ceil(max panel rows / 2), nmat)
+__global__ void __launch_bounds__(FB) k_trsm_tc(TileSetDev ts, int mat0, int k,
+                                                float* __restrict__ tiles, ErrWord* err) {
+  extern __shared__ __align__(1024) unsigned char dsm_tc[];
+  const int m = mat0 + blockIdx.y;
+  const int nt = ts.nt[m];
+  if (k >= nt) return;
+  const int fb = ts.vbase[m] / TILE;
+  const int c0p = ts.colptr[fb + k];
+  const int cnt = ts.colptr[fb + k + 1] - c0p;
+  const int t0 = 2 * (int)blockIdx.x;
+  if (t0 >= cnt) return;
+  const bool two = t0 + 1 < cnt;
+  const long long tb = ts.tbase[m];
+  float* a0 = tiles + tile_at(ts, tb, fb, ts.colidx[c0p + t0], k);
+  float* a1 = two ? tiles + tile_at(ts, tb, fb, ts.colidx[c0p + t0 + 1], k) : a0;
+  const float* lkk = tiles + tile_at(ts, tb, fb, k, k);
+  float v[32];
+  int row, col0;
+  uint32_t tmem;
+  const bool ok = tc_product(dsm_tc, a0, a1, lkk, v, row, col0, tmem, err, m);
+  // every A tile is staged (the barrier inside tc_product) before any is overwritten
+  if (ok && (row < 64 || two)) {
+    float* out = (row < 64 ? a0 : a1) + (row & 63) * TILE + col0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      reinterpret_cast<float4*>(out)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2],
+                                                      v[4 * q + 3]);
+  }
+  tc_release(tmem);
+}
+
+// Trailing update A_ij -= L_ik L_jk^T for stored panel rows i >= j of column
+// k: CTA (jj, p) updates the targets (jj + 2p, jj) and (jj + 2p + 1, jj).  The
+// CTA whose first target is tile (k+1, k+1) then factors it (step k+1's
+// potrf); the launch's last CTA does so when column k does not reach row k+1.
+// grid = (max panel rows * pmax + 1, nmat), pmax = ceil(max panel rows / 2)
+__global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int k, int pmax,
+                                                float* __restrict__ tiles, ErrWord* err) {
+  extern __shared__ __align__(1024) unsigned char dsm_tc[];
+  const int m = mat0 + blockIdx.y;
+  const int nt = ts.nt[m];
+  if (k >= nt) return;
+  const int fb = ts.vbase[m] / TILE;
+  const int c0p = ts.colptr[fb + k];
+  const int cnt = ts.colptr[fb + k + 1] - c0p;
+  const long long tb = ts.tbase[m];
+  if ((int)blockIdx.x == (int)gridDim.x - 1) {
+    if (k + 1 < nt && ts.kmin[fb + k + 1] > k)
+      potrf_tile<float>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_tc, err, m);
+    return;
+  }
+  const int jj = (int)blockIdx.x / pmax, p = (int)blockIdx.x % pmax;
+  const int ii0 = jj + 2 * p;
+  if (jj >= cnt || ii0 >= cnt) return;
+  const bool two = ii0 + 1 < cnt;
+  const int j = ts.colidx[c0p + jj];
+  const int i0 = ts.colidx[c0p + ii0];
+  const float* l0 = tiles + tile_at(ts, tb, fb, i0, k);
+  const float* l1 = two ? tiles + tile_at(ts, tb, fb, ts.colidx[c0p + ii0 + 1], k) : l0;
+  const float* ljk = tiles + tile_at(ts, tb, fb, j, k);
+  float* d0 = tiles + tile_at(ts, tb, fb, i0, j);
+  float* d1 = two ? tiles + tile_at(ts, tb, fb, ts.colidx[c0p + ii0 + 1], j) : d0;
+  float v[32];
+  int row, col0;
+  uint32_t tmem;
+  const bool ok = tc_product(dsm_tc, l0, l1, ljk, v, row, col0, tmem, err, m);
+  if (ok && (row < 64 || two)) {
+    float* out = (row < 64 ? d0 : d1) + (row & 63) * TILE + col0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float4 c = reinterpret_cast<float4*>(out)[q];
+      c.x -= v[4 * q];
+      c.y -= v[4 * q + 1];
+      c.z -= v[4 * q + 2];
+      c.w -= v[4 * q + 3];
+      reinterpret_cast<float4*>(out)[q] = c;
+    }
+  }
+  tc_release(tmem);
+  if (ok && i0 == k + 1 && j == k + 1) {
+    __threadfence();
+    __syncthreads();  // the whole tile is written
+    potrf_tile<float>(d0, dsm_tc, err, m);
+  }
+}
+
+// The FP32 factorization with its panel and trailing updates on the tensor cores.
+static void factor_tiles_tc(const TileSetDev& ts, int mat0, int nmat, int max_nt,
+                            const int* col_max, float* tiles, ErrWord* err, cudaStream_t s,
+                            LaunchHook* hook) {
+  const int sm_potrf = (2 * TILE + 1) * (TILE + 1) * (int)sizeof(float);
+  const int sm_tc = (int)tc::SMEM_BYTES;
+  cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_potrf);
+  cudaFuncSetAttribute(k_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_tc);
+  cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_tc);
+  hook->before(SFCDD_K_POTRF);
+  k_potrf<float><<<nmat, FB, sm_potrf, s>>>(ts, mat0, 0, tiles, err);
+  hook->after(SFCDD_K_POTRF);
+  for (int k = 0; k < max_nt; ++k) {
+    const int rows = col_max[k];
+    if (rows > 0) {
+      const int pmax = (rows + 1) / 2;
+      hook->before(SFCDD_K_TRSM);
+      k_trsm_tc<<<dim3(pmax, nmat), FB, sm_tc, s>>>(ts, mat0, k, tiles, err);
+      hook->after(SFCDD_K_TRSM);
+      hook->before(SFCDD_K_SYRK);
+      k_syrk_tc<<<dim3(rows * pmax + 1, nmat), FB, sm_tc, s>>>(ts, mat0, k, pmax, tiles, err);
+      hook->after(SFCDD_K_SYRK);
+    } else if (k + 1 < max_nt) {
+      hook->before(SFCDD_K_POTRF);
+      k_potrf<float><<<nmat, FB, sm_potrf, s>>>(ts, mat0, k + 1, tiles, err);
+      hook->after(SFCDD_K_POTRF);
+    }
+  }
+}
+
 template <class T, int SPLIT>
 static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                            T* tiles, int* diag_cnt, ErrWord* err, cudaStream_t s, LaunchHook* hook) {
@@ -502,7 +677,7 @@ static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt,
 
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                   void* tiles, Store st, int* diag_cnt, ErrWord* err, cudaStream_t s,
-                  LaunchHook* hook, int split) {
+                  LaunchHook* hook, int split, bool tensor_cores) {
   if (st == Store::F64) {
     if (split == 4)
       factor_tiles_t<double, 4>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, diag_cnt, err, s,
@@ -510,6 +685,8 @@ void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const in
     else
       factor_tiles_t<double, 1>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, diag_cnt, err, s,
                                 hook);
+  } else if (tensor_cores) {
+    factor_tiles_tc(ts, mat0, nmat, max_nt, col_max, (float*)tiles, err, s, hook);
   } else {
     factor_tiles_t<float, 1>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, diag_cnt, err, s, hook);
   }

@@ -334,7 +334,7 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 // trailing update of step k factors diagonal tile k+1 once its last update is in.
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                   void* tiles, Store st, int* diag_cnt, ErrWord* err, cudaStream_t s,
-                  LaunchHook* hook, int split = 1);
+                  LaunchHook* hook, int split = 1, bool tensor_cores = false);
 // Substitution form of the factors of matrices [mat0, mat0+nmat) (after
 // factor_tiles, same precision): every stored off-diagonal tile L_IK becomes
 // Lh_IK = L_IK L_KK^{-1} in place, ut receives Lh_IK^T in the same slot and

@@ -23,7 +23,8 @@ class Solver:
 
     def __init__(self, levels, P, overlap, *, precision="fp64", variant="additive",
                  weighting="omega", q=0, coeffs=None, flexible=-1, stream=None,
-                 profile=False, local_order="lex", slabs_local=0, slabs_coarse=0):
+                 profile=False, local_order="lex", slabs_local=0, slabs_coarse=0,
+                 tensor_cores=-1):
         L = _lib.lib()
         self.levels = tuple(int(l) for l in levels)
         self.d = len(self.levels)
@@ -46,6 +47,7 @@ class Solver:
         opt.local_order = {"lex": 0, "curve": 1}[local_order]
         opt.slabs_local = int(slabs_local)
         opt.slabs_coarse = int(slabs_coarse)
+        opt.tensor_cores = int(tensor_cores)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -220,7 +222,7 @@ class BatchSolver:
 
     def __init__(self, levels_list, P, overlap, *, precision="fp64", weighting="omega", q=0,
                  coeffs=None, flexible=-1, stream=None, local_order="lex", slabs_local=0,
-                 slabs_coarse=0):
+                 slabs_coarse=0, tensor_cores=-1):
         L = _lib.lib()
         self.levels = [tuple(int(l) for l in lv) for lv in levels_list]
         self.nsub = len(self.levels)
@@ -240,6 +242,7 @@ class BatchSolver:
         opt.local_order = {"lex": 0, "curve": 1}[local_order]
         opt.slabs_local = int(slabs_local)
         opt.slabs_coarse = int(slabs_coarse)
+        opt.tensor_cores = int(tensor_cores)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

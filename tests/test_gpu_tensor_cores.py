@@ -1,0 +1,100 @@
+"""The FP32 / BF16 local factorization with its panel and trailing-update tile
+products on the tensor cores (tcgen05, TF32 operands with the hi/lo split, FP32
+accumulation) against the CUDA-core factorization and the oracle.
+
+Bars: an FP32 factor is accurate to about kappa(A_i) u_32 whatever unit forms
+its tile products (kappa(A_i) up to 1.2e4 on these grids, u_32 = 6e-8, so
+kappa u_32 = 7e-4): the FP32 preconditioner apply is within 1e-3 relative of the
+FP64 one for both factorizations, and the tensor-core one is within 3x the
+CUDA-core one (the split keeps 2^-22 per operand against the 2^-24 of an FP32
+rounding, over 64-term sums either way); the solves keep the FP64 outer iteration's 1e-10 true
+residual and the exact solution to 1e-8, with iteration counts within +-1 of
+the CUDA-core factors'.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import exact, grid, schwarz
+from paper_2110_11211_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2110_11211_gb300.build import build
+    build()
+
+
+GRIDS = [((6, 6), 8, 0.5), ((9, 5, 3), 64, 1.0), ((10, 5, 3), 128, 1.0), ((5, 4, 3, 3), 32, 0.5),
+         ((3, 2, 3, 2), 8, 0.5)]
+
+
+@pytest.mark.parametrize("levels,P,gamma", GRIDS)
+def test_fp32_apply_tensor_cores_vs_fp64(levels, P, gamma):
+    from paper_2110_11211_gb300.solver import Solver
+    g = torch.tensor(inputs.uniform(71, grid.num_unknowns(levels)), device="cuda")
+    with Solver(levels, P, gamma) as s:
+        ref = s.apply_precond(g)
+    err = {}
+    for tc in (1, 0):
+        with Solver(levels, P, gamma, precision="fp32", tensor_cores=tc) as s:
+            z = s.apply_precond(g)
+        err[tc] = float(torch.linalg.norm(z - ref) / torch.linalg.norm(ref))
+    print("apply error vs FP64, tensor cores / CUDA cores:", err[1], err[0])
+    assert err[0] <= 1e-3 and err[1] <= 1e-3, err
+    assert err[1] <= 3.0 * err[0] + 1e-6, err
+
+
+def test_fp32_apply_tensor_cores_vs_oracle():
+    from paper_2110_11211_gb300.solver import Solver
+    levels, P, gamma = (7, 5), 12, 0.5
+    S = schwarz.Schwarz(levels, P, gamma)
+    g = inputs.uniform(72, S.N)
+    with Solver(levels, P, gamma, precision="fp32", tensor_cores=1) as s:
+        z = s.apply_precond(torch.tensor(g, device="cuda")).cpu().numpy()
+    ref = S.apply(g)
+    assert np.linalg.norm(z - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("levels,P,gamma", GRIDS[:2] + GRIDS[3:])
+def test_solve_with_tensor_core_factors(levels, P, gamma, precision):
+    from paper_2110_11211_gb300.solver import Solver
+    f_np = inputs.uniform(73, grid.num_unknowns(levels))
+    f = torch.tensor(f_np, device="cuda")
+    its = {}
+    for tc in (1, 0):
+        with Solver(levels, P, gamma, precision=precision, tensor_cores=tc) as s:
+            u, st = s.solve(f, rtol=1e-10, maxit=1000)
+        assert st.true_rel_res <= 2e-10
+        its[tc] = st.iters
+        if tc == 1:
+            ue = exact.solve(levels, f_np)
+            assert np.linalg.norm(u.cpu().numpy() - ue) <= 1e-8 * np.linalg.norm(ue)
+    assert abs(its[1] - its[0]) <= 1, its
+
+
+def test_batch_tensor_core_factors():
+    from paper_2110_11211_gb300.solver import BatchSolver
+    levels = inputs.combi_levels(3, (10,))
+    f = torch.tensor(inputs.uniform(74, sum(inputs.grid_size(lv) for lv in levels)),
+                     device="cuda")
+    sol = {}
+    for tc in (1, 0):
+        with BatchSolver(levels, 16, 0.5, precision="fp32", tensor_cores=tc) as b:
+            sol[tc], tot, per = b.solve(f, rtol=1e-10)
+        assert tot.fail_index == 0
+    assert float(torch.linalg.norm(sol[1] - sol[0]) / torch.linalg.norm(sol[0])) <= 1e-8
+
+
+def test_fp64_tensor_cores_unsupported():
+    from paper_2110_11211_gb300._lib import SfcddError
+    from paper_2110_11211_gb300.solver import Solver
+    with pytest.raises(SfcddError):
+        Solver((6, 6), 8, 0.5, precision="fp64", tensor_cores=1)
+    with pytest.raises(SfcddError):
+        Solver((6, 6), 8, 0.5, precision="fp32", tensor_cores=2)
