@@ -75,11 +75,13 @@ typedef struct {
                            next.  sfcdd_autotune picks it by measurement. */
   int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 4.
                            FP32 / BF16 local factors require 2 or 4 (INVALID_ARG otherwise). */
-  int tensor_cores;     /* FP32 / BF16 local factors: the panel and trailing-update tile
-                           products of the factorization on the tensor cores (tcgen05, TF32
-                           operands with the hi/lo split, FP32 accumulation: FP32-accurate)
-                           when 1 or -1 (default), on CUDA cores when 0.  FP64 factors: the
-                           tile products stay on the FP64 units (1 is UNSUPPORTED). */
+  int tensor_cores;     /* the panel and trailing-update tile products of the local and coarse
+                           factorizations on the tensor cores (tcgen05) when 1 or -1 (default),
+                           on CUDA cores when 0.  FP32 / BF16 local factors: TF32 operands
+                           with the hi/lo split, FP32 accumulation (FP32-accurate).  FP64
+                           factors: exact 8-bit digit slices of each row (Ozaki, Ogita, Oishi
+                           and Rump's error-free splitting) multiplied as bf16 with exact FP32
+                           accumulation, combined in integers and rounded once to FP64. */
 } sfcdd_options;
 
 typedef struct {

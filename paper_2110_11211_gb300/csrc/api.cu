@@ -357,7 +357,7 @@ struct sfcdd_handle {
   long long ltile_elems = 0, ctile_elems = 0;
   int max_nt = 0, nt0 = 0, max_ltiles = 0, max_ctiles = 0;
   int nsub_local = 1, nsub_coarse = 4;
-  bool tensor_cores = false;  // FP32 factorization tile products on tcgen05
+  bool tensor_cores = false;  // factorization tile products on tcgen05 (FP32 split / FP64 sliced)
   int cb_coarse = 4;  // tiles per unit diagonal block of the coarse substitution form
   long long fwd_tiles_l = 0, bwd_tiles_l = 0, fwd_tiles_c = 0, bwd_tiles_c = 0;
   // substitution work lists (each with its own ticket counters: the items of a
@@ -724,8 +724,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
   if (!valid_slabs(h->precision, h->nsub_local, h->nsub_coarse)) return SFCDD_ERR_INVALID_ARG;
   if (o.tensor_cores < -1 || o.tensor_cores > 1) return SFCDD_ERR_INVALID_ARG;
-  if (h->precision == SFCDD_FP64 && o.tensor_cores == 1) return SFCDD_ERR_UNSUPPORTED;
-  h->tensor_cores = h->precision != SFCDD_FP64 && o.tensor_cores != 0;
+  h->tensor_cores = o.tensor_cores != 0;
   h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
   h->stream = (cudaStream_t)o.stream;
   h->profiling = o.profile != 0;
@@ -996,7 +995,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     });
     CoarseHook ch(pf2);
     factor_tiles(cts, 0, 1, h->nt0, h->col_max_coarse.data(), h->ctiles, Store::F64, diag_cnt,
-                 h->err, s2, &ch, 4);
+                 h->err, s2, &ch, 4, h->tensor_cores);
     pf2.run(SFCDD_K_COARSE_FACTOR, [&] {
       if (h->cb_coarse > 1)
         unitize_blocks(cts, h->nt0, h->cb_coarse, h->stored[P], h->ctiles, h->cut, xs, s2);

@@ -618,7 +618,6 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   sfcdd_options o;
   sfcdd_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision == SFCDD_FP64 && o.tensor_cores == 1) return SFCDD_ERR_UNSUPPORTED;
   if (o.variant != SFCDD_ADDITIVE || o.precision < 0 || o.precision > 2 || o.weighting < 0 ||
       o.weighting > 1 || o.tensor_cores < -1 || o.tensor_cores > 1)
     return o.variant != SFCDD_ADDITIVE ? SFCDD_ERR_UNSUPPORTED : SFCDD_ERR_INVALID_ARG;
@@ -866,7 +865,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
     void after(int) override {}
   } nohook;
   factor_tiles(b->ts, 0, b->nlocal, b->max_nt_local, b->sky.col_max_local.data(), work_tiles, cst,
-               diag_cnt, b->err, s, &nohook, 1, cst != Store::F64 && o.tensor_cores != 0);
+               diag_cnt, b->err, s, &nohook, 1, o.tensor_cores != 0);
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
   void* work_ut = nullptr;
   BTRY(balloc(b, (unsigned char**)&work_ut, b->sky.ltiles * TILE2 * esz));
@@ -893,7 +892,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
                                                                         b->ts, b->ctiles);
   }
   factor_tiles(b->ts, b->nlocal, nsub, b->max_nt_coarse, b->sky.col_max_coarse.data(), b->ctiles,
-               Store::F64, diag_cnt, b->err, s, &nohook);
+               Store::F64, diag_cnt, b->err, s, &nohook, 1, o.tensor_cores != 0);
   BTRY(balloc(b, &b->cut, b->sky.ctiles * TILE2));
   unitize_tiles(b->ts, b->nlocal, nsub, b->sky.max_ctiles, b->ctiles, b->cut, Store::F64, s);
   SFCDD_CUDA_OK(cudaGetLastError());

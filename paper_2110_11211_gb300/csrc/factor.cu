@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "oz_tile.cuh"
 #include "tc_tile.cuh"
 
 namespace sfcdd {
@@ -614,6 +615,185 @@ __global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int k, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 panel and trailing update on the bf16 tensor cores by exact slicing
+// (oz_tile.cuh): the same two-targets-per-CTA structure as the FP32 kernels,
+// seven digit slices per operand, seven FP32 accumulator groups in 512 tensor-
+// memory columns, one FP64 rounding per result.
+
+__device__ __forceinline__ bool oz_product(unsigned char* dsm, const double* a0, const double* a1,
+                                           const double* b, uint32_t& tmem, ErrWord* err, int m) {
+  int* ex = reinterpret_cast<int*>(dsm + oz::E_OFF);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + oz::BAR_OFF);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc::smem_addr(tslot)),
+                 "r"(oz::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init1(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const int t = threadIdx.x;
+  if (t < 128)
+    oz::stage_row(dsm + oz::A_OFF, oz::A_SLICE, ex, t < 64 ? a0 : a1, t & 63, t);
+  else if (t < 192)
+    oz::stage_row(dsm + oz::B_OFF, oz::B_SLICE, ex + 128, b, t - 128, t - 128);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  tmem = *tslot;
+  if (t == 0) {
+    oz::issue_products(tmem, tc::smem_addr(dsm + oz::A_OFF), tc::smem_addr(dsm + oz::B_OFF));
+    tc::mma_commit(bar);
+  }
+  const bool ok = tc::mbar_wait_bounded(bar, 0, 1ll << 24);
+  tc::fence_after_sync();
+  if (!ok && (t & 31) == 0 && atomicCAS(&err->code, 0, (int)SFCDD_ERR_TIMEOUT) == 0)
+    err->index = m;
+  return ok;
+}
+
+__device__ __forceinline__ void oz_release(uint32_t tmem) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(oz::TMEM_COLS)
+                 : "memory");
+}
+
+// This thread's row (of the 128) and its 32 columns of D = A B^T, written to
+// out0 (rows 0-63) or out1 (rows 64-127): overwritten (SUB = false) or
+// subtracted from (SUB = true).
+template <bool SUB>
+__device__ __forceinline__ void oz_emit(const unsigned char* dsm, uint32_t tmem, double* out0,
+                                        double* out1, bool two) {
+  const int* ex = reinterpret_cast<const int*>(dsm + oz::E_OFF);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * (w & 3) + lane;
+  const uint32_t tl = tmem + ((uint32_t)(32 * (w & 3)) << 16);
+  const bool mine = row < 64 || two;
+  double* out = (row < 64 ? out0 : out1) + (row & 63) * TILE;
+#pragma unroll 1
+  for (int q = 0; q < 2; ++q) {
+    const int c0 = 32 * (w >> 2) + 16 * q;
+    double v[16];
+    oz::read_combine16(tl, c0, ex[row], ex + 128, v);  // every lane: .sync.aligned loads
+    if (mine) {
+#pragma unroll
+      for (int j = 0; j < 16; j += 2) {
+        double2* o = reinterpret_cast<double2*>(out + c0 + j);
+        if (SUB) {
+          double2 c = *o;
+          c.x -= v[j];
+          c.y -= v[j + 1];
+          *o = c;
+        } else {
+          *o = make_double2(v[j], v[j + 1]);
+        }
+      }
+    }
+  }
+}
+
+// Panel L_ik = A_ik Linv_kk^T in FP64, two stored tiles of column k per CTA.
+// grid = (ceil(max panel rows / 2), nmat)
+__global__ void __launch_bounds__(FB) k_trsm_oz(TileSetDev ts, int mat0, int k,
+                                                double* __restrict__ tiles, ErrWord* err) {
+  extern __shared__ __align__(1024) unsigned char dsm_oz[];
+  const int m = mat0 + blockIdx.y;
+  const int nt = ts.nt[m];
+  if (k >= nt) return;
+  const int fb = ts.vbase[m] / TILE;
+  const int c0p = ts.colptr[fb + k];
+  const int cnt = ts.colptr[fb + k + 1] - c0p;
+  const int t0 = 2 * (int)blockIdx.x;
+  if (t0 >= cnt) return;
+  const bool two = t0 + 1 < cnt;
+  const long long tb = ts.tbase[m];
+  double* a0 = tiles + tile_at(ts, tb, fb, ts.colidx[c0p + t0], k);
+  double* a1 = two ? tiles + tile_at(ts, tb, fb, ts.colidx[c0p + t0 + 1], k) : a0;
+  const double* lkk = tiles + tile_at(ts, tb, fb, k, k);
+  uint32_t tmem;
+  // every A tile is staged (the barrier inside oz_product) before any is overwritten
+  if (oz_product(dsm_oz, a0, a1, lkk, tmem, err, m)) oz_emit<false>(dsm_oz, tmem, a0, a1, two);
+  oz_release(tmem);
+}
+
+// Trailing update A_ij -= L_ik L_jk^T in FP64; same target map as k_syrk_tc.
+// grid = (max panel rows * pmax + 1, nmat), pmax = ceil(max panel rows / 2)
+__global__ void __launch_bounds__(FB) k_syrk_oz(TileSetDev ts, int mat0, int k, int pmax,
+                                                double* __restrict__ tiles, ErrWord* err) {
+  extern __shared__ __align__(1024) unsigned char dsm_oz[];
+  const int m = mat0 + blockIdx.y;
+  const int nt = ts.nt[m];
+  if (k >= nt) return;
+  const int fb = ts.vbase[m] / TILE;
+  const int c0p = ts.colptr[fb + k];
+  const int cnt = ts.colptr[fb + k + 1] - c0p;
+  const long long tb = ts.tbase[m];
+  if ((int)blockIdx.x == (int)gridDim.x - 1) {
+    if (k + 1 < nt && ts.kmin[fb + k + 1] > k)
+      potrf_tile<double>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_oz, err, m);
+    return;
+  }
+  const int jj = (int)blockIdx.x / pmax, p = (int)blockIdx.x % pmax;
+  const int ii0 = jj + 2 * p;
+  if (jj >= cnt || ii0 >= cnt) return;
+  const bool two = ii0 + 1 < cnt;
+  const int j = ts.colidx[c0p + jj];
+  const int i0 = ts.colidx[c0p + ii0];
+  const double* l0 = tiles + tile_at(ts, tb, fb, i0, k);
+  const double* l1 = two ? tiles + tile_at(ts, tb, fb, ts.colidx[c0p + ii0 + 1], k) : l0;
+  const double* ljk = tiles + tile_at(ts, tb, fb, j, k);
+  double* d0 = tiles + tile_at(ts, tb, fb, i0, j);
+  double* d1 = two ? tiles + tile_at(ts, tb, fb, ts.colidx[c0p + ii0 + 1], j) : d0;
+  uint32_t tmem;
+  const bool ok = oz_product(dsm_oz, l0, l1, ljk, tmem, err, m);
+  if (ok) oz_emit<true>(dsm_oz, tmem, d0, d1, two);
+  oz_release(tmem);
+  if (ok && i0 == k + 1 && j == k + 1) {
+    __threadfence();
+    __syncthreads();  // the whole tile is written
+    potrf_tile<double>(d0, dsm_oz, err, m);
+  }
+}
+
+// The FP64 factorization with its panel and trailing updates on the tensor cores.
+static void factor_tiles_oz(const TileSetDev& ts, int mat0, int nmat, int max_nt,
+                            const int* col_max, double* tiles, ErrWord* err, cudaStream_t s,
+                            LaunchHook* hook) {
+  const int sm_potrf = (2 * TILE + 1) * (TILE + 1) * (int)sizeof(double);
+  const int sm_oz = (int)oz::SMEM_BYTES;
+  cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_potrf);
+  cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_oz);
+  cudaFuncSetAttribute(k_syrk_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_oz);
+  hook->before(SFCDD_K_POTRF);
+  k_potrf<double><<<nmat, FB, sm_potrf, s>>>(ts, mat0, 0, tiles, err);
+  hook->after(SFCDD_K_POTRF);
+  for (int k = 0; k < max_nt; ++k) {
+    const int rows = col_max[k];
+    if (rows > 0) {
+      const int pmax = (rows + 1) / 2;
+      hook->before(SFCDD_K_TRSM);
+      k_trsm_oz<<<dim3(pmax, nmat), FB, sm_oz, s>>>(ts, mat0, k, tiles, err);
+      hook->after(SFCDD_K_TRSM);
+      hook->before(SFCDD_K_SYRK);
+      k_syrk_oz<<<dim3(rows * pmax + 1, nmat), FB, sm_oz, s>>>(ts, mat0, k, pmax, tiles, err);
+      hook->after(SFCDD_K_SYRK);
+    } else if (k + 1 < max_nt) {
+      hook->before(SFCDD_K_POTRF);
+      k_potrf<double><<<nmat, FB, sm_potrf, s>>>(ts, mat0, k + 1, tiles, err);
+      hook->after(SFCDD_K_POTRF);
+    }
+  }
+}
+
 // The FP32 factorization with its panel and trailing updates on the tensor cores.
 static void factor_tiles_tc(const TileSetDev& ts, int mat0, int nmat, int max_nt,
                             const int* col_max, float* tiles, ErrWord* err, cudaStream_t s,
@@ -678,7 +858,9 @@ static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt,
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                   void* tiles, Store st, int* diag_cnt, ErrWord* err, cudaStream_t s,
                   LaunchHook* hook, int split, bool tensor_cores) {
-  if (st == Store::F64) {
+  if (st == Store::F64 && tensor_cores) {
+    factor_tiles_oz(ts, mat0, nmat, max_nt, col_max, (double*)tiles, err, s, hook);
+  } else if (st == Store::F64) {
     if (split == 4)
       factor_tiles_t<double, 4>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, diag_cnt, err, s,
                                 hook);

@@ -1,6 +1,8 @@
-"""The FP32 / BF16 local factorization with its panel and trailing-update tile
-products on the tensor cores (tcgen05, TF32 operands with the hi/lo split, FP32
-accumulation) against the CUDA-core factorization and the oracle.
+"""The factorizations with their panel and trailing-update tile products on the
+tensor cores against the CUDA-core factorizations and the oracle: FP32 / BF16
+local factors (tcgen05 kind::tf32, hi/lo split, FP32 accumulation) and FP64
+factors (exact 8-bit digit slices as bf16, exact FP32 accumulation, one FP64
+rounding).
 
 Bars: an FP32 factor is accurate to about kappa(A_i) u_32 whatever unit forms
 its tile products (kappa(A_i) up to 1.2e4 on these grids, u_32 = 6e-8, so
@@ -91,10 +93,50 @@ def test_batch_tensor_core_factors():
     assert float(torch.linalg.norm(sol[1] - sol[0]) / torch.linalg.norm(sol[0])) <= 1e-8
 
 
-def test_fp64_tensor_cores_unsupported():
+def test_invalid_tensor_core_option():
     from paper_2110_11211_gb300._lib import SfcddError
     from paper_2110_11211_gb300.solver import Solver
     with pytest.raises(SfcddError):
-        Solver((6, 6), 8, 0.5, precision="fp64", tensor_cores=1)
-    with pytest.raises(SfcddError):
         Solver((6, 6), 8, 0.5, precision="fp32", tensor_cores=2)
+
+
+# FP64 factors from sliced tensor-core products: the same FP64 bar as the
+# CUDA-core factorization (apply within 1e-12 of the oracle / of each other)
+@pytest.mark.parametrize("levels,P,gamma", GRIDS)
+def test_fp64_apply_sliced_products(levels, P, gamma):
+    from paper_2110_11211_gb300.solver import Solver
+    g = torch.tensor(inputs.uniform(75, grid.num_unknowns(levels)), device="cuda")
+    z = {}
+    for tc in (1, 0):
+        with Solver(levels, P, gamma, precision="fp64", tensor_cores=tc) as s:
+            z[tc] = s.apply_precond(g)
+    rel = float(torch.linalg.norm(z[1] - z[0]) / torch.linalg.norm(z[0]))
+    print("FP64 apply, sliced tensor-core vs CUDA-core factors:", rel)
+    assert rel <= 1e-12
+
+
+def test_fp64_apply_sliced_vs_oracle():
+    from paper_2110_11211_gb300.solver import Solver
+    for levels, P, gamma in [((7, 5), 12, 0.5), ((4, 4, 3), 10, 1.0)]:
+        S = schwarz.Schwarz(levels, P, gamma)
+        g = inputs.uniform(76, S.N)
+        with Solver(levels, P, gamma, precision="fp64", tensor_cores=1) as s:
+            z = s.apply_precond(torch.tensor(g, device="cuda")).cpu().numpy()
+        ref = S.apply(g)
+        assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("levels,P,gamma", GRIDS[:3])
+def test_fp64_solve_sliced_products(levels, P, gamma):
+    from paper_2110_11211_gb300.solver import Solver
+    f_np = inputs.uniform(77, grid.num_unknowns(levels))
+    f = torch.tensor(f_np, device="cuda")
+    out = {}
+    for tc in (1, 0):
+        with Solver(levels, P, gamma, precision="fp64", tensor_cores=tc) as s:
+            out[tc] = s.solve(f, rtol=1e-10, maxit=1000)
+    (u1, st1), (u0, st0) = out[1], out[0]
+    assert st1.true_rel_res <= 2e-10 and abs(st1.iters - st0.iters) <= 1
+    assert float(torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)) <= 1e-9
+    ue = exact.solve(levels, f_np)
+    assert np.linalg.norm(u1.cpu().numpy() - ue) <= 1e-8 * np.linalg.norm(ue)
