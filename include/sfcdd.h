@@ -261,6 +261,23 @@ int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out);
  * the fastest; drops the captured solve graph.  Errors as sfcdd_autotune. */
 int sfcdd_batch_autotune(sfcdd_batch* b, int reps, sfcdd_tuning* out);
 
+/* Failure-detection self-tests (no counterpart in the paper); neither faults,
+ * traps nor hangs the GPU, and the handle stays usable afterwards.
+ *   SFCDD_SELFTEST_WAIT_TIMEOUT: runs a forward substitution of the handle's
+ *     factors whose first work item is never scheduled; the items depending on
+ *     it poll result slots that nothing writes until their bounded spin (about
+ *     4M polls) runs out, record SFCDD_ERR_TIMEOUT with the waiting site, and the
+ *     remaining waiters stop on seeing the error word.  The result slots and work
+ *     counters are restored afterwards.
+ *   SFCDD_SELFTEST_BREAKDOWN: factors a host-built 64 x 64 tile with a negative
+ *     pivot through the diagonal-tile factorization the setup uses; it must
+ *     record SFCDD_ERR_NOT_SPD with the matrix index it was given (4242).
+ * Returns the status the device recorded (the expected error code on success)
+ * and *detail = its index or site; the error word is cleared again.
+ * Synchronises the stream.  Errors: INVALID_ARG (unknown kind), CUDA. */
+enum sfcdd_selftest_kind { SFCDD_SELFTEST_WAIT_TIMEOUT = 1, SFCDD_SELFTEST_BREAKDOWN = 2 };
+int sfcdd_selftest(sfcdd_handle* h, int kind, int* detail);
+
 /* Introspection for parity checks (all synchronise the stream). */
 int sfcdd_get_info(const sfcdd_handle* h, sfcdd_info* info);
 /* keys_dev: N uint64 Hilbert keys by lexicographic id (Sec. 3.2).

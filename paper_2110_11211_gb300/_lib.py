@@ -33,6 +33,7 @@ EXPORTS = [
     "sfcdd_batch_offsets", "sfcdd_batch_solve", "sfcdd_batch_info", "sfcdd_batch_destroy",
     "sfcdd_estimate_spectrum", "sfcdd_richardson", "sfcdd_solve_homogeneous",
     "sfcdd_batch_setup_each", "sfcdd_batch_combine", "sfcdd_autotune", "sfcdd_batch_autotune",
+    "sfcdd_selftest",
 ]
 
 
@@ -114,6 +115,7 @@ def lib() -> C.CDLL:
                                          C.c_int, C.c_double, C.POINTER(Options), C.POINTER(H)]
     L.sfcdd_batch_combine.argtypes = [H, C.POINTER(C.c_double), P, P, C.c_longlong, P]
     L.sfcdd_autotune.argtypes = [H, C.c_int, C.POINTER(Tuning)]
+    L.sfcdd_selftest.argtypes = [H, C.c_int, C.POINTER(C.c_int)]
     L.sfcdd_batch_autotune.argtypes = [H, C.c_int, C.POINTER(Tuning)]
     L.sfcdd_batch_offsets.argtypes = [H, C.POINTER(C.c_longlong)]
     L.sfcdd_batch_solve.argtypes = [H, P, P, C.c_double, C.c_int, C.POINTER(Stats),

@@ -1226,6 +1226,10 @@ int richardson_impl(sfcdd_handle* h, double* u_dev, double xi, double rtol, int 
       });
     }
     TRY(read_scalars(h));
+    if (h->sc_host->status) {  // non-finite input seen by the initialization
+      rc = h->sc_host->status;
+      break;
+    }
     const double rel = (homogeneous || h->sc_host->bb > 0) ? h->sc_host->true_rel : 0.0;
     if (!(rel == rel)) {
       rc = SFCDD_ERR_NAN;
@@ -1484,6 +1488,50 @@ int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, in
   SFCDD_CUDA_OK(cudaGetLastError());
   pf.collect();
   return SFCDD_OK;
+}
+
+int sfcdd_selftest(sfcdd_handle* h, int kind, int* detail) {
+  if (!h || (kind != SFCDD_SELFTEST_WAIT_TIMEOUT && kind != SFCDD_SELFTEST_BREAKDOWN))
+    return SFCDD_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->err, 0, sizeof(ErrWord), s));
+  if (kind == SFCDD_SELFTEST_BREAKDOWN) {
+    // identity with a negative pivot at row 17: the diagonal factorization must
+    // report NOT_SPD with the index it was given
+    std::vector<double> a(TILE2, 0.0);
+    for (int i = 0; i < TILE; ++i) a[(size_t)i * TILE + i] = i == 17 ? -1.0 : 2.0;
+    double* t = nullptr;
+    SFCDD_CUDA_OK(cudaMalloc(&t, TILE2 * sizeof(double)));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(t, a.data(), TILE2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_potrf_one(t, h->err, 4242, s);
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    cudaFree(t);
+  } else {
+    // a forward substitution whose first work item never runs: the items that
+    // depend on its rows wait on result slots nothing writes, give up after the
+    // bounded spin, record TIMEOUT, and every other waiter then stops waiting
+    const auto& wl = h->lists[LIST_MAIN];
+    if (wl.n < 2) return SFCDD_ERR_INVALID_ARG;
+    const unsigned long long one = 1;
+    SFCDD_CUDA_OK(cudaMemcpyAsync(wl.tf, &one, sizeof(one), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemsetAsync(h->tmp, 0, (size_t)h->N * sizeof(double), s));
+    SFCDD_CUDA_OK(cudaMemsetAsync(h->g0, 0, (size_t)h->nt0 * TILE * sizeof(double), s));
+    TrsvArgs af = trsv_args(h, true, h->tmp, nullptr, LIST_MAIN);
+    launch_trsv_fwd(af, h->st, s, wl.n - 1);
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    // restore the substitution state: pending result slots, tickets at zero
+    launch_fill_pending(h->ybuf, h->vtotal, s);
+    launch_fill_pending(h->dbuf, h->vtotal, s);
+    SFCDD_CUDA_OK(cudaMemsetAsync(wl.tf, 0, sizeof(unsigned long long), s));
+    SFCDD_CUDA_OK(cudaMemsetAsync(wl.tb, 0, sizeof(unsigned long long), s));
+  }
+  ErrWord e{};
+  SFCDD_CUDA_OK(cudaMemcpyAsync(&e, h->err, sizeof(ErrWord), cudaMemcpyDeviceToHost, s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(h->err, 0, sizeof(ErrWord), s));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+  if (detail) *detail = e.index;
+  return e.code;
 }
 
 int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out) {

@@ -294,6 +294,17 @@ __device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err,
   }
 }
 
+__global__ void __launch_bounds__(FB) k_potrf_one(double* tile, ErrWord* err, int m) {
+  extern __shared__ __align__(16) unsigned char dsm_one[];
+  potrf_tile<double>(tile, dsm_one, err, m);
+}
+
+void launch_potrf_one(double* tile, ErrWord* err, int m, cudaStream_t s) {
+  const int smem = (2 * TILE + 1) * (TILE + 1) * (int)sizeof(double);
+  cudaFuncSetAttribute(k_potrf_one, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_potrf_one<<<1, FB, smem, s>>>(tile, err, m);
+}
+
 template <class T>
 __global__ void __launch_bounds__(FB) k_potrf(TileSetDev ts, int mat0, int k, T* __restrict__ tiles,
                                               ErrWord* err) {

@@ -408,7 +408,11 @@ struct TrsvArgs {
   ErrWord* err;
   const PcgScalars* sc;        // per problem (md.sub); null: no early exit
 };
-void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s);
+// grid > 0 launches that many CTAs instead of one per work item (self-test only)
+void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s, int grid = 0);
+// Factorization and inversion of one 64 x 64 FP64 tile in place (self-test of the
+// breakdown report: a non-positive pivot sets NOT_SPD with index m).
+void launch_potrf_one(double* tile, ErrWord* err, int m, cudaStream_t s);
 void launch_trsv_bwd(const TrsvArgs& a, Store st, cudaStream_t s);
 
 }  // namespace sfcdd

@@ -400,17 +400,17 @@ void launch_fill_pending(double* p, long long n, cudaStream_t s) {
 }
 
 template <class T, class A, bool FWD>
-static void launch_k(const TrsvArgs& a, cudaStream_t s) {
+static void launch_k(const TrsvArgs& a, cudaStream_t s, int grid = 0) {
   constexpr int bytes = Plan<(int)sizeof(T)>::BYTES;
   cudaFuncSetAttribute(k_trsv<T, A, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  k_trsv<T, A, FWD><<<a.nwork, NTHR, bytes, s>>>(a);
+  k_trsv<T, A, FWD><<<grid > 0 ? grid : a.nwork, NTHR, bytes, s>>>(a);
 }
 
-void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s) {
+void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s, int grid) {
   switch (st) {
-    case Store::F64: launch_k<double, double, true>(a, s); break;
-    case Store::F32: launch_k<float, float, true>(a, s); break;
-    default: launch_k<__nv_bfloat16, float, true>(a, s); break;
+    case Store::F64: launch_k<double, double, true>(a, s, grid); break;
+    case Store::F32: launch_k<float, float, true>(a, s, grid); break;
+    default: launch_k<__nv_bfloat16, float, true>(a, s, grid); break;
   }
 }
 

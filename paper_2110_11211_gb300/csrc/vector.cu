@@ -217,6 +217,10 @@ __global__ void __launch_bounds__(VB) k_energy(int n, const double* __restrict__
       sc->rtol = rtol;
       sc->flexible = flexible;
       sc->done = esq > 0.0 ? 0 : 1;
+      if (!(t[0] == t[0]) || isinf(t[0])) {  // non-finite initial iterate
+        sc->status = SFCDD_ERR_NAN;
+        sc->done = 1;
+      }
     } else {
       sc->true_rel = sc->esq0 > 0.0 ? sqrt(esq / sc->esq0) : 0.0;
     }
@@ -385,6 +389,10 @@ __global__ void __launch_bounds__(VB) k_init_pcg(int n, const double* __restrict
     sc->rtol = rtol;
     sc->flexible = flexible;
     sc->done = t[0] > 0.0 ? 0 : 1;
+    if (!(t[0] == t[0]) || isinf(t[0])) {  // non-finite right-hand side
+      sc->status = SFCDD_ERR_NAN;
+      sc->done = 1;
+    }
   });
 }
 

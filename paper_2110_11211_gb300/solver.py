@@ -152,6 +152,14 @@ class Solver:
         return {"slabs_local": t.slabs_local, "slabs_coarse": t.slabs_coarse,
                 "apply_ms": t.apply_ms, "candidates": t.candidates}
 
+    def selftest(self, kind):
+        """Failure-detection self-test ('wait_timeout' or 'breakdown'): returns
+        (status the device recorded, index or site)."""
+        k = {"wait_timeout": 1, "breakdown": 2}[kind]
+        d = C.c_int(-1)
+        rc = self._L.sfcdd_selftest(self._h, k, C.byref(d))
+        return rc, d.value
+
     def apply_operator(self, x: torch.Tensor, curve_order=False):
         y = torch.empty_like(x)
         check("sfcdd_apply_operator",
