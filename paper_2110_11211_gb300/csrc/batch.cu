@@ -255,8 +255,9 @@ __global__ void k_b_invpad(const SubDesc* __restrict__ sub, const unsigned* __re
 
 __global__ void k_b_env_local(const SubDesc* __restrict__ sub, const int* __restrict__ msub,
                               const unsigned* __restrict__ code, const int* __restrict__ invpad,
-                              TileSetDev ts, int* tfirst) {
-  const int m = blockIdx.y;
+                              TileSetDev ts, int nlocal, int* tfirst) {
+  const int m = grid_mat();
+  if (m >= nlocal) return;
   const SubDesc& sd = sub[msub[m]];
   const int i = m - sd.mat0;
   const int n = ts.n[m];
@@ -294,9 +295,11 @@ __global__ void __launch_bounds__(256) k_b_assemble_local(const SubDesc* __restr
                                                           const int* __restrict__ msub,
                                                           const unsigned* __restrict__ code,
                                                           const int* __restrict__ invpad,
-                                                          TileSetDev ts, T* __restrict__ tiles) {
+                                                          TileSetDev ts, int nlocal,
+                                                          T* __restrict__ tiles) {
   __shared__ double sm[TILE2];
-  const int m = blockIdx.y;
+  const int m = grid_mat();
+  if (m >= nlocal) return;
   const SubDesc& sd = sub[msub[m]];
   const int nt = ts.nt[m];
   const int fb = ts.vbase[m] / TILE;
@@ -613,6 +616,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
                      double overlap, const sfcdd_options* opt) {
   if (!levels || !Ps || nsub < 1 || d < 1 || d > MAXD || !(overlap > 0))
     return SFCDD_ERR_INVALID_ARG;
+  if (nsub > 65535) return SFCDD_ERR_UNSUPPORTED;  // per-subgrid launches index grid.y
   for (int si = 0; si < nsub; ++si)
     if (Ps[si] < 2) return SFCDD_ERR_INVALID_ARG;
   sfcdd_options o;
@@ -818,8 +822,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
     b->ts.linv = linv;
   }
   launch_envelope_init(b->ts, b->nmat, max_nt_all, tfirst, s);
-  k_b_env_local<<<dim3((max_nl + 255) / 256, b->nlocal), 256, 0, s>>>(
-      b->dsub, b->d_msub, b->code, b->invpad, b->ts, tfirst);
+  k_b_env_local<<<mat_grid((max_nl + 255) / 256, b->nlocal), 256, 0, s>>>(
+      b->dsub, b->d_msub, b->code, b->invpad, b->ts, b->nlocal, tfirst);
   k_b_env_coarse<<<gsub, 256, 0, s>>>(b->dsub, b->code, b->invpad, b->ts, tfirst);
   std::vector<int> tf(nrows);
   SFCDD_CUDA_OK(cudaMemcpyAsync(tf.data(), tfirst, nrows * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -852,12 +856,12 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   BTRY(balloc(b, (unsigned char**)&work_tiles, b->sky.ltiles * TILE2 * esz));
   switch (cst) {
     case Store::F64:
-      k_b_assemble_local<double><<<dim3(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
-          b->dsub, b->d_msub, b->code, b->invpad, b->ts, (double*)work_tiles);
+      k_b_assemble_local<double><<<mat_grid(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
+          b->dsub, b->d_msub, b->code, b->invpad, b->ts, b->nlocal, (double*)work_tiles);
       break;
     default:
-      k_b_assemble_local<float><<<dim3(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
-          b->dsub, b->d_msub, b->code, b->invpad, b->ts, (float*)work_tiles);
+      k_b_assemble_local<float><<<mat_grid(b->sky.max_ltiles, b->nlocal), 256, 0, s>>>(
+          b->dsub, b->d_msub, b->code, b->invpad, b->ts, b->nlocal, (float*)work_tiles);
       break;
   }
   struct NoHook : LaunchHook {

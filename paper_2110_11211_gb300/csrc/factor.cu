@@ -34,8 +34,9 @@ __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
 
 // ---------------------------------------------------------------------------
 // Envelopes.
-__global__ void k_envelope_init(TileSetDev ts, int* tfirst) {
-  const int m = blockIdx.y;
+__global__ void k_envelope_init(TileSetDev ts, int nmat, int* tfirst) {
+  const int m = grid_mat();
+  if (m >= nmat) return;
   const int nt = ts.nt[m];
   const int fb = ts.vbase[m] / TILE;
   for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nt; I += gridDim.x * blockDim.x)
@@ -43,14 +44,15 @@ __global__ void k_envelope_init(TileSetDev ts, int* tfirst) {
 }
 
 void launch_envelope_init(const TileSetDev& ts, int nmat, int max_nt, int* tfirst, cudaStream_t s) {
-  dim3 grid((max_nt + 127) / 128, nmat);
-  k_envelope_init<<<grid, 128, 0, s>>>(ts, tfirst);
+  k_envelope_init<<<mat_grid((max_nt + 127) / 128, nmat), 128, 0, s>>>(ts, nmat, tfirst);
 }
 
 // Row r of A_i: smallest local column among its neighbours inside Omega_i.
 __global__ void k_envelope_local(GridDev g, PartDev pd, const unsigned* __restrict__ code,
-                                 const int* __restrict__ invpad, TileSetDev ts, int* tfirst) {
-  const int m = blockIdx.y;
+                                 const int* __restrict__ invpad, TileSetDev ts, int nmat,
+                                 int* tfirst) {
+  const int m = grid_mat();
+  if (m >= nmat) return;
   const int n = ts.n[m];
   const int fb = ts.vbase[m] / TILE;
   const int start = pd.start[m];
@@ -65,8 +67,8 @@ __global__ void k_envelope_local(GridDev g, PartDev pd, const unsigned* __restri
 void launch_envelope_local(const GridDev& g, const PartDev& pd, const unsigned* code,
                            const int* invpad, const TileSetDev& ts, int nmat, int max_n, int* tfirst,
                            cudaStream_t s) {
-  dim3 grid((max_n + 255) / 256, nmat);
-  k_envelope_local<<<grid, 256, 0, s>>>(g, pd, code, invpad, ts, tfirst);
+  k_envelope_local<<<mat_grid((max_n + 255) / 256, nmat), 256, 0, s>>>(g, pd, code, invpad, ts,
+                                                                      nmat, tfirst);
 }
 
 // Coarse row a: smallest coarse row adjacent to row a (factor numbering).
@@ -91,9 +93,11 @@ template <class T>
 __global__ void __launch_bounds__(FB) k_assemble_local(GridDev g, PartDev pd,
                                                        const unsigned* __restrict__ code,
                                                        const int* __restrict__ invpad,
-                                                       TileSetDev ts, int mat0, T* __restrict__ tiles) {
+                                                       TileSetDev ts, int mat0, int nmat,
+                                                       T* __restrict__ tiles) {
   __shared__ double sm[TILE2];
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   const int fb = ts.vbase[m] / TILE;
   const int idx = blockIdx.x;
@@ -113,16 +117,16 @@ __global__ void __launch_bounds__(FB) k_assemble_local(GridDev g, PartDev pd,
 void launch_assemble_local(const GridDev& g, const PartDev& pd, const unsigned* code,
                            const int* invpad, const TileSetDev& ts, int mat0, int nmat, int max_tiles,
                            void* tiles, Store st, cudaStream_t s) {
-  dim3 grid(max_tiles, nmat);
+  const dim3 grid = mat_grid(max_tiles, nmat);
   switch (st) {
     case Store::F64:
-      k_assemble_local<double><<<grid, FB, 0, s>>>(g, pd, code, invpad, ts, mat0, (double*)tiles);
+      k_assemble_local<double><<<grid, FB, 0, s>>>(g, pd, code, invpad, ts, mat0, nmat, (double*)tiles);
       break;
     case Store::F32:
-      k_assemble_local<float><<<grid, FB, 0, s>>>(g, pd, code, invpad, ts, mat0, (float*)tiles);
+      k_assemble_local<float><<<grid, FB, 0, s>>>(g, pd, code, invpad, ts, mat0, nmat, (float*)tiles);
       break;
     default:
-      k_assemble_local<__nv_bfloat16><<<grid, FB, 0, s>>>(g, pd, code, invpad, ts, mat0,
+      k_assemble_local<__nv_bfloat16><<<grid, FB, 0, s>>>(g, pd, code, invpad, ts, mat0, nmat,
                                                           (__nv_bfloat16*)tiles);
       break;
   }
@@ -389,11 +393,13 @@ __device__ __forceinline__ void mma_rows(T (&acc)[RA][4], T (*Xt)[TILE + 4], T (
 // diagonal.  grid = (max panel rows * SPLIT, nmat); a CTA reads and writes
 // only the rows of its slab of A_ik.
 template <class T, int SPLIT>
-__global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int k, T* __restrict__ tiles) {
+__global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int nmat, int k,
+                                             T* __restrict__ tiles) {
   extern __shared__ __align__(16) unsigned char dsm_trsm[];
   T (*At)[TILE + 4] = reinterpret_cast<T (*)[TILE + 4]>(dsm_trsm);
   T (*Bt)[TILE + 4] = At + TILE;
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
@@ -428,13 +434,15 @@ __global__ void __launch_bounds__(FB) k_trsm(TileSetDev ts, int mat0, int k, T* 
 // factors it, or, when column k does not reach row k+1, the launch's last CTA
 // does.  grid = (max pairs * SPLIT + 1, nmat)
 template <class T, int SPLIT>
-__global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int k, T* __restrict__ tiles,
+__global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int nmat, int k,
+                                             T* __restrict__ tiles,
                                              int* __restrict__ diag_cnt, ErrWord* err) {
   extern __shared__ __align__(16) unsigned char dsm_syrk[];
   T (*Xt)[TILE + 4] = reinterpret_cast<T (*)[TILE + 4]>(dsm_syrk);
   T (*Yt)[TILE + 4] = Xt + TILE;
   __shared__ int s_last;
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
@@ -540,10 +548,11 @@ __device__ __forceinline__ void tc_release(uint32_t tmem) {
 
 // Panel L_ik = A_ik Linv_kk^T, two stored tiles of column k per CTA.
 // grid = (ceil(max panel rows / 2), nmat)
-__global__ void __launch_bounds__(FB) k_trsm_tc(TileSetDev ts, int mat0, int k,
+__global__ void __launch_bounds__(FB) k_trsm_tc(TileSetDev ts, int mat0, int nmat, int k,
                                                 float* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_tc[];
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
@@ -576,10 +585,11 @@ __global__ void __launch_bounds__(FB) k_trsm_tc(TileSetDev ts, int mat0, int k,
 // CTA whose first target is tile (k+1, k+1) then factors it (step k+1's
 // potrf); the launch's last CTA does so when column k does not reach row k+1.
 // grid = (max panel rows * pmax + 1, nmat), pmax = ceil(max panel rows / 2)
-__global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int k, int pmax,
+__global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int nmat, int k, int pmax,
                                                 float* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_tc[];
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
@@ -714,10 +724,11 @@ __device__ __forceinline__ void oz_emit(const unsigned char* dsm, uint32_t tmem,
 
 // Panel L_ik = A_ik Linv_kk^T in FP64, two stored tiles of column k per CTA.
 // grid = (ceil(max panel rows / 2), nmat)
-__global__ void __launch_bounds__(FB) k_trsm_oz(TileSetDev ts, int mat0, int k,
+__global__ void __launch_bounds__(FB) k_trsm_oz(TileSetDev ts, int mat0, int nmat, int k,
                                                 double* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_oz[];
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
@@ -738,10 +749,11 @@ __global__ void __launch_bounds__(FB) k_trsm_oz(TileSetDev ts, int mat0, int k,
 
 // Trailing update A_ij -= L_ik L_jk^T in FP64; same target map as k_syrk_tc.
 // grid = (max panel rows * pmax + 1, nmat), pmax = ceil(max panel rows / 2)
-__global__ void __launch_bounds__(FB) k_syrk_oz(TileSetDev ts, int mat0, int k, int pmax,
+__global__ void __launch_bounds__(FB) k_syrk_oz(TileSetDev ts, int mat0, int nmat, int k, int pmax,
                                                 double* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_oz[];
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   if (k >= nt) return;
   const int fb = ts.vbase[m] / TILE;
@@ -792,10 +804,11 @@ static void factor_tiles_oz(const TileSetDev& ts, int mat0, int nmat, int max_nt
     if (rows > 0) {
       const int pmax = (rows + 1) / 2;
       hook->before(SFCDD_K_TRSM);
-      k_trsm_oz<<<dim3(pmax, nmat), FB, sm_oz, s>>>(ts, mat0, k, tiles, err);
+      k_trsm_oz<<<mat_grid(pmax, nmat), FB, sm_oz, s>>>(ts, mat0, nmat, k, tiles, err);
       hook->after(SFCDD_K_TRSM);
       hook->before(SFCDD_K_SYRK);
-      k_syrk_oz<<<dim3(rows * pmax + 1, nmat), FB, sm_oz, s>>>(ts, mat0, k, pmax, tiles, err);
+      k_syrk_oz<<<mat_grid(rows * pmax + 1, nmat), FB, sm_oz, s>>>(ts, mat0, nmat, k, pmax, tiles,
+                                                                    err);
       hook->after(SFCDD_K_SYRK);
     } else if (k + 1 < max_nt) {
       hook->before(SFCDD_K_POTRF);
@@ -822,10 +835,11 @@ static void factor_tiles_tc(const TileSetDev& ts, int mat0, int nmat, int max_nt
     if (rows > 0) {
       const int pmax = (rows + 1) / 2;
       hook->before(SFCDD_K_TRSM);
-      k_trsm_tc<<<dim3(pmax, nmat), FB, sm_tc, s>>>(ts, mat0, k, tiles, err);
+      k_trsm_tc<<<mat_grid(pmax, nmat), FB, sm_tc, s>>>(ts, mat0, nmat, k, tiles, err);
       hook->after(SFCDD_K_TRSM);
       hook->before(SFCDD_K_SYRK);
-      k_syrk_tc<<<dim3(rows * pmax + 1, nmat), FB, sm_tc, s>>>(ts, mat0, k, pmax, tiles, err);
+      k_syrk_tc<<<mat_grid(rows * pmax + 1, nmat), FB, sm_tc, s>>>(ts, mat0, nmat, k, pmax, tiles,
+                                                                    err);
       hook->after(SFCDD_K_SYRK);
     } else if (k + 1 < max_nt) {
       hook->before(SFCDD_K_POTRF);
@@ -852,11 +866,11 @@ static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt,
     const int rows = col_max[k];
     if (rows > 0) {
       hook->before(SFCDD_K_TRSM);
-      k_trsm<T, SPLIT><<<dim3(rows * SPLIT, nmat), FB, sm_gemm, s>>>(ts, mat0, k, tiles);
+      k_trsm<T, SPLIT><<<mat_grid(rows * SPLIT, nmat), FB, sm_gemm, s>>>(ts, mat0, nmat, k, tiles);
       hook->after(SFCDD_K_TRSM);
       hook->before(SFCDD_K_SYRK);
-      k_syrk<T, SPLIT><<<dim3(rows * (rows + 1) / 2 * SPLIT + 1, nmat), FB, sm_gemm, s>>>(
-          ts, mat0, k, tiles, diag_cnt, err);
+      k_syrk<T, SPLIT><<<mat_grid(rows * (rows + 1) / 2 * SPLIT + 1, nmat), FB, sm_gemm, s>>>(
+          ts, mat0, nmat, k, tiles, diag_cnt, err);
       hook->after(SFCDD_K_SYRK);
     } else if (k + 1 < max_nt) {
       hook->before(SFCDD_K_POTRF);
@@ -916,12 +930,14 @@ __device__ __forceinline__ void mma_4x4_from(T (&acc)[4][4], T (*Xt)[TILE + 4],
 // k >= column, so each warp starts its k loop at its first column (threads of
 // a warp share a column block: c0 = 4 (tid / 16)).  grid = (max stored, nmat)
 template <class T>
-__global__ void __launch_bounds__(FB) k_unitize(TileSetDev ts, int mat0, T* __restrict__ tiles,
+__global__ void __launch_bounds__(FB) k_unitize(TileSetDev ts, int mat0, int nmat,
+                                                T* __restrict__ tiles,
                                                 T* __restrict__ ut) {
   extern __shared__ __align__(16) unsigned char dsm_unit[];
   T (*Xt)[TILE + 4] = reinterpret_cast<T (*)[TILE + 4]>(dsm_unit);
   T (*Yt)[TILE + 4] = Xt + TILE;
-  const int m = mat0 + blockIdx.y;
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
   const int nt = ts.nt[m];
   const int fb = ts.vbase[m] / TILE;
   if ((int)blockIdx.x >= stored_tiles(ts, fb, nt)) return;
@@ -972,7 +988,7 @@ static void unitize_t(const TileSetDev& ts, int mat0, int nmat, int max_stored, 
   if (nmat <= 0 || max_stored <= 0) return;
   const int sm = 2 * TILE * (TILE + 4) * (int)sizeof(T);
   cudaFuncSetAttribute(k_unitize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  k_unitize<T><<<dim3(max_stored, nmat), FB, sm, s>>>(ts, mat0, tiles, ut);
+  k_unitize<T><<<mat_grid(max_stored, nmat), FB, sm, s>>>(ts, mat0, nmat, tiles, ut);
 }
 
 // ---------------------------------------------------------------------------
@@ -1171,8 +1187,9 @@ __global__ void k_unpack_dense(TileSetDev ts, int m, const double* __restrict__ 
 __global__ void k_lorder_keys(TileSetDev ts, const int* __restrict__ mstart, const int* __restrict__ mN,
                               const int* __restrict__ mcbase, const int* __restrict__ lbase,
                               const unsigned* __restrict__ code, unsigned long long* __restrict__ keys,
-                              unsigned* __restrict__ vals) {
-  const int m = blockIdx.y;
+                              unsigned* __restrict__ vals, int nmat) {
+  const int m = grid_mat();
+  if (m >= nmat) return;
   const int n = ts.n[m], start = mstart[m], N = mN[m];
   const unsigned* cs = code + mcbase[m];
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
@@ -1207,8 +1224,8 @@ void local_order_lex(const TileSetDev& ts, int nmat, int max_n, const int* mstar
                      cudaStream_t s) {
   int mbits = 1;
   while ((1 << mbits) < nmat) ++mbits;
-  k_lorder_keys<<<dim3((max_n + 255) / 256, nmat), 256, 0, s>>>(ts, mstart, mN, mcbase, lbase, code,
-                                                                 keys, vals);
+  k_lorder_keys<<<mat_grid((max_n + 255) / 256, nmat), 256, 0, s>>>(ts, mstart, mN, mcbase, lbase,
+                                                                     code, keys, vals, nmat);
   radix_sort_pairs(keys, vals, (int)total, 32 + mbits, temp, s, nullptr);
   k_lorder_scatter<<<152 * 8, 256, 0, s>>>(ts, mstart, mN, lbase, total, keys, vals, lperm, linv);
 }

@@ -34,6 +34,17 @@ constexpr int TILE = 64;          // tile edge of the packed factors
 constexpr int TILE2 = TILE * TILE;
 constexpr int MAXD = 8;
 
+// Launches over many matrices: the matrix index runs over grid.y x grid.z
+// (grid.y is limited to 65535); the excess CTAs of the last z slice return.
+inline dim3 mat_grid(unsigned x, int nmat) {
+  const unsigned n = nmat > 0 ? (unsigned)nmat : 1u;
+  const unsigned y = n < 65535u ? n : 65535u;
+  return dim3(x, y, (n + y - 1) / y);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ int grid_mat() { return (int)(blockIdx.y + gridDim.y * blockIdx.z); }
+#endif
+
 // Grid description passed by value to kernels.
 struct GridDev {
   int d;

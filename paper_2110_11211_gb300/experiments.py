@@ -16,7 +16,13 @@ rescaling is a multiple of the identity and changes neither count.  The D_i
 weighting of eq. (Di) coincides with the omega_i weighting for gamma = 1/2
 (Lemma on the weightings), so the studies at gamma = 1/2 cover it.
 
-Usage: python -m paper_2110_11211_gb300.experiments [E1 ... E7 | all]
+E8 (Sec. 4.3, on one GPU): the combination technique on the Poisson problem
+with u = ||x||_2 prod sin(pi x_i), d = 2..6, growing L, P_hat = 2^{L-8} (at least 1):
+the error of the combined solution at seeded points against u, with the number
+of subgrids, unknowns and PCG iterations (FP32 local factors, FP64 outer
+iteration to relative residual 1e-8, as the study stops).
+
+Usage: python -m paper_2110_11211_gb300.experiments [E1 ... E8 | all]
            [--pmax P] [--json FILE]
 """
 from __future__ import annotations
@@ -127,7 +133,34 @@ def configs(name: str, pmax: int):
     return out
 
 
+CT_LEVELS = {2: range(6, 17), 3: range(6, 14), 4: range(6, 12), 5: range(7, 11), 6: range(7, 9)}
+
+
+def run_ct(d, L, npts=1 << 14):
+    """One combination-technique solve of the Sec. 4.3 problem (E8)."""
+    from .combination import Combination
+    P_hat = max(1, 2 ** (L - 8))
+    pts = torch.tensor(inputs.unit_points(44, npts, d), device="cuda")
+    ue = inputs.ct_exact(pts.cpu().numpy())
+    t0 = time.perf_counter()
+    with Combination(d, L, P_hat, precision="fp32") as ct:
+        ct.solve(rtol=1e-8, maxit=20000)
+        out = ct.evaluate(pts).cpu().numpy()
+        tot, per = ct.stats
+        its = [p.iters for p in per]
+        row = dict(study="E8", d=d, L=L, P_hat=P_hat, subgrids=len(ct.levels), N=ct.batch.N,
+                   iters_max=max(its), iters_mean=float(sum(its)) / len(its),
+                   failed=tot.fail_index)
+    row["max_error"] = float(abs(out - ue).max())
+    row["wall_s"] = time.perf_counter() - t0
+    return row
+
+
 def fmt(row) -> str:
+    if row.get("study") == "E8":
+        return (f"d={row['d']} L={row['L']} P_hat={row['P_hat']} subgrids={row['subgrids']} "
+                f"N={row['N']} iters max/mean={row['iters_max']}/{row['iters_mean']:.1f} "
+                f"max error={row['max_error']:.3e} ({row['wall_s']:.2f} s)")
     if "skipped" in row:
         return (f"d={row['d']} levels={row['levels']} P={row['P']} gamma={row['gamma']} "
                 f"q={row['q']} {row['variant']}/{row['weighting']}: skipped ({row['skipped']})")
@@ -149,10 +182,23 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if not torch.cuda.is_available():
         raise SystemExit("the iteration-count studies run on the GPU path: no CUDA device")
-    names = ["E1", "E2", "E3", "E4", "E5", "E6", "E7"] if "all" in a.studies else a.studies
+    names = ["E1", "E2", "E3", "E4", "E5", "E6", "E7", "E8"] if "all" in a.studies else a.studies
     rows = []
     t0 = time.perf_counter()
     for name in names:
+        if name == "E8":
+            for d, Ls in CT_LEVELS.items():
+                for L in Ls:
+                    if a.budget > 0 and time.perf_counter() - t0 > a.budget:
+                        print("time budget reached", flush=True)
+                        return rows
+                    row = run_ct(d, L)
+                    rows.append(row)
+                    print(name, fmt(row), flush=True)
+                    if a.json:
+                        with open(a.json, "w") as fh:
+                            json.dump(rows, fh, indent=1)
+            continue
         for cfg in configs(name, a.pmax):
             if a.budget > 0 and time.perf_counter() - t0 > a.budget:
                 print("time budget reached", flush=True)

@@ -76,3 +76,22 @@ def test_combination_set_d4_l12_13_P64():
         fs = f[offs[k]:offs[k + 1]]
         ue = exact.solve(lv, fs)
         assert np.linalg.norm(u[offs[k]:offs[k + 1]] - ue) <= 1e-8 * np.linalg.norm(ue), lv
+
+
+def test_more_local_matrices_than_one_grid_dimension():
+    """1100 subgrids x 64 subdomains = 70,400 local matrices, beyond the 65,535
+    CTAs of one grid dimension: every subgrid still matches its single solve."""
+    from paper_2110_11211_gb300.solver import BatchSolver, Solver
+    lv = (5, 6)
+    n = inputs.grid_size(lv)
+    nsub = 1100
+    f = torch.tensor(inputs.uniform(97, n * nsub), device="cuda")
+    with BatchSolver([lv] * nsub, 64, 0.5, precision="fp32") as b:
+        u, tot, per = b.solve(f, rtol=1e-10)
+        assert tot.fail_index == 0
+        offs = b.offsets
+    for s in (0, 517, nsub - 1):
+        with Solver(lv, 64, 0.5, precision="fp32") as one:
+            us, st = one.solve(f[offs[s]:offs[s + 1]].contiguous(), rtol=1e-10)
+        rel = float(torch.linalg.norm(u[offs[s]:offs[s + 1]] - us) / torch.linalg.norm(us))
+        assert rel <= 1e-8, (s, rel)
