@@ -55,7 +55,9 @@ constexpr long long SPIN_FAST = 1 << 12;   // polls before the poller starts to 
 // Shared-memory plan of a launch whose local factors have element size ES.
 template <int ES>
 struct Plan {
-  static constexpr int RING = 2 * TILE2 * ES;  // slab ring: two local tiles
+  // slab ring: 32 KB (one FP64 or two FP32 tiles, four BF16), so that four or more
+  // CTAs fit an SM; a 64-row FP64 slab then has a single stage
+  static constexpr int RING = (ES == 8 ? 1 : 2) * TILE2 * ES;
   static constexpr int ZBUF = MAXST * TILE * 8;
   static constexpr int BYTES = RING + ZBUF + 3 * MAXST * 8;
 };
