@@ -659,10 +659,7 @@ __device__ __forceinline__ bool oz_product(unsigned char* dsm, const double* a0,
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   const int t = threadIdx.x;
-  if (t < 128)
-    oz::stage_row(dsm + oz::A_OFF, oz::A_SLICE, ex, t < 64 ? a0 : a1, t & 63, t);
-  else if (t < 192)
-    oz::stage_row(dsm + oz::B_OFF, oz::B_SLICE, ex + 128, b, t - 128, t - 128);
+  oz::stage_all(dsm, a0, a1, b);
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
@@ -701,13 +698,13 @@ __device__ __forceinline__ void oz_emit(const unsigned char* dsm, uint32_t tmem,
   const bool mine = row < 64 || two;
   double* out = (row < 64 ? out0 : out1) + (row & 63) * TILE;
 #pragma unroll 1
-  for (int q = 0; q < 2; ++q) {
-    const int c0 = 32 * (w >> 2) + 16 * q;
-    double v[16];
-    oz::read_combine16(tl, c0, ex[row], ex + 128, v);  // every lane: .sync.aligned loads
+  for (int q = 0; q < 4; ++q) {
+    const int c0 = 32 * (w >> 2) + 8 * q;
+    double v[8];
+    oz::read_combine8(tl, c0, ex[row], ex + 128, v);  // every lane: .sync.aligned loads
     if (mine) {
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) {
+      for (int j = 0; j < 8; j += 2) {
         double2* o = reinterpret_cast<double2*>(out + c0 + j);
         if (SUB) {
           double2 c = *o;

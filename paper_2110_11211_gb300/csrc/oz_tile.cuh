@@ -16,7 +16,7 @@
 // |G_s| <= 64 (2^16 + 5 2^14) < 2^24 and every accumulation is exact.  The
 // dropped terms (digit pairs with i + j > 6 and the truncation t) are below
 // 2^-55 |A| |B^T| relative, the size of one FP64 rounding of the sum.  The
-// seven G_s are combined exactly in 128-bit integers and rounded once to FP64.
+// seven G_s are combined in one 64-bit integer and rounded once to FP64.
 //
 // Shared-memory operand layout (bf16, K-major, no swizzle): core matrices of
 // 8 rows x 16 bytes (8 x 8 bf16); row r, column c of a slice at byte
@@ -42,7 +42,8 @@ constexpr uint32_t B_SLICE = 64 * 64 * 2;   // 8 KB
 constexpr uint32_t A_OFF = 0;
 constexpr uint32_t B_OFF = S * A_SLICE;                 // 112 KB
 constexpr uint32_t E_OFF = B_OFF + S * B_SLICE;         // 168 KB: row exponents (192 ints)
-constexpr uint32_t BAR_OFF = E_OFF + 192 * 4;
+constexpr uint32_t MAX_OFF = E_OFF + 192 * 4;           // row maxima as bit patterns (192 u64)
+constexpr uint32_t BAR_OFF = MAX_OFF + 192 * 8;
 constexpr uint32_t SMEM_BYTES = BAR_OFF + 16;
 constexpr uint32_t TMEM_COLS = 512;  // 7 groups x 64 columns, rounded up
 constexpr int ZERO_ROW = -100000;    // exponent of an all-zero row
@@ -66,67 +67,101 @@ __device__ __forceinline__ int row_exponent(double maxabs) {
   return E == 0 ? ZERO_ROW : E - 1022;
 }
 
-// The seven signed digits of x relative to 2^e (digit 0 most significant).
-__device__ __forceinline__ void digits(double x, int e, int (&n)[S]) {
+// bf16 bit pattern of an integer n with |n| <= 256 (exact): 0x4B400000 + n is
+// the FP32 pattern of 1.5 2^23 + n, so subtracting 1.5 2^23 in FP32 gives n
+// exactly; n has at most 9 significant bits, so its FP32 pattern ends in 16 zeros.
+__device__ __forceinline__ uint32_t bf16_of_int(int n) {
+  const float f = __int_as_float(0x4B400000 + n) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// The seven balanced digits of x relative to 2^e, as bf16 bit patterns: with
+// X = floor(|x| 2^{56 - e}) and Y = X + 0x808080808080 (128 added to the six low
+// bytes), digit 0 is Y >> 48 in [0, 256] and digit i > 0 is byte 6 - i of Y minus
+// 128, in [-128, 127]; sum_i digit_i 2^{8(6-i)} = X exactly; the sign of x is
+// applied to every digit.
+__device__ __forceinline__ void digits_bf16(double x, int e, uint32_t (&d)[S]) {
   const long long b = __double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7FF);
   unsigned long long X = 0;
   if (E != 0 && e != ZERO_ROW) {
     const unsigned long long M = (unsigned long long)(b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = 4 + (E - 1023) - e;  // X = floor(|x| 2^{56 - e}) = M 2^sh, sh <= 3
+    const int sh = 4 + (E - 1023) - e;
     X = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
   }
-  int carry = 0;
-#pragma unroll
-  for (int i = S - 1; i >= 0; --i) {
-    int v = (int)((X >> (8 * (S - 1 - i))) & 0xFFull) + carry;
-    carry = 0;
-    if (i > 0 && v >= 128) {
-      v -= 256;
-      carry = 1;
-    }
-    n[i] = v;
-  }
-  if (b < 0) {
-#pragma unroll
-    for (int i = 0; i < S; ++i) n[i] = -n[i];
-  }
+  const unsigned long long Y = X + 0x808080808080ull;
+  const uint32_t yh = (uint32_t)(Y >> 32), yl = (uint32_t)Y;
+  const int sg = b < 0 ? -1 : 1;
+  d[0] = bf16_of_int(sg * (int)(yh >> 16));
+  d[1] = bf16_of_int(sg * ((int)((yh >> 8) & 0xFFu) - 128));
+  d[2] = bf16_of_int(sg * ((int)(yh & 0xFFu) - 128));
+  d[3] = bf16_of_int(sg * ((int)(yl >> 24) - 128));
+  d[4] = bf16_of_int(sg * ((int)((yl >> 16) & 0xFFu) - 128));
+  d[5] = bf16_of_int(sg * ((int)((yl >> 8) & 0xFFu) - 128));
+  d[6] = bf16_of_int(sg * ((int)(yl & 0xFFu) - 128));
 }
 
-// Rows [row0, row0 + 64) of the operand from a row-major 64 x 64 FP64 tile
-// `src`: thread t < 64 of the calling group handles row t.  Writes the seven
-// digit slices (bf16) and the row exponent.
-__device__ __forceinline__ void stage_row(unsigned char* slices, uint32_t slice_bytes, int* ex,
-                                          const double* __restrict__ src, int r, int row) {
-  const double2* p = reinterpret_cast<const double2*>(src + r * 64);
-  double m = 0.0;
-#pragma unroll 8
-  for (int q = 0; q < 32; ++q) {
-    const double2 v = p[q];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+// Stage the 192 operand rows (A: rows 0-63 of a0, rows 64-127 of a1; B: rows of b)
+// as digit slices, every thread of the CTA taking six (row, 8-column chunk)
+// tasks: a warp covers 8 rows x 4 chunks, so its loads are 256-byte row pieces
+// and its 16-byte slice stores fill whole 128-byte lines.  All loads are issued
+// first and kept in registers; the row maxima come from shared atomics on the
+// bit patterns of |x| (which order like the values), then the digits are written.
+__device__ __forceinline__ void stage_all(unsigned char* dsm, const double* __restrict__ a0,
+                                          const double* __restrict__ a1,
+                                          const double* __restrict__ b) {
+  int* ex = reinterpret_cast<int*>(dsm + E_OFF);
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(dsm + MAX_OFF);
+  for (int i = threadIdx.x; i < 192; i += blockDim.x) mx[i] = 0ull;
+  __syncthreads();
+  constexpr int NT = 192 * 8;
+  constexpr int PER = NT / 256;  // tasks per thread (the kernels run 256 threads)
+  ulonglong2 v[PER][4];
+  int rows[PER], cs[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int T = threadIdx.x + 256 * j;
+    const int g = T >> 6, w = T & 63;
+    const int row = 8 * g + (w & 7), c = 4 * (w >> 5) + ((w & 31) >> 3);
+    rows[j] = row;
+    cs[j] = c;
+    const double* src = row < 64 ? a0 + row * 64 : row < 128 ? a1 + (row - 64) * 64 : b + (row - 128) * 64;
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(src + 8 * c);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) v[j][h] = p[h];
   }
-  const int e = row_exponent(m);
-  ex[row] = e;
-  for (int c8 = 0; c8 < 8; ++c8) {
-    uint32_t w[S][4];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    unsigned long long m = 0ull;
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      m = max(m, max(v[j][h].x & 0x7FFFFFFFFFFFFFFFull, v[j][h].y & 0x7FFFFFFFFFFFFFFFull));
+    atomicMax(&mx[rows[j]], m);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 192; i += blockDim.x)
+    ex[i] = row_exponent(__longlong_as_double((long long)mx[i]));
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int row = rows[j];
+    const int e = ex[row];
+    uint32_t wd[S][4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      const double2 v = p[4 * c8 + h];
-      int n0[S], n1[S];
-      digits(v.x, e, n0);
-      digits(v.y, e, n1);
+      uint32_t d0[S], d1[S];
+      digits_bf16(__longlong_as_double((long long)v[j][h].x), e, d0);
+      digits_bf16(__longlong_as_double((long long)v[j][h].y), e, d1);
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
-        const uint32_t lo = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)n0[i]));
-        const uint32_t hi = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)n1[i]));
-        w[i][h] = lo | (hi << 16);
-      }
+      for (int i = 0; i < S; ++i) wd[i][h] = d0[i] | (d1[i] << 16);
     }
-    const uint32_t off = core_offset(row, c8);
+    unsigned char* base = row < 128 ? dsm + A_OFF : dsm + B_OFF;
+    const uint32_t sl = row < 128 ? A_SLICE : B_SLICE;
+    const uint32_t off = core_offset(row < 128 ? row : row - 128, cs[j]);
 #pragma unroll
     for (int i = 0; i < S; ++i)
-      *reinterpret_cast<uint4*>(slices + (size_t)i * slice_bytes + off) =
-          make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+      *reinterpret_cast<uint4*>(base + (size_t)i * sl + off) =
+          make_uint4(wd[i][0], wd[i][1], wd[i][2], wd[i][3]);
   }
 }
 
@@ -156,70 +191,54 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t abase, ui
   }
 }
 
-// 2^{er + ec} (hi 2^{-40} + lo 2^{-64}) rounded once to FP64, with
-// hi = sum_{s<=3} G_s 2^{8(3-s)}, lo = sum_{s>=4} G_s 2^{8(6-s)}.
-__device__ __forceinline__ double combine(long long hi, long long lo, int er, int ec) {
-  const __int128 V = (__int128)hi * ((__int128)1 << 24) + (__int128)lo;  // value = V 2^{er + ec - 64}
-  if (V == 0) return 0.0;
-  const bool neg = V < 0;
-  const unsigned __int128 U = neg ? (unsigned __int128)(-V) : (unsigned __int128)V;
-  const unsigned long long uh = (unsigned long long)(U >> 64), ul = (unsigned long long)U;
-  const int msb = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);
-  unsigned long long m;
-  int top = msb;
-  if (msb <= 52) {
-    m = ul << (52 - msb);
-  } else {
-    const int sh = msb - 52;
-    m = (unsigned long long)(U >> sh);
-    const unsigned __int128 rem = U & (((unsigned __int128)1 << sh) - 1);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    if (rem > half || (rem == half && (m & 1ull))) ++m;
-    if (m == (1ull << 53)) {
-      m >>= 1;
-      ++top;
-    }
-  }
-  const int E = top + er + ec - 64 + 1023;
-  if (E <= 0 || E >= 2047) {  // outside the normal range: scale in FP64
-    const double mant = (double)(long long)m * (neg ? -1.0 : 1.0);
-    return ldexp(mant, top - 52 + er + ec - 64);
-  }
-  const unsigned long long bits =
-      (neg ? (1ull << 63) : 0ull) | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
+// An exact integer |g| < 2^24 held as FP32 bits (a group sum), read with integer
+// instructions.
+__device__ __forceinline__ long long int_of_f32(uint32_t b) {
+  if ((b & 0x7FFFFFFFu) == 0u) return 0;
+  const int e = (int)((b >> 23) & 0xFFu) - 127;  // 0..23
+  const long long mag = (long long)(((b & 0x7FFFFFu) | 0x800000u) >> (23 - e));
+  return (b >> 31) ? -mag : mag;
 }
 
-// 16 accumulator columns [c0, c0 + 16) of this thread's lane for every group,
-// combined into FP64 values v[16] (column scales ec[c0 + j]).
-__device__ __forceinline__ void read_combine16(uint32_t tmem_lane, int c0, int er,
-                                               const int* ecols, double (&v)[16]) {
-  long long hi[16], lo[16];
+// 8 accumulator columns [c0, c0 + 8) of this thread's lane for every group (the
+// seven loads issued back to back, one wait), combined into FP64 values v[8]:
+//   D = 2^{er + ec} sum_s 2^{-8(s+2)} G_s = W 2^{er + ec - 54},
+//   W = sum_s G_s 2^{8(6-s) - 10}   (|W| < 2^61),
+// where the two lowest groups are shifted right (dropping bits below 2^-74 of
+// 2^{er + ec}, far below an FP64 rounding of D); W is converted once, to nearest,
+// and scaled by adding to the exponent field.
+__device__ __forceinline__ void read_combine8(uint32_t tmem_lane, int c0, int er,
+                                              const int* ecols, double (&v)[8]) {
+  uint32_t r[NG][8];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
-#pragma unroll
-  for (int s = 0; s < NG; ++s) {
-    uint32_t r[16];
+  for (int s = 0; s < NG; ++s)
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[s][0]), "=r"(r[s][1]), "=r"(r[s][2]), "=r"(r[s][3]), "=r"(r[s][4]),
+          "=r"(r[s][5]), "=r"(r[s][6]), "=r"(r[s][7])
         : "r"(tmem_lane + 64u * s + (uint32_t)c0)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const long long g = (long long)__float2int_rn(__uint_as_float(r[j]));
-      if (s <= 3) hi[j] += g * (1ll << (8 * (3 - s)));
-      else lo[j] += g * (1ll << (8 * (6 - s)));
+  for (int j = 0; j < 8; ++j) {
+    long long W = 0;
+#pragma unroll
+    for (int s = 0; s < NG; ++s) {
+      const long long g = int_of_f32(r[s][j]);
+      const int sh = 8 * (6 - s) - 10;  // 38, 30, 22, 14, 6, -2, -10
+      W += sh >= 0 ? g * (1ll << sh) : (g >> (-sh));
     }
+    const int ec = ecols[c0 + j];
+    double d = 0.0;
+    if (W != 0 && er != ZERO_ROW && ec != ZERO_ROW) {
+      d = __ll2double_rn(W);
+      const int E = (int)((__double_as_longlong(d) >> 52) & 0x7FF) + er + ec - 54;
+      d = (E > 0 && E < 2047)
+              ? __longlong_as_double(__double_as_longlong(d) + ((long long)(er + ec - 54) << 52))
+              : ldexp(d, er + ec - 54);
+    }
+    v[j] = d;
   }
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    v[j] = (er == ZERO_ROW || ecols[c0 + j] == ZERO_ROW) ? 0.0
-                                                         : combine(hi[j], lo[j], er, ecols[c0 + j]);
 }
 
 }  // namespace oz
