@@ -692,6 +692,7 @@ int build_partition(sfcdd_handle* h) {
 
 int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
                const sfcdd_options* opt) {
+  NvtxRange nvtx("sfcdd setup");
   if (!levels || d < 1 || d > MAXD || P < 2 || !(overlap > 0)) return SFCDD_ERR_INVALID_ARG;
   h->d = d;
   long long N = 1;
@@ -1020,6 +1021,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
                  h->err, s, &pf, compute_st == Store::F64 ? 4 : 1, h->tensor_cores);
   }
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
+  NvtxRange nvtx_unit("sfcdd setup: substitution form");
   void* work_ut = nullptr;
   TRY(dalloc(h, (unsigned char**)&work_ut, h->ltile_elems * esz));
   if (h->variant != SFCDD_COARSE_ONLY)
@@ -1113,6 +1115,7 @@ int read_scalars(sfcdd_handle* h) {
 // norm ||x_k||_A <= rtol ||x_0||_A (Sec. 4) instead of the residual.
 int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats,
              bool homogeneous = false) {
+  NvtxRange nvtx("sfcdd pcg");
   if (!(rtol >= 0) || maxit < 0) return SFCDD_ERR_INVALID_ARG;
   cudaStream_t s = h->stream;
   TRY(build_graph(h));
@@ -1200,6 +1203,7 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats,
 // is the true relative residual.  Every step reads the stopping quantity back.
 int richardson_impl(sfcdd_handle* h, double* u_dev, double xi, double rtol, int maxit,
                     sfcdd_stats* stats, bool homogeneous) {
+  NvtxRange nvtx("sfcdd richardson");
   cudaStream_t s = h->stream;
   cudaEvent_t e0, e1;
   SFCDD_CUDA_OK(cudaEventCreate(&e0));
@@ -1535,6 +1539,7 @@ int sfcdd_selftest(sfcdd_handle* h, int kind, int* detail) {
 }
 
 int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out) {
+  NvtxRange nvtx("sfcdd autotune");
   if (!h || reps < 1) return SFCDD_ERR_INVALID_ARG;
   cudaStream_t s = h->stream;
   const bool prof = h->profiling;

@@ -614,6 +614,7 @@ int build_graph(sfcdd_batch* b, int maxit) {
 
 int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const int* Ps,
                      double overlap, const sfcdd_options* opt) {
+  NvtxRange nvtx("sfcdd batch setup");
   if (!levels || !Ps || nsub < 1 || d < 1 || d > MAXD || !(overlap > 0))
     return SFCDD_ERR_INVALID_ARG;
   if (nsub > 65535) return SFCDD_ERR_UNSUPPORTED;  // per-subgrid launches index grid.y
@@ -1021,6 +1022,7 @@ int sfcdd_batch_offsets(const sfcdd_batch* b, long long* offsets_host) {
 
 int sfcdd_batch_solve(sfcdd_batch* b, const double* f_dev, double* u_dev, double rtol, int maxit,
                       sfcdd_stats* per_sub, sfcdd_stats* total) {
+  NvtxRange nvtx("sfcdd batch solve");
   if (!b || !f_dev || !u_dev || !(rtol >= 0) || maxit < 1) return SFCDD_ERR_INVALID_ARG;
   cudaStream_t s = b->stream;
   BTRY(build_graph(b, maxit));

@@ -27,12 +27,22 @@
 #include <vector>
 
 #include "../../include/sfcdd.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace sfcdd {
 
 constexpr int TILE = 64;          // tile edge of the packed factors
 constexpr int TILE2 = TILE * TILE;
 constexpr int MAXD = 8;
+
+// Named range for profilers (NVTX; free when no tool is attached): setup
+// stages, solves and tuning show up as spans on the host timeline.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Launches over many matrices: the matrix index runs over grid.y x grid.z
 // (grid.y is limited to 65535); the excess CTAs of the last z slice return.
