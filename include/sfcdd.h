@@ -197,7 +197,8 @@ int sfcdd_solve_homogeneous(sfcdd_handle* h, const double* x0_dev, double* u_dev
  * the offsets returned by sfcdd_batch_offsets (nsub + 1 entries, last = total).
  * Supported options: precision, weighting, q (<= 0: per-subgrid rule), flexible,
  * coeffs (shared), stream, slabs_local / slabs_coarse (defaults 1 and 1 for FP64,
- * 1 and 4 otherwise); variant must be SFCDD_ADDITIVE (else UNSUPPORTED).
+ * 1 and 4 otherwise), tensor_cores, variant SFCDD_ADDITIVE or SFCDD_BALANCED
+ * (eq. balSW: two coarse solves and one local solve per apply; else UNSUPPORTED).
  * At most 65535 subgrids (UNSUPPORTED beyond); any number of local matrices.
  * Errors as sfcdd_setup_ex / sfcdd_solve; per_sub (nsub entries) and total may
  * be NULL; total->iters is the largest iteration count, total->fail_index the

@@ -47,7 +47,7 @@ class Combination:
     default is the Poisson test problem of Sec. 4.3."""
 
     def __init__(self, d: int, L: int, P_hat: int, gamma: float = 0.5, *, precision="fp64",
-                 q=0, rhs=inputs.ct_rhs):
+                 q=0, rhs=inputs.ct_rhs, variant="additive"):
         from .solver import BatchSolver
         self.d, self.L, self.P_hat = int(d), int(L), int(P_hat)
         if self.L < self.d + 1:
@@ -57,7 +57,8 @@ class Combination:
         self.coef = [coefficient(self.d, i) for _, i in self.subgrids]
         self.P = [subdomain_count(self.d, i, self.P_hat, inputs.grid_size(lv))
                   for lv, i in self.subgrids]
-        self.batch = BatchSolver(self.levels, self.P, gamma, precision=precision, q=q)
+        self.batch = BatchSolver(self.levels, self.P, gamma, precision=precision, q=q,
+                                 variant=variant)
         f = np.concatenate([rhs(lv) for lv in self.levels])
         self.f = torch.tensor(f, device="cuda")
         self.u = None

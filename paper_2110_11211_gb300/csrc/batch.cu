@@ -65,6 +65,15 @@ struct sfcdd_batch {
   TrsvWork *work_f = nullptr, *work_b = nullptr;
   int nwork = 0;
   unsigned long long *ticket_f = nullptr, *ticket_b = nullptr;
+  // balanced operator (eq. balSW): local-only and coarse-only work lists, each
+  // with its own ticket counters, and the vectors w = F r, r - A w, t
+  int variant = SFCDD_ADDITIVE;
+  struct List {
+    TrsvWork *f = nullptr, *b = nullptr;
+    int n = 0;
+    unsigned long long *tf = nullptr, *tb = nullptr;
+  } local_list, coarse_list;
+  double *bw = nullptr, *bgg = nullptr, *bt = nullptr;
   double *ybuf = nullptr, *dbuf = nullptr, *zcbuf = nullptr;
   double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr,
          *g0 = nullptr;
@@ -148,6 +157,27 @@ int batch_configure(sfcdd_batch* b, int nsub_local, int nsub_coarse) {
   if (!b->ticket_b) BTRY(balloc(b, &b->ticket_b, 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_f, 0, sizeof(unsigned long long), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(b->ticket_b, 0, sizeof(unsigned long long), s));
+  if (b->variant == SFCDD_BALANCED) {
+    for (int li = 0; li < 2; ++li) {
+      std::vector<char> inc(b->nmat, li == 0 ? 1 : 0);
+      for (int si = 0; si < b->nsub; ++si) inc[b->hsub[si].cmat] = li == 0 ? 0 : 1;
+      std::vector<TrsvWork> lf, lb;
+      build_worklists(b->h_nt, inc, nsl, lf, lb);
+      auto& L = li == 0 ? b->local_list : b->coarse_list;
+      bfree(b, L.f);
+      bfree(b, L.b);
+      L.n = (int)lf.size();
+      BTRY(balloc(b, &L.f, L.n));
+      BTRY(balloc(b, &L.b, L.n));
+      SFCDD_CUDA_OK(cudaMemcpyAsync(L.f, lf.data(), lf.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+      SFCDD_CUDA_OK(cudaMemcpyAsync(L.b, lb.data(), lb.size() * sizeof(TrsvWork), cudaMemcpyHostToDevice, s));
+      if (!L.tf) BTRY(balloc(b, &L.tf, 1));
+      if (!L.tb) BTRY(balloc(b, &L.tb, 1));
+      SFCDD_CUDA_OK(cudaMemsetAsync(L.tf, 0, sizeof(unsigned long long), s));
+      SFCDD_CUDA_OK(cudaMemsetAsync(L.tb, 0, sizeof(unsigned long long), s));
+      SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    }
+  }
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
   return SFCDD_OK;
 }
@@ -381,6 +411,10 @@ __global__ void __launch_bounds__(BT) k_b_init(const SubDesc* __restrict__ sub,
     c.rtol = rtol;
     c.flexible = flexible;
     c.done = bb > 0.0 ? 0 : 1;
+    if (!(bb == bb) || isinf(bb)) {  // non-finite right-hand side
+      c.status = SFCDD_ERR_NAN;
+      c.done = 1;
+    }
   }
 }
 
@@ -498,6 +532,95 @@ __global__ void __launch_bounds__(BT) k_b_prolong(const SubDesc* __restrict__ su
   for (int i = threadIdx.x; i < sd.g.N; i += BT) p[sd.base + i] = z[sd.base + i] + beta * p[sd.base + i];
 }
 
+
+// Balanced operator (eq. balSW), z = t - F A t + w with w = F r and
+// t = C_(1) (r - A w), in three per-subgrid kernels between substitution pairs
+// over the coarse-only and the local-only work lists.  Each CTA owns its whole
+// subgrid, so a vector it writes is complete for its stencil after a barrier.
+// 1: w = R_0^T d_0 (from the coarse solve of R_0 r), gg = r - A w.
+template <int D>
+__global__ void __launch_bounds__(BT) k_b_bal_w(const SubDesc* __restrict__ sub,
+                                                const unsigned* __restrict__ code,
+                                                const int* __restrict__ invpad, TileSetDev ts,
+                                                const double* __restrict__ dvec,
+                                                const double* __restrict__ r, double* __restrict__ w,
+                                                double* __restrict__ gg, const PcgScalars* sc) {
+  if (sc[blockIdx.x].done) return;
+  const SubDesc& sd = sub[blockIdx.x];
+  const int cbase = ts.vbase[sd.cmat];
+  auto lvbase = [&](int i) { return __ldg(&ts.vbase[sd.mat0 + i]); };
+  for (int i = threadIdx.x; i < sd.g.N; i += BT)
+    w[sd.base + i] = prolong_point(sd.pd, 2, dvec, cbase, lvbase, ts.linv, i);
+  __syncthreads();
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    double wi;
+    const double aw = stencil_point<D>(sd.g, code + sd.base, invpad + sd.ibase, w + sd.base, i, wi);
+    gg[sd.base + i] = r[sd.base + i] - aw;
+  }
+}
+
+// 2: t = sum_i omega_i R_i^T d_i (local solves of gg), g0 = R_0 A t (A t in q).
+template <int D>
+__global__ void __launch_bounds__(BT) k_b_bal_t(const SubDesc* __restrict__ sub,
+                                                const unsigned* __restrict__ code,
+                                                const int* __restrict__ invpad, TileSetDev ts,
+                                                const double* __restrict__ dvec,
+                                                double* __restrict__ t, double* __restrict__ q,
+                                                double* __restrict__ g0, const PcgScalars* sc) {
+  if (sc[blockIdx.x].done) return;
+  const SubDesc& sd = sub[blockIdx.x];
+  const int cbase = ts.vbase[sd.cmat];
+  auto lvbase = [&](int i) { return __ldg(&ts.vbase[sd.mat0 + i]); };
+  for (int i = threadIdx.x; i < sd.g.N; i += BT)
+    t[sd.base + i] = prolong_point(sd.pd, 1, dvec, cbase, lvbase, ts.linv, i);
+  __syncthreads();
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    double ti;
+    q[sd.base + i] = stencil_point<D>(sd.g, code + sd.base, invpad + sd.ibase, t + sd.base, i, ti);
+  }
+  __syncthreads();
+  restrict_sub(sd, q, g0);
+}
+
+// 3: v = R_0^T d_0 (coarse solve of R_0 A t), z = t - v + w, r^T z -> beta,
+// p = z + beta p.
+__global__ void __launch_bounds__(BT) k_b_bal_z(const SubDesc* __restrict__ sub, TileSetDev ts,
+                                                const double* __restrict__ dvec,
+                                                const double* __restrict__ t,
+                                                const double* __restrict__ w,
+                                                const double* __restrict__ r,
+                                                double* __restrict__ z, double* __restrict__ p,
+                                                PcgScalars* sc) {
+  __shared__ double sh[BT / 32];
+  PcgScalars& c = sc[blockIdx.x];
+  if (c.done) return;
+  const SubDesc& sd = sub[blockIdx.x];
+  const int cbase = ts.vbase[sd.cmat];
+  auto lvbase = [&](int i) { return __ldg(&ts.vbase[sd.mat0 + i]); };
+  double a1 = 0.0, a2 = 0.0;
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) {
+    const double v = prolong_point(sd.pd, 2, dvec, cbase, lvbase, ts.linv, i);
+    const double zi = t[sd.base + i] - v + w[sd.base + i];
+    const double ri = r[sd.base + i];
+    a1 += ri * zi;
+    a2 += ri * z[sd.base + i];
+    z[sd.base + i] = zi;
+  }
+  const double rz_new = block_sum(a1, sh);
+  const double rz_old = block_sum(a2, sh);
+  double beta;
+  if (c.iter == 0) beta = 0.0;
+  else if (c.flexible) beta = (rz_new - rz_old) / c.rz;
+  else beta = rz_new / c.rz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.beta = beta;
+    c.rz_old = rz_old;
+    c.rz = rz_new;
+  }
+  for (int i = threadIdx.x; i < sd.g.N; i += BT) p[sd.base + i] = z[sd.base + i] + beta * p[sd.base + i];
+}
+
 // Loop condition of the graph's WHILE node: another iteration while any
 // subgrid is still running and fewer than maxit iterations have been done.
 __global__ void k_b_cond(const PcgScalars* sc, int nsub, int* iter_counter, int maxit,
@@ -547,7 +670,8 @@ __global__ void __launch_bounds__(BT) k_b_true_res(const SubDesc* __restrict__ s
     default: KERNEL<8><<<grid, block, smem, stream>>>(__VA_ARGS__); break;          \
   }
 
-TrsvArgs batch_trsv_args(sfcdd_batch* b, bool fwd) {
+// list 0: every matrix; 1: the local matrices; 2: the coarse matrices
+TrsvArgs batch_trsv_args(sfcdd_batch* b, bool fwd, int list = 0, const double* rhs = nullptr) {
   TrsvArgs a{};
   a.ts = b->ts;
   a.md = b->d_md;
@@ -563,15 +687,38 @@ TrsvArgs batch_trsv_args(sfcdd_batch* b, bool fwd) {
   a.work = fwd ? b->work_f : b->work_b;
   a.nwork = b->nwork;
   a.ticket = fwd ? b->ticket_f : b->ticket_b;
+  if (list != 0) {
+    const auto& L = list == 1 ? b->local_list : b->coarse_list;
+    a.work = fwd ? L.f : L.b;
+    a.nwork = L.n;
+    a.ticket = fwd ? L.tf : L.tb;
+  }
+  if (rhs) a.rhs = rhs;
   a.err = b->err;
   a.sc = b->sc;
   return a;
 }
 
+void enqueue_pair(sfcdd_batch* b, int list, const double* rhs, cudaStream_t s) {
+  launch_trsv_fwd(batch_trsv_args(b, true, list, rhs), b->st, s);
+  launch_trsv_bwd(batch_trsv_args(b, false, list, rhs), b->st, s);
+}
+
+// z = C^{-1} r for every subgrid (R_0 r already in g0), r^T z, beta, p update
 void enqueue_apply(sfcdd_batch* b, cudaStream_t s) {
-  launch_trsv_fwd(batch_trsv_args(b, true), b->st, s);
-  launch_trsv_bwd(batch_trsv_args(b, false), b->st, s);
-  k_b_prolong<<<b->nsub, BT, 0, s>>>(b->dsub, b->ts, b->dbuf, b->r, b->z, b->p, b->sc);
+  if (b->variant != SFCDD_BALANCED) {
+    enqueue_pair(b, 0, nullptr, s);
+    k_b_prolong<<<b->nsub, BT, 0, s>>>(b->dsub, b->ts, b->dbuf, b->r, b->z, b->p, b->sc);
+    return;
+  }
+  enqueue_pair(b, 2, nullptr, s);  // d_0 = A_0^{-1} R_0 r
+  SFCDD_DISPATCH_D(k_b_bal_w, b->d, b->nsub, BT, 0, s, b->dsub, b->code, b->invpad, b->ts, b->dbuf,
+                   b->r, b->bw, b->bgg, b->sc);
+  enqueue_pair(b, 1, b->bgg, s);   // d_i = A_i^{-1} R_i (r - A w)
+  SFCDD_DISPATCH_D(k_b_bal_t, b->d, b->nsub, BT, 0, s, b->dsub, b->code, b->invpad, b->ts, b->dbuf,
+                   b->bt, b->q, b->g0, b->sc);
+  enqueue_pair(b, 2, nullptr, s);  // d_0 = A_0^{-1} R_0 A t
+  k_b_bal_z<<<b->nsub, BT, 0, s>>>(b->dsub, b->ts, b->dbuf, b->bt, b->bw, b->r, b->z, b->p, b->sc);
 }
 
 int build_graph(sfcdd_batch* b, int maxit) {
@@ -623,9 +770,11 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   sfcdd_options o;
   sfcdd_default_options(&o);
   if (opt) o = *opt;
-  if (o.variant != SFCDD_ADDITIVE || o.precision < 0 || o.precision > 2 || o.weighting < 0 ||
-      o.weighting > 1 || o.tensor_cores < -1 || o.tensor_cores > 1)
-    return o.variant != SFCDD_ADDITIVE ? SFCDD_ERR_UNSUPPORTED : SFCDD_ERR_INVALID_ARG;
+  const bool variant_ok = o.variant == SFCDD_ADDITIVE || o.variant == SFCDD_BALANCED;
+  if (!variant_ok || o.precision < 0 || o.precision > 2 || o.weighting < 0 || o.weighting > 1 ||
+      o.tensor_cores < -1 || o.tensor_cores > 1)
+    return !variant_ok ? SFCDD_ERR_UNSUPPORTED : SFCDD_ERR_INVALID_ARG;
+  b->variant = o.variant;
   b->nsub = nsub;
   b->d = d;
   b->gamma = overlap;
@@ -928,6 +1077,11 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   BTRY(balloc(b, &b->p, b->Ntot));
   BTRY(balloc(b, &b->q, b->Ntot));
   BTRY(balloc(b, &b->z, b->Ntot));
+  if (b->variant == SFCDD_BALANCED) {
+    BTRY(balloc(b, &b->bw, b->Ntot));
+    BTRY(balloc(b, &b->bgg, b->Ntot));
+    BTRY(balloc(b, &b->bt, b->Ntot));
+  }
   BTRY(balloc(b, &b->g0, std::max<long long>(g0base, 1)));
   SFCDD_CUDA_OK(cudaMemsetAsync(b->g0, 0, std::max<long long>(g0base, 1) * sizeof(double), s));
   BTRY(balloc(b, &b->sc, nsub));

@@ -230,7 +230,7 @@ class BatchSolver:
 
     def __init__(self, levels_list, P, overlap, *, precision="fp64", weighting="omega", q=0,
                  coeffs=None, flexible=-1, stream=None, local_order="lex", slabs_local=0,
-                 slabs_coarse=0, tensor_cores=-1):
+                 slabs_coarse=0, tensor_cores=-1, variant="additive"):
         L = _lib.lib()
         self.levels = [tuple(int(l) for l in lv) for lv in levels_list]
         self.nsub = len(self.levels)
@@ -244,6 +244,7 @@ class BatchSolver:
             self._coeffs = (C.c_double * self.d)(*[float(c) for c in coeffs])
             opt.coeffs = C.cast(self._coeffs, C.POINTER(C.c_double))
         opt.q = int(q)
+        opt.variant = _lib.VARIANT[variant]
         opt.weighting = _lib.WEIGHTING[weighting]
         opt.precision = _lib.PRECISION[precision]
         opt.flexible = int(flexible)

@@ -95,3 +95,55 @@ def test_more_local_matrices_than_one_grid_dimension():
             us, st = one.solve(f[offs[s]:offs[s + 1]].contiguous(), rtol=1e-10)
         rel = float(torch.linalg.norm(u[offs[s]:offs[s + 1]] - us) / torch.linalg.norm(us))
         assert rel <= 1e-8, (s, rel)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_balanced_batch_equals_single_solves(precision):
+    """eq. balSW in the batched solver: every subgrid's solution and iteration
+    count equal its single balanced solve (and the oracle's balanced PCG count)."""
+    from paper_2110_11211_gb300.solver import BatchSolver, Solver
+    levels = [(6, 4), (3, 7), (5, 5), (2, 8), (4, 4)]
+    Ps = [8, 6, 16, 4, 5]
+    sizes = [inputs.grid_size(lv) for lv in levels]
+    f = np.concatenate([inputs.uniform(80 + s, n) for s, n in enumerate(sizes)])
+    with BatchSolver(levels, Ps, 0.5, precision=precision, variant="balanced") as b:
+        u, tot, per = b.solve(torch.tensor(f, device="cuda"), rtol=1e-10)
+        offs = b.offsets
+        u = u.cpu().numpy()
+    assert tot.fail_index == 0
+    for s, (lv, P) in enumerate(zip(levels, Ps)):
+        fs = f[offs[s]:offs[s + 1]]
+        with Solver(lv, P, 0.5, precision=precision, variant="balanced") as one:
+            us, st = one.solve(torch.tensor(fs, device="cuda"), rtol=1e-10)
+        assert abs(per[s].iters - st.iters) <= 1, (s, per[s].iters, st.iters)
+        us = us.cpu().numpy()
+        assert np.linalg.norm(u[offs[s]:offs[s + 1]] - us) <= 1e-8 * np.linalg.norm(us)
+        if precision == "fp64":
+            S = schwarz.Schwarz(lv, P, 0.5)
+            _, ko, _ = krylov.pcg(lambda v: S.A @ v, S.apply_balanced, fs, rtol=1e-10)
+            assert abs(per[s].iters - ko) <= 1, (s, per[s].iters, ko)
+
+
+def test_balanced_combination_fewer_iterations_same_solution():
+    from paper_2110_11211_gb300.combination import Combination
+    pts = torch.tensor(inputs.unit_points(98, 2000, 2), device="cuda")
+    out, its = {}, {}
+    for variant in ("additive", "balanced"):
+        with Combination(2, 11, 8, precision="fp32", variant=variant) as ct:
+            ct.solve(rtol=1e-10)
+            its[variant] = ct.stats[0].iters
+            out[variant] = ct.evaluate(pts)
+    assert its["balanced"] < its["additive"], its
+    assert float((out["balanced"] - out["additive"]).abs().max()) <= 1e-7 * float(out["additive"].abs().max())
+
+
+def test_batch_non_finite_rhs_reports_nan():
+    from paper_2110_11211_gb300._lib import SfcddError
+    from paper_2110_11211_gb300.solver import BatchSolver
+    levels = [(5, 4), (4, 5)]
+    f = inputs.uniform(99, sum(inputs.grid_size(lv) for lv in levels))
+    f[3] = float("nan")
+    with BatchSolver(levels, 4, 0.5) as b:
+        with pytest.raises(SfcddError) as e:
+            b.solve(torch.tensor(f, device="cuda"), rtol=1e-10)
+        assert e.value.code == -6
