@@ -644,7 +644,6 @@ __global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int nma
 
 __device__ __forceinline__ bool oz_product(unsigned char* dsm, const double* a0, const double* a1,
                                            const double* b, uint32_t& tmem, ErrWord* err, int m) {
-  int* ex = reinterpret_cast<int*>(dsm + oz::E_OFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + oz::BAR_OFF);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   if (threadIdx.x < 32) {
