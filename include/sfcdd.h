@@ -69,10 +69,14 @@ typedef struct {
                            factor: 0 (default) lexicographic grid order (a fill-reducing order:
                            the factor's envelope shrinks to a band), 1 ascending curve position.
                            A_i^{-1} and therefore the preconditioner are the same either way. */
-  int slabs_local;      /* row slabs per 64-row tile row in the local substitutions (one CTA
-                           each): 1, 2 or 4 (rows of 64, 32, 16); 0 (default) = 1.  Splitting
-                           shortens the GEMV on the dependency chain from one tile row to the
-                           next.  sfcdd_autotune picks it by measurement. */
+  int slabs_local;      /* work items of the local substitutions.  1, 2 or 4: row slabs per
+                           64-row tile row (rows of 64, 32, 16), one CTA each, chained through
+                           result slots in L2; splitting shortens the GEMV on the dependency
+                           chain from one tile row to the next.  -1: one CTA per local matrix
+                           sweeping all its tile rows, chained through shared memory (local
+                           matrices of at most 192 tile rows, INVALID_ARG otherwise).
+                           0 (default): -1 where the local matrices allow it, else 1.
+                           sfcdd_autotune picks it by measurement. */
   int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 4.
                            FP32 / BF16 local factors require 2 or 4 (INVALID_ARG otherwise). */
   int tensor_cores;     /* the panel and trailing-update tile products of the local and coarse

@@ -144,9 +144,14 @@ void build_worklists(const std::vector<int>& nt, const std::vector<char>& includ
   };
   std::vector<Item> items;
   for (int m = 0; m < (int)nt.size(); ++m)
-    if (include[m])
+    if (include[m]) {
+      if (nsub[m] == 0) {
+        items.push_back({0, 1, m, -1, 0});  // whole matrix: depends on nothing, taken first
+        continue;
+      }
       for (int r = 0; r < nt[m]; ++r)
         for (int sl = 0; sl < nsub[m]; ++sl) items.push_back({r + 1, nt[m], m, r, sl});
+    }
   std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
     const long long l = a.num * b.den, rr = b.num * a.den;
     return l != rr ? l < rr : a.m < b.m;
@@ -155,7 +160,7 @@ void build_worklists(const std::vector<int>& nt, const std::vector<char>& includ
   wb.clear();
   for (const Item& it : items) {
     wf.push_back({it.m, it.r, it.s});
-    wb.push_back({it.m, nt[it.m] - 1 - it.r, it.s});
+    wb.push_back({it.m, it.r < 0 ? -1 : nt[it.m] - 1 - it.r, it.s});
   }
 }
 
@@ -312,6 +317,9 @@ void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
   }
 }
 
+// Whole-matrix sweeps keep a local matrix's vector in shared memory.
+bool whole_fits(int max_nt) { return max_nt > 0 && max_nt * TILE * (int)sizeof(double) <= WHOLE_ZV_BYTES; }
+
 }  // namespace sfcdd
 
 struct sfcdd_handle {
@@ -360,6 +368,11 @@ struct sfcdd_handle {
   bool tensor_cores = false;  // factorization tile products on tcgen05 (FP32 split / FP64 sliced)
   int cb_coarse = 4;  // tiles per unit diagonal block of the coarse substitution form
   long long fwd_tiles_l = 0, bwd_tiles_l = 0, fwd_tiles_c = 0, bwd_tiles_c = 0;
+  // local factor elements the substitutions need (nonzero rows of the off-block
+  // tiles, whole E tiles), from the zero-row bounds nzr
+  int* d_nzr = nullptr;
+  std::vector<int> h_nzr;
+  long long fwd_elems_l = 0, bwd_elems_l = 0;
   // substitution work lists (each with its own ticket counters: the items of a
   // launch map to tickets modulo the list length): the variant's matrices, and
   // for the balanced variant the local matrices and the coarse matrix alone
@@ -382,6 +395,7 @@ struct sfcdd_handle {
   int graph_kernels[SFCDD_K_COUNT] = {0};
   // accounting
   bool profiling = false;
+  bool auto_local = false;  // slabs_local left to the library: whole-matrix items when they fit
   long long launches[SFCDD_K_COUNT] = {0};
   double ms[SFCDD_K_COUNT] = {0};
   double setup_ms = 0, solve_ms = 0;
@@ -410,7 +424,8 @@ int dalloc(sfcdd_handle* h, T** p, size_t count) {
 // coarse rows of 64, 32 or 16.  FP32 / BF16 launches size their shared memory
 // for the local tiles, so a full 64-row FP64 coarse stage needs an FP64 launch.
 bool valid_slabs(int precision, int nsub_local, int nsub_coarse) {
-  const bool l = nsub_local == 1 || nsub_local == 2 || nsub_local == 4;
+  // nsub_local 0: one CTA per local matrix (whole-matrix sweeps)
+  const bool l = nsub_local == 0 || nsub_local == 1 || nsub_local == 2 || nsub_local == 4;
   const bool c = nsub_coarse == 1 || nsub_coarse == 2 || nsub_coarse == 4;
   return l && c && (precision == SFCDD_FP64 || nsub_coarse != 1);
 }
@@ -484,6 +499,27 @@ struct CoarseHook : LaunchHook {
 
 enum { LIST_MAIN = 0, LIST_LOCAL = 1, LIST_COARSE = 2 };
 
+// Local factor elements each substitution needs, from the zero-row bounds:
+// forward, the nonzero rows of the off-block Lh tiles; backward, the E tile of
+// every row and the nonzero columns of the Lh^T tiles (the same elements).
+static int count_local_elems(sfcdd_handle* h) {
+  const int P = h->P;
+  if (h->variant == SFCDD_COARSE_ONLY) return SFCDD_OK;
+  const int nrows = (int)h->h_nzr.size();
+  SFCDD_CUDA_OK(cudaMemcpy(h->h_nzr.data(), h->d_nzr, nrows * sizeof(int), cudaMemcpyDeviceToHost));
+  long long off = 0, diag = 0;
+  for (int m = 0; m < P; ++m) {
+    const int fb = h->h_vbase[m] / TILE;
+    for (int I = 0; I < h->h_nt[m]; ++I) {
+      off += (long long)(I - h->h_kmin[fb + I]) * h->h_nzr[fb + I] * TILE;
+      diag += TILE2;
+    }
+  }
+  h->fwd_elems_l = off;
+  h->bwd_elems_l = off + diag;
+  return SFCDD_OK;
+}
+
 TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalars* sc,
                    int list = LIST_MAIN) {
   TrsvArgs a{};
@@ -505,6 +541,7 @@ TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalar
   a.ticket = fwd ? wl.tf : wl.tb;
   a.err = h->err;
   a.sc = sc;
+  if (h->nsub_local == 0 && list != LIST_COARSE) a.zv_doubles = h->max_nt * TILE;
   return a;
 }
 
@@ -607,6 +644,7 @@ void enqueue_iteration(sfcdd_handle* h, Prof& pf) {
 int configure_substitution(sfcdd_handle* h, int nsub_local, int nsub_coarse) {
   const int P = h->P;
   cudaStream_t s = h->stream;
+  if (nsub_local == 0 && (!whole_fits(h->max_nt) || !h->d_nzr)) return SFCDD_ERR_INVALID_ARG;
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
   if (h->iter_graph) {
     cudaGraphExecDestroy(h->iter_graph);
@@ -721,7 +759,10 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   if (h->precision < 0 || h->precision > 2 || h->variant < 0 || h->variant > 3 ||
       h->weighting < 0 || h->weighting > 1)
     return SFCDD_ERR_INVALID_ARG;
-  h->nsub_local = o.slabs_local == 0 ? 1 : o.slabs_local;
+  // public -1: one CTA per local matrix (internal 0); 0: decided once the tile
+  // rows are known
+  h->auto_local = o.slabs_local == 0;
+  h->nsub_local = o.slabs_local == 0 ? 1 : (o.slabs_local == -1 ? 0 : o.slabs_local);
   h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
   if (!valid_slabs(h->precision, h->nsub_local, h->nsub_coarse)) return SFCDD_ERR_INVALID_ARG;
   if (o.tensor_cores < -1 || o.tensor_cores > 1) return SFCDD_ERR_INVALID_ARG;
@@ -964,6 +1005,11 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->ts.rowoff = h->d_rowoff;
   h->ts.colptr = h->d_colptr;
   h->ts.colidx = h->d_colidx;
+  // zero-row bounds: whole tiles until the local factors are scanned
+  h->h_nzr.assign(nrows, TILE);
+  TRY(dalloc(h, &h->d_nzr, nrows));
+  SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_nzr, h->h_nzr.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
+  h->ts.nzr = h->d_nzr;
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors above go out of scope
 
   TRY(dalloc(h, &h->err, 1));
@@ -1042,10 +1088,15 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     h->ltiles = work_tiles;
     h->lut = work_ut;
   }
+  if (h->variant != SFCDD_COARSE_ONLY)
+    pf.run(SFCDD_K_TRSM, [&] {
+      launch_offblock_rows(h->ts, 0, P, h->max_nt, h->ltiles, h->st, h->d_nzr, s);
+    });
   SFCDD_CUDA_OK(cudaStreamWaitEvent(s, ev_coarse, 0));
   cudaEventDestroy(ev_coarse);
   SFCDD_CUDA_OK(cudaGetLastError());
 
+  if (h->auto_local && h->variant != SFCDD_COARSE_ONLY && whole_fits(h->max_nt)) h->nsub_local = 0;
   TRY(configure_substitution(h, h->nsub_local, h->nsub_coarse));
   if (h->variant == SFCDD_BALANCED)
     for (int k = 0; k < 4; ++k) TRY(dalloc(h, &h->bal[k], N));
@@ -1081,6 +1132,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   h->setup_ms = ms;
+  TRY(count_local_elems(h));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (xs) dfree(h, xs);
@@ -1514,7 +1566,10 @@ int sfcdd_selftest(sfcdd_handle* h, int kind, int* detail) {
   } else {
     // a forward substitution whose first work item never runs: the items that
     // depend on its rows wait on result slots nothing writes, give up after the
-    // bounded spin, record TIMEOUT, and every other waiter then stops waiting
+    // bounded spin, record TIMEOUT, and every other waiter then stops waiting.
+    // Whole-matrix items depend on nothing, so the test runs on row slabs.
+    const int keep_l = h->nsub_local;
+    if (keep_l == 0) TRY(configure_substitution(h, 1, h->nsub_coarse));
     const auto& wl = h->lists[LIST_MAIN];
     if (wl.n < 2) return SFCDD_ERR_INVALID_ARG;
     const unsigned long long one = 1;
@@ -1529,6 +1584,15 @@ int sfcdd_selftest(sfcdd_handle* h, int kind, int* detail) {
     launch_fill_pending(h->dbuf, h->vtotal, s);
     SFCDD_CUDA_OK(cudaMemsetAsync(wl.tf, 0, sizeof(unsigned long long), s));
     SFCDD_CUDA_OK(cudaMemsetAsync(wl.tb, 0, sizeof(unsigned long long), s));
+    if (keep_l == 0) {
+      ErrWord e{};
+      SFCDD_CUDA_OK(cudaMemcpyAsync(&e, h->err, sizeof(ErrWord), cudaMemcpyDeviceToHost, s));
+      SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+      SFCDD_CUDA_OK(cudaMemsetAsync(h->err, 0, sizeof(ErrWord), s));
+      TRY(configure_substitution(h, 0, h->nsub_coarse));
+      SFCDD_CUDA_OK(cudaMemcpyAsync(h->err, &e, sizeof(ErrWord), cudaMemcpyHostToDevice, s));
+      SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    }
   }
   ErrWord e{};
   SFCDD_CUDA_OK(cudaMemcpyAsync(&e, h->err, sizeof(ErrWord), cudaMemcpyDeviceToHost, s));
@@ -1555,11 +1619,12 @@ int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out) {
   int best_l = h->nsub_local, best_c = h->nsub_coarse, cand = 0;
   float best = -1.f;
   int rc = SFCDD_OK;
-  const int opts[3] = {1, 2, 4};
-  for (int il = 0; il < 3 && rc == SFCDD_OK; ++il)
+  const int opts[4] = {1, 2, 4, 0};  // 0: whole-matrix local items
+  for (int il = 0; il < 4 && rc == SFCDD_OK; ++il)
     for (int ic = 0; ic < 3 && rc == SFCDD_OK; ++ic) {
       const int sl = opts[il], sc = opts[ic];
       if (!valid_slabs(h->precision, sl, sc)) continue;
+      if (sl == 0 && (!whole_fits(h->max_nt) || h->variant == SFCDD_COARSE_ONLY)) continue;
       rc = configure_substitution(h, sl, sc);
       if (rc != SFCDD_OK) break;
       Prof pf(h, s);
@@ -1590,7 +1655,7 @@ int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out) {
   if (ec != 0) return ec;
   TRY(configure_substitution(h, best_l, best_c));
   if (out) {
-    out->slabs_local = best_l;
+    out->slabs_local = best_l == 0 ? -1 : best_l;
     out->slabs_coarse = best_c;
     out->apply_ms = best / reps;
     out->candidates = cand;
@@ -1727,11 +1792,12 @@ double sfcdd_kernel_work(const sfcdd_handle* h, int kc) {
   if (!h) return 0.0;
   const double esz = h->precision == SFCDD_FP64 ? 8 : (h->precision == SFCDD_FP32 ? 4 : 2);
   const bool loc = h->variant != SFCDD_COARSE_ONLY, crs = h->variant != SFCDD_ONE_LEVEL;
-  // forward: the Lh tiles left of each row's diagonal block; backward: the
-  // E tiles of the row's diagonal block and the Lh^T tiles below it
+  // forward: the nonzero rows of the Lh tiles left of each row's diagonal
+  // block; backward: the E tiles of the row's diagonal block and the nonzero
+  // columns of the Lh^T tiles below it (coarse: whole tiles)
   const double t2 = (double)TILE2;
-  const double lf = loc ? (double)h->fwd_tiles_l * t2 * esz : 0.0;
-  const double lb = loc ? (double)h->bwd_tiles_l * t2 * esz : 0.0;
+  const double lf = loc ? (double)h->fwd_elems_l * esz : 0.0;
+  const double lb = loc ? (double)h->bwd_elems_l * esz : 0.0;
   const double cf = crs ? (double)h->fwd_tiles_c * t2 * 8.0 : 0.0;
   const double cbk = crs ? (double)h->bwd_tiles_c * t2 * 8.0 : 0.0;
   switch (kc) {

@@ -125,6 +125,7 @@ void bfree(sfcdd_batch* b, void* p) {
 // slab) items for the given slab counts; drops the captured solve graph.
 int batch_configure(sfcdd_batch* b, int nsub_local, int nsub_coarse) {
   cudaStream_t s = b->stream;
+  if (nsub_local == 0 && !whole_fits(b->max_nt_local)) return SFCDD_ERR_INVALID_ARG;
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
@@ -696,6 +697,7 @@ TrsvArgs batch_trsv_args(sfcdd_batch* b, bool fwd, int list = 0, const double* r
   if (rhs) a.rhs = rhs;
   a.err = b->err;
   a.sc = b->sc;
+  if (b->nsub_local == 0 && list != 2) a.zv_doubles = b->max_nt_local * TILE;
   return a;
 }
 
@@ -993,6 +995,15 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   b->ts.rowoff = d_rowoff;
   b->ts.colptr = d_colptr;
   b->ts.colidx = d_colidx;
+  // zero-row bounds of the off-block tiles: whole tiles until the factors are scanned
+  {
+    int* d_nzr = nullptr;
+    BTRY(balloc(b, &d_nzr, nrows));
+    const std::vector<int> whole(nrows, TILE);
+    SFCDD_CUDA_OK(cudaMemcpyAsync(d_nzr, whole.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    b->ts.nzr = d_nzr;
+  }
 
   // local matrices and factors (Sec. 3.1), coarse matrices and FP64 factors (eq. csm)
   BTRY(balloc(b, &b->err, 1));
@@ -1038,6 +1049,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
     b->ltiles = work_tiles;
     b->lut = work_ut;
   }
+  launch_offblock_rows(b->ts, 0, b->nlocal, b->max_nt_local, b->ltiles, b->st,
+                       const_cast<int*>(b->ts.nzr), s);
   BTRY(balloc(b, &b->ctiles, b->sky.ctiles * TILE2));
   {
     const int smem = TILE2 * (int)(sizeof(double) + sizeof(int));
@@ -1049,6 +1062,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
                Store::F64, diag_cnt, b->err, s, &nohook, 1, o.tensor_cores != 0);
   BTRY(balloc(b, &b->cut, b->sky.ctiles * TILE2));
   unitize_tiles(b->ts, b->nlocal, nsub, b->sky.max_ctiles, b->ctiles, b->cut, Store::F64, s);
+  launch_offblock_rows(b->ts, b->nlocal, nsub, b->max_nt_coarse, b->ctiles, Store::F64,
+                       const_cast<int*>(b->ts.nzr), s);
   SFCDD_CUDA_OK(cudaGetLastError());
   b->factor_bytes = b->sky.ltiles * TILE2 * (b->precision == 0 ? 8 : b->precision == 1 ? 4 : 2) +
                     b->sky.ctiles * TILE2 * 8;
@@ -1057,9 +1072,10 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   // coarse rows in 16-row slabs; sfcdd_batch_autotune may change both counts)
   b->h_start = start_all;
   {
-    const int sl = o.slabs_local == 0 ? 1 : o.slabs_local;
+    // slabs_local -1: one CTA per local matrix (internal 0)
+    const int sl = o.slabs_local == 0 ? 1 : (o.slabs_local == -1 ? 0 : o.slabs_local);
     const int sc = o.slabs_coarse == 0 ? (b->st == Store::F64 ? 1 : 4) : o.slabs_coarse;
-    const bool ok = (sl == 1 || sl == 2 || sl == 4) && (sc == 1 || sc == 2 || sc == 4) &&
+    const bool ok = (sl == 0 || sl == 1 || sl == 2 || sl == 4) && (sc == 1 || sc == 2 || sc == 4) &&
                     (b->st == Store::F64 || sc != 1);
     if (!ok) return SFCDD_ERR_INVALID_ARG;
     BTRY(batch_configure(b, sl, sc));
@@ -1254,13 +1270,14 @@ int sfcdd_batch_autotune(sfcdd_batch* b, int reps, sfcdd_tuning* out) {
   cudaEvent_t e0, e1;
   SFCDD_CUDA_OK(cudaEventCreate(&e0));
   SFCDD_CUDA_OK(cudaEventCreate(&e1));
-  const int opts[3] = {1, 2, 4};
+  const int opts[4] = {1, 2, 4, 0};  // 0: whole-matrix local items
   int best_l = b->nsub_local, best_c = b->nsub_coarse, cand = 0, rc = SFCDD_OK;
   float best = -1.f;
-  for (int il = 0; il < 3 && rc == SFCDD_OK; ++il)
+  for (int il = 0; il < 4 && rc == SFCDD_OK; ++il)
     for (int ic = 0; ic < 3 && rc == SFCDD_OK; ++ic) {
       const int sl = opts[il], sc = opts[ic];
       if (b->st != Store::F64 && sc == 1) continue;  // 64-row FP64 stage: FP64 launches only
+      if (sl == 0 && !whole_fits(b->max_nt_local)) continue;
       rc = batch_configure(b, sl, sc);
       if (rc != SFCDD_OK) break;
       for (int k = 0; k < 2; ++k) pair();
@@ -1289,7 +1306,7 @@ int sfcdd_batch_autotune(sfcdd_batch* b, int reps, sfcdd_tuning* out) {
   if (e.code != 0) return e.code;
   BTRY(batch_configure(b, best_l, best_c));
   if (out) {
-    out->slabs_local = best_l;
+    out->slabs_local = best_l == 0 ? -1 : best_l;
     out->slabs_coarse = best_c;
     out->apply_ms = best / reps;
     out->candidates = cand;

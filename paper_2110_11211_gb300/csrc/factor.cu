@@ -987,6 +987,53 @@ static void unitize_t(const TileSetDev& ts, int mat0, int nmat, int max_stored, 
   k_unitize<T><<<mat_grid(max_stored, nmat), FB, sm, s>>>(ts, mat0, nmat, tiles, ut);
 }
 
+// Zero rows of the off-block Lh tiles.  The Cholesky factor keeps the row
+// envelope of A_i (no fill left of a row's first nonzero), and Lh = L D^{-1}
+// keeps every zero row of L zero, so in tile row I the rows whose envelope
+// starts inside the diagonal tile are zero in all of the row's off-block tiles.
+// With the narrow local bands of curve-ordered subdomains that is most rows.
+// The bound is taken from the stored values themselves (any nonzero bit
+// pattern counts, -0 included), so skipping the rows beyond it is exact in every
+// precision.  One warp per tile row, scanning each tile from its last row up.
+template <int ES>
+__global__ void k_offblock_rows(TileSetDev ts, int mat0, int nmat, const unsigned char* __restrict__ tiles,
+                                int* __restrict__ nzr) {
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
+  const int I = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (I >= ts.nt[m]) return;  // whole warp
+  const int fb = ts.vbase[m] / TILE;
+  const long long tb = ts.tbase[m];
+  constexpr int WPR = TILE * ES / 4;  // 32-bit words per tile row
+  int last = 0;
+  for (int K = ts.kmin[fb + I]; K < I; ++K) {
+    const uint32_t* tp = reinterpret_cast<const uint32_t*>(tiles + tile_at(ts, tb, fb, I, K) * ES);
+    for (int rr = TILE - 1; rr >= last; --rr) {
+      uint32_t w = 0;
+#pragma unroll
+      for (int j = lane; j < WPR; j += 32) w |= __ldg(tp + rr * WPR + j);
+      if (__any_sync(0xffffffffu, w != 0u)) {
+        last = rr + 1;
+        break;
+      }
+    }
+  }
+  if (lane == 0) nzr[fb + I] = last;
+}
+
+void launch_offblock_rows(const TileSetDev& ts, int mat0, int nmat, int max_nt, const void* tiles,
+                          Store st, int* nzr, cudaStream_t s) {
+  if (nmat <= 0 || max_nt <= 0) return;
+  const dim3 grid = mat_grid((max_nt + 3) / 4, nmat);
+  const unsigned char* t = static_cast<const unsigned char*>(tiles);
+  switch (st) {
+    case Store::F64: k_offblock_rows<8><<<grid, 128, 0, s>>>(ts, mat0, nmat, t, nzr); break;
+    case Store::F32: k_offblock_rows<4><<<grid, 128, 0, s>>>(ts, mat0, nmat, t, nzr); break;
+    default: k_offblock_rows<2><<<grid, 128, 0, s>>>(ts, mat0, nmat, t, nzr); break;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Substitution form with cb-tile diagonal blocks (one matrix, FP64).  D_J is
 // the lower block-triangular cb x cb-tile diagonal block J of the factor and

@@ -193,6 +193,10 @@ struct TileSetDev {
   const int* colidx;         // those rows, ascending
   const int* lperm;          // [vbase + r] curve position of local row r (null: curve order)
   const int* linv;           // [vbase + o] local row of offset o in the range (null: curve order)
+  // [fb + I] rows of tile row I's off-block tiles that may hold nonzeros: rows
+  // nzr.. of every Lh tile left of the row's diagonal block are zero, and so are
+  // columns nzr.. of their transposes (null: no such bound, read whole tiles)
+  const int* nzr;
 };
 
 __device__ __forceinline__ long long tile_at(const TileSetDev& ts, long long tb, int fb, int I,
@@ -391,7 +395,7 @@ void launch_coarse_adjacency(const GridDev& g, const PartDev& pd, const unsigned
 // trsv.cu
 struct TrsvWork {
   int mat;
-  int row;
+  int row;   // tile row; -1: the whole matrix (one CTA sweeps all its rows)
   int slab;  // rows [64 / nsub * slab, 64 / nsub * (slab + 1)) of the tile row
 };
 // Where the right-hand side of a matrix comes from and which solve it belongs to:
@@ -410,6 +414,10 @@ struct MatDesc {
 // written in the current launch.
 constexpr unsigned long long TRSV_PENDING = 0x7FF4DEADBEEF0000ull;
 void launch_fill_pending(double* p, long long n, cudaStream_t s);
+// Largest shared-memory vector of a whole-matrix substitution item (a local
+// matrix of up to 192 tile rows).
+constexpr int WHOLE_ZV_BYTES = 96 * 1024;
+bool whole_fits(int max_nt);
 struct TrsvArgs {
   TileSetDev ts;
   const MatDesc* md;           // per matrix
@@ -428,9 +436,17 @@ struct TrsvArgs {
   unsigned long long* ticket;  // monotone ticket counter
   ErrWord* err;
   const PcgScalars* sc;        // per problem (md.sub); null: no early exit
+  // > 0: the local matrices of the work list are whole-matrix items (row < 0),
+  // each swept by one CTA through a shared-memory vector of this many doubles
+  // (the largest local tile count times TILE); 0: row-slab items only
+  int zv_doubles;
 };
 // grid > 0 launches that many CTAs instead of one per work item (self-test only)
 void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s, int grid = 0);
+// Fills nzr[fb + I] of the local matrices [mat0, mat0 + nmat) (cb = 1) from the
+// stored Lh tiles: one past the last row holding a nonzero bit pattern.
+void launch_offblock_rows(const TileSetDev& ts, int mat0, int nmat, int max_nt, const void* tiles,
+                          Store st, int* nzr, cudaStream_t s);
 // Factorization and inversion of one 64 x 64 FP64 tile in place (self-test of the
 // breakdown report: a non-positive pivot sets NOT_SPD with index m).
 void launch_potrf_one(double* tile, ErrWord* err, int m, cudaStream_t s);

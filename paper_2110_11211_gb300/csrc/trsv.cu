@@ -53,11 +53,13 @@ constexpr long long MBAR_LIMIT = 1ll << 26;
 constexpr long long SPIN_FAST = 1 << 12;   // polls before the poller starts to back off
 
 // Shared-memory plan of a launch whose local factors have element size ES.
-template <int ES>
+template <int ES, bool WHOLE = false>
 struct Plan {
   // slab ring: 32 KB (one FP64 or two FP32 tiles, four BF16), so that four or more
-  // CTAs fit an SM; a 64-row FP64 slab then has a single stage
-  static constexpr int RING = (ES == 8 ? 1 : 2) * TILE2 * ES;
+  // CTAs fit an SM; a 64-row FP64 slab then has a single stage.  Launches with
+  // whole-matrix items: eight 32-row pieces (FP64 128 KB: a CTA streams the whole
+  // matrix and needs the bytes in flight of an SM), plus the matrix vector.
+  static constexpr int RING = WHOLE ? 8 * 32 * TILE * ES : (ES == 8 ? 1 : 2) * TILE2 * ES;
   static constexpr int ZBUF = MAXST * TILE * 8;
   static constexpr int BYTES = RING + ZBUF + 3 * MAXST * 8;
 };
@@ -153,6 +155,13 @@ __device__ __forceinline__ void sm_pair(const __nv_bfloat16* p, float& a, float&
   b = __uint_as_float(u & 0xffff0000u);
 }
 
+// One element of a shared-memory slab row as the accumulation type.
+__device__ __forceinline__ double sm_one(const double* p) { return *p; }
+__device__ __forceinline__ float sm_one(const float* p) { return *p; }
+__device__ __forceinline__ float sm_one(const __nv_bfloat16* p) {
+  return __uint_as_float((unsigned)*reinterpret_cast<const unsigned short*>(p) << 16);
+}
+
 // Sums v[i] over the 32 lanes for the warp's RPW rows: log2(RPW) halving
 // exchanges (each lane keeps the half its lane bit selects) followed by a
 // butterfly over the remaining lanes.  Every lane returns the total of row
@@ -229,24 +238,53 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
     nE = blk1 - blk0;
     ntile = nE + ncl;
   }
+  // Zero rows of the off-block tiles.  Forward: only the slab's rows below the
+  // tile row's bound are streamed and applied (none: z = b).  Backward: an Lh^T
+  // tile whose source row bound is at most TILE / 2 has its nonzeros in the left
+  // half of every row; only those halves are streamed and applied, against the
+  // first TILE / 2 entries of x_c.
+  int nrow = R;
+  if (FWD && a.ts.nzr) {
+    nrow = min(R, max(0, a.ts.nzr[fb + r] - R * slab));
+    if (nrow == 0) ntile = 0;
+  }
+  auto half_tile = [&](int t) {
+    return !FWD && t >= nE && a.ts.nzr != nullptr && a.ts.nzr[fb + cl[ncl - 1 - (t - nE)]] <= TILE / 2;
+  };
   if (threadIdx.x >= NCONS) {
-    if (threadIdx.x == NCONS) {
-      for (int t = 0; t < ntile; ++t) {
-        const int s = t % NS, k = t / NS;
-        if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 10);
-        const T* src;
-        if (FWD) {
-          src = row0 + (long long)t * TILE2;
-        } else if (t < nE) {
-          // E(r, kp): ut holds the block's lower tiles, the tiles array its upper ones
-          const int kp = blk0 + t;
-          src = (kp <= r ? ut + tile_at(a.ts, tb, fb, r, kp) : lt + tile_at(a.ts, tb, fb, kp, r)) +
-                soff;
-        } else {
-          src = ut + tile_at(a.ts, tb, fb, cl[ncl - 1 - (t - nE)], r) + soff;
+    // producer warp: every lane waits for the stage; lane 0 (or, for half
+    // tiles, the lanes row by row) issues the copies
+    const int pl = threadIdx.x - NCONS;
+    for (int t = 0; t < ntile; ++t) {
+      const int s = t % NS, k = t / NS;
+      if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 10);
+      unsigned char* dst = sm.ring + (size_t)s * SB;
+      const T* src;
+      unsigned bytes = SB;
+      if (FWD) {
+        src = row0 + (long long)t * TILE2;
+        bytes = (unsigned)(nrow * TILE * (int)sizeof(T));
+      } else if (t < nE) {
+        // E(r, kp): ut holds the block's lower tiles, the tiles array its upper ones
+        const int kp = blk0 + t;
+        src = (kp <= r ? ut + tile_at(a.ts, tb, fb, r, kp) : lt + tile_at(a.ts, tb, fb, kp, r)) +
+              soff;
+      } else {
+        src = ut + tile_at(a.ts, tb, fb, cl[ncl - 1 - (t - nE)], r) + soff;
+      }
+      // half tiles: FP64 copies the left halves row by row; narrower types keep
+      // one copy of the slab (their rows' halves are too short to copy alone)
+      if (sizeof(T) < 8 || !half_tile(t)) {
+        if (pl == 0) {
+          mbar_expect_tx(&sm.full[s], bytes);
+          bulk_copy(dst, src, bytes, &sm.full[s]);
         }
-        mbar_expect_tx(&sm.full[s], SB);
-        bulk_copy(sm.ring + (size_t)s * SB, src, SB, &sm.full[s]);
+      } else {
+        constexpr unsigned HB = TILE / 2 * sizeof(T);  // 16-byte multiple for every T
+        if (pl == 0) mbar_expect_tx(&sm.full[s], R * HB);
+        __syncwarp();
+        for (int j = pl; j < R; j += 32)
+          bulk_copy(dst + (size_t)j * TILE * sizeof(T), src + (long long)j * TILE, HB, &sm.full[s]);
       }
     }
     return;
@@ -286,38 +324,51 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
     if (threadIdx.x < R)
       a.y[vb + rbase + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
   }
+  // dependency vector of tile tt: z of the block comes from the forward launch
+  // (a previous kernel, never the sentinel), the other vectors from this launch
+  auto dep = [&](int tt) -> const double* {
+    return FWD       ? a.y + vb + (k0 + tt) * TILE
+           : tt < nE ? a.zc + vb + (blk0 + tt) * TILE
+                     : a.dout + vb + cl[ncl - 1 - (tt - nE)] * TILE;
+  };
   for (int t = 0; t < ntile; ++t) {
     const int s = t % NS;
     const unsigned ph = (t / NS) & 1;
     double* zs = sm.zbuf + s * TILE;
-    double2 v;
+    const bool half = half_tile(t);
+    double2 v = make_double2(0.0, 0.0);
     if (w == 0) {
       // every warp is done with the previous use of stage s (and of zs)
       if (t >= NS) mbar_wait(&sm.empty[s], ph ^ 1, a.err, 13);
-      // z of the block comes from the forward launch (a previous kernel, never
-      // the sentinel), the other vectors from this launch
-      const double* dp = FWD      ? a.y + vb + (k0 + t) * TILE
-                         : t < nE ? a.zc + vb + (blk0 + t) * TILE
-                                  : a.dout + vb + cl[ncl - 1 - (t - nE)] * TILE;
-      v = wait_pair(dp + 2 * lane, a.err, FWD ? 1 : 2);
-      *reinterpret_cast<double2*>(zs + 2 * lane) = v;
+      if (!half || lane < TILE / 4) {
+        v = wait_pair(dep(t) + 2 * lane, a.err, FWD ? 1 : 2);
+        *reinterpret_cast<double2*>(zs + 2 * lane) = v;
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.zbar[s]);
     } else {
       mbar_wait(&sm.zbar[s], ph, a.err, 14);
-      v = *reinterpret_cast<const double2*>(zs + 2 * lane);
+      if (!half) v = *reinterpret_cast<const double2*>(zs + 2 * lane);
     }
-    // backward: + E z, - Lh^T x
-    const bool neg = !FWD && t >= nE;
-    const A v0 = A(neg ? -v.x : v.x), v1 = A(neg ? -v.y : v.y);
     mbar_wait(&sm.full[s], ph, a.err, 11);
     const T* st = reinterpret_cast<const T*>(sm.ring + (size_t)s * SB);
+    if (half) {
+      // - Lh^T x on the left half: column `lane`
+      const A vh = A(-zs[lane]);
 #pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-      A l0, l1;
-      sm_pair(st + (rloc + i) * TILE + 2 * lane, l0, l1);
-      acc[i] = fma(l0, v0, acc[i]);
-      acc[i] = fma(l1, v1, acc[i]);
+      for (int i = 0; i < RPW; ++i) acc[i] = fma(sm_one(st + (rloc + i) * TILE + lane), vh, acc[i]);
+    } else {
+      // backward: + E z, - Lh^T x
+      const bool neg = !FWD && t >= nE;
+      const A v0 = A(neg ? -v.x : v.x), v1 = A(neg ? -v.y : v.y);
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        if (FWD && rloc + i >= nrow) break;  // zero rows (not streamed)
+        A l0, l1;
+        sm_pair(st + (rloc + i) * TILE + 2 * lane, l0, l1);
+        acc[i] = fma(l0, v0, acc[i]);
+        acc[i] = fma(l1, v1, acc[i]);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.empty[s]);
@@ -337,9 +388,258 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
   }
 }
 
-template <class T, class A, bool FWD>
+// ---------------------------------------------------------------------------
+// Whole-matrix items: one CTA sweeps every tile row of a local matrix (cb = 1,
+// zero-row bounds known), so the row-to-row chain passes through shared
+// memory and a CTA barrier instead of result slots in L2 polled by other CTAs.
+// With the narrow bands of curve-ordered subdomains the chain carries about one
+// off-block tile per row, which makes the cross-CTA hand-off the bound of the
+// row-slab items; here a step costs the tile's FMAs and two barriers.  The
+// matrix vector (z, then x) lives in shared memory.
+//   forward   z_I = b_I - sum_{K < I} Lh_IK z_K   (rows below nzr[I]: z = b)
+//   backward  x_I = E_I z_I - sum_{K > I} Lh_KI^T x_K  (columns below nzr[K])
+// The producer warp streams the factor in pieces of 32 tile rows (forward: the
+// nonzero rows of each off-block tile; backward: the two halves of E_I, then
+// per Lh^T tile its left halves (FP64, nzr[K] <= TILE / 2: 64 rows of 32
+// columns, packed) or its two halves) through an eight-stage ring.  Consumer
+// thread (j, g) = (tid / 8, tid % 8) owns tile rows j and j + 32 and the
+// 16-byte chunks g + 8 k of a piece row, so each quarter-warp phase of a
+// shared load reads one contiguous 128-byte row segment.
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Right-hand side of local row grow of matrix m (zero beyond its size).
+__device__ __forceinline__ double local_rhs(const TrsvArgs& a, const MatDesc& md, int vb, int n,
+                                            int grow) {
+  if (grow >= n) return 0.0;
+  int pos;
+  if (a.ts.lperm) {
+    pos = a.ts.lperm[vb + grow];
+  } else {
+    pos = md.start + grow;
+    if (pos >= md.rhs_len) pos -= md.rhs_len;
+  }
+  return a.rhs[md.rhs_base + pos];
+}
+
+// acc += sum over the thread's CH chunks of one piece row (EPC elements each)
+// times the matching entries of the vector slice xs.
+template <class T, class A, int CH>
+__device__ __forceinline__ void piece_row_dot(const T* __restrict__ row, int g, const A* xs, A& acc) {
+  constexpr int EPC = 16 / (int)sizeof(T);
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    const T* p = row + (g + 8 * k) * EPC;
+#pragma unroll
+    for (int e = 0; e < EPC; e += 2) {
+      A l0, l1;
+      sm_pair(p + e, l0, l1);
+      acc = fma(l0, xs[k * EPC + e], acc);
+      acc = fma(l1, xs[k * EPC + e + 1], acc);
+    }
+  }
+}
+
+template <class A>
+__device__ __forceinline__ A sum8(A v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
+template <class T, class A, bool FWD, int RING>
+__device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const T* __restrict__ ut,
+                             int m, const RowSmem& sm, double* __restrict__ zv) {
+  constexpr int PR = 32;                                   // rows of a piece
+  constexpr unsigned PB = PR * TILE * sizeof(T);           // piece bytes
+  constexpr int NS = (RING / (int)PB) < MAXST ? (RING / (int)PB) : MAXST;
+  constexpr int EPC = 16 / (int)sizeof(T);                 // elements per 16-byte chunk
+  constexpr int CH = TILE / EPC / 8;                       // chunks of a full row per thread
+  constexpr unsigned HB = TILE / 2 * sizeof(T);            // half a tile row
+  static_assert(NS >= 2, "whole-matrix ring needs two pieces");
+  const long long tb = a.ts.tbase[m];
+  const int vb = a.ts.vbase[m];
+  const int fb = vb / TILE;
+  const int nt = a.ts.nt[m];
+  auto half_piece = [&](int K) { return sizeof(T) == 8 && a.ts.nzr[fb + K] <= TILE / 2; };
+
+  if (threadIdx.x >= NCONS) {
+    // producer warp: the pieces in consumption order
+    const int pl = threadIdx.x - NCONS;
+    int t = 0;
+    auto put = [&](const T* src, unsigned bytes, bool half) {
+      const int s = t % NS, k = t / NS;
+      if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 20);
+      unsigned char* dst = sm.ring + (size_t)s * PB;
+      if (!half) {
+        if (pl == 0) {
+          mbar_expect_tx(&sm.full[s], bytes);
+          bulk_copy(dst, src, bytes, &sm.full[s]);
+        }
+      } else {
+        if (pl == 0) mbar_expect_tx(&sm.full[s], TILE * HB);
+        __syncwarp();
+        for (int j = pl; j < TILE; j += 32)
+          bulk_copy(dst + (size_t)j * HB, src + (long long)j * TILE, HB, &sm.full[s]);
+      }
+      ++t;
+    };
+    if (FWD) {
+      for (int I = 0; I < nt; ++I) {
+        const int nz = a.ts.nzr[fb + I];
+        for (int K = a.ts.kmin[fb + I]; K < I; ++K)
+          for (int p = 0; p * PR < nz; ++p)
+            put(lt + tile_at(a.ts, tb, fb, I, K) + (long long)p * PR * TILE,
+                (unsigned)(min(PR, nz - p * PR) * TILE * (int)sizeof(T)), false);
+      }
+    } else {
+      if (pl == 0) {
+        const unsigned zb = (unsigned)(nt * TILE * (int)sizeof(double));
+        mbar_expect_tx(&sm.zbar[0], zb);
+        bulk_copy(zv, a.zc + vb, zb, &sm.zbar[0]);
+      }
+      for (int I = nt - 1; I >= 0; --I) {
+        const T* e = ut + tile_at(a.ts, tb, fb, I, I);
+        put(e, PB, false);
+        put(e + PR * TILE, PB, false);
+        const int* cl = a.ts.colidx + a.ts.colptr[fb + I];
+        const int ncl = a.ts.colptr[fb + I + 1] - a.ts.colptr[fb + I];
+        for (int q = 0; q < ncl; ++q) {
+          const int K = cl[q];
+          const T* src = ut + tile_at(a.ts, tb, fb, K, I);
+          if (half_piece(K)) {
+            put(src, 0, true);
+          } else {
+            put(src, PB, false);
+            put(src + PR * TILE, PB, false);
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int j = tid >> 3, g = tid & 7;
+  const MatDesc md = a.md[m];
+  const int n = a.ts.n[m];
+  int t = 0;
+  // next piece: wait for it; returns its rows
+  auto take = [&]() -> const T* {
+    const int s = t % NS;
+    mbar_wait(&sm.full[s], (t / NS) & 1, a.err, 21);
+    return reinterpret_cast<const T*>(sm.ring + (size_t)s * PB);
+  };
+  auto give = [&]() {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.empty[t % NS]);
+    ++t;
+  };
+  // the thread's entries of a full vector tile: chunks g + 8 k
+  auto slice = [&](int K, A (&xs)[CH * EPC], bool neg) {
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) {
+        const double v = zv[K * TILE + (g + 8 * k) * EPC + e];
+        xs[k * EPC + e] = A(neg ? -v : v);
+      }
+  };
+
+  if (FWD) {
+    // the right-hand side, gathered once: zv holds b_I until z_I replaces it
+    for (int r = tid; r < nt * TILE; r += NCONS) zv[r] = local_rhs(a, md, vb, n, r);
+    consumers_sync();
+    for (int I = 0; I < nt; ++I) {
+      const int r0 = I * TILE + j, r1 = r0 + PR;
+      const int nz = a.ts.nzr[fb + I];
+      A acc0 = A(0), acc1 = A(0);
+      for (int K = a.ts.kmin[fb + I]; K < I; ++K) {
+        A xs[CH * EPC];
+        slice(K, xs, false);
+        for (int p = 0; p * PR < nz; ++p) {
+          const T* st = take();
+          if (j < nz - p * PR) piece_row_dot<T, A, CH>(st + j * TILE, g, xs, p ? acc1 : acc0);
+          give();
+        }
+      }
+      acc0 = sum8(acc0);
+      acc1 = sum8(acc1);
+      if (g == 0) {
+        const double z0 = double(A(zv[r0]) - acc0), z1 = double(A(zv[r1]) - acc1);
+        zv[r0] = z0;
+        zv[r1] = z1;
+        a.y[vb + r0] = z0;
+        a.y[vb + r1] = z1;
+        a.zc[vb + r0] = z0;
+        a.zc[vb + r1] = z1;
+        // the backward slots, polled by row-slab items of other launches
+        a.dout[vb + r0] = __longlong_as_double((long long)TRSV_PENDING);
+        a.dout[vb + r1] = __longlong_as_double((long long)TRSV_PENDING);
+      }
+      consumers_sync();  // z_I visible to the next rows
+    }
+  } else {
+    mbar_wait(&sm.zbar[0], 0, a.err, 22);  // z in zv
+    for (int I = nt - 1; I >= 0; --I) {
+      A acc0 = A(0), acc1 = A(0);
+      {
+        A xs[CH * EPC];
+        slice(I, xs, false);
+        const T* st = take();
+        piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc0);
+        give();
+        st = take();
+        piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc1);
+        give();
+      }
+      const int* cl = a.ts.colidx + a.ts.colptr[fb + I];
+      const int ncl = a.ts.colptr[fb + I + 1] - a.ts.colptr[fb + I];
+      for (int q = 0; q < ncl; ++q) {
+        const int K = cl[q];
+        if (half_piece(K)) {
+          // 64 rows of 32 columns: chunks g and g + 8 of rows j and j + 32
+          A xs[2 * EPC];
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int e = 0; e < EPC; ++e) xs[k * EPC + e] = A(-zv[K * TILE + (g + 8 * k) * EPC + e]);
+          const T* st = take();
+          piece_row_dot<T, A, 2>(st + j * (TILE / 2), g, xs, acc0);
+          piece_row_dot<T, A, 2>(st + (j + PR) * (TILE / 2), g, xs, acc1);
+          give();
+        } else {
+          A xs[CH * EPC];
+          slice(K, xs, true);
+          const T* st = take();
+          piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc0);
+          give();
+          st = take();
+          piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc1);
+          give();
+        }
+      }
+      acc0 = sum8(acc0);
+      acc1 = sum8(acc1);
+      consumers_sync();  // every read of z_I is done
+      if (g == 0) {
+        const int r0 = I * TILE + j, r1 = r0 + PR;
+        zv[r0] = double(acc0);
+        zv[r1] = double(acc1);
+        a.dout[vb + r0] = double(acc0);
+        a.dout[vb + r1] = double(acc1);
+        // the forward slots, polled by row-slab items of other launches
+        a.y[vb + r0] = __longlong_as_double((long long)TRSV_PENDING);
+        a.y[vb + r1] = __longlong_as_double((long long)TRSV_PENDING);
+      }
+      consumers_sync();  // x_I visible to the next rows
+    }
+  }
+}
+
+template <class T, class A, bool FWD, bool WHOLE>
 __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
-  using PL = Plan<(int)sizeof(T)>;
+  using PL = Plan<(int)sizeof(T), WHOLE>;
   extern __shared__ __align__(128) unsigned char dsm_trsv[];
   RowSmem sm;
   sm.ring = dsm_trsv;
@@ -362,6 +662,13 @@ __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
   const TrsvWork wk = a.work[t];
   const MatDesc md = a.md[wk.mat];
   if (a.sc && a.sc[md.sub].done) return;
+  if (wk.row < 0) {
+    if constexpr (WHOLE)
+      sweep_matrix<T, A, FWD, PL::RING>(a, reinterpret_cast<const T*>(a.ltiles),
+                                        reinterpret_cast<const T*>(a.lut), wk.mat, sm,
+                                        reinterpret_cast<double*>(dsm_trsv + PL::BYTES));
+    return;
+  }
   if (md.coarse) {
     // a full-row FP64 coarse item needs a 32 KB stage: FP64 launches only (host checks)
     bool done = false;
@@ -403,9 +710,16 @@ void launch_fill_pending(double* p, long long n, cudaStream_t s) {
 
 template <class T, class A, bool FWD>
 static void launch_k(const TrsvArgs& a, cudaStream_t s, int grid = 0) {
-  constexpr int bytes = Plan<(int)sizeof(T)>::BYTES;
-  cudaFuncSetAttribute(k_trsv<T, A, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  k_trsv<T, A, FWD><<<grid > 0 ? grid : a.nwork, NTHR, bytes, s>>>(a);
+  const int nblk = grid > 0 ? grid : a.nwork;
+  if (a.zv_doubles > 0) {
+    const int bytes = Plan<(int)sizeof(T), true>::BYTES + a.zv_doubles * (int)sizeof(double);
+    cudaFuncSetAttribute(k_trsv<T, A, FWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    k_trsv<T, A, FWD, true><<<nblk, NTHR, bytes, s>>>(a);
+  } else {
+    constexpr int bytes = Plan<(int)sizeof(T)>::BYTES;
+    cudaFuncSetAttribute(k_trsv<T, A, FWD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    k_trsv<T, A, FWD, false><<<nblk, NTHR, bytes, s>>>(a);
+  }
 }
 
 void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s, int grid) {
