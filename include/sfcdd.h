@@ -77,7 +77,7 @@ typedef struct {
                            matrices of at most 192 tile rows, INVALID_ARG otherwise).
                            0 (default): -1 where the local matrices allow it, else 1.
                            sfcdd_autotune picks it by measurement. */
-  int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 4.
+  int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 2.
                            FP32 / BF16 local factors require 2 or 4 (INVALID_ARG otherwise). */
   int tensor_cores;     /* the panel and trailing-update tile products of the local and coarse
                            factorizations on the tensor cores (tcgen05) when 1 or -1 (default),
@@ -86,6 +86,11 @@ typedef struct {
                            factors: exact 8-bit digit slices of each row (Ozaki, Ogita, Oishi
                            and Rump's error-free splitting) multiplied as bf16 with exact FP32
                            accumulation, combined in integers and rounded once to FP64. */
+  int coarse_block;     /* tiles per unit diagonal block of the coarse substitution form
+                           (L = Lh blockdiag(D_J), Sec. 3.1 solves): 1, 2, 4 or 8; 0 (default)
+                           = 4.  Larger blocks shorten the coarse substitutions' dependency
+                           chain (nt0 / coarse_block steps) at the price of inverting larger
+                           diagonal blocks in the setup. */
 } sfcdd_options;
 
 typedef struct {
@@ -201,7 +206,8 @@ int sfcdd_solve_homogeneous(sfcdd_handle* h, const double* x0_dev, double* u_dev
  * the offsets returned by sfcdd_batch_offsets (nsub + 1 entries, last = total).
  * Supported options: precision, weighting, q (<= 0: per-subgrid rule), flexible,
  * coeffs (shared), stream, slabs_local / slabs_coarse (defaults 1 and 1 for FP64,
- * 1 and 4 otherwise), tensor_cores, variant SFCDD_ADDITIVE or SFCDD_BALANCED
+ * 1 and 4 otherwise; slabs_local -1: one CTA per local matrix), tensor_cores,
+ * variant SFCDD_ADDITIVE or SFCDD_BALANCED
  * (eq. balSW: two coarse solves and one local solve per apply; else UNSUPPORTED).
  * At most 65535 subgrids (UNSUPPORTED beyond); any number of local matrices.
  * Errors as sfcdd_setup_ex / sfcdd_solve; per_sub (nsub entries) and total may

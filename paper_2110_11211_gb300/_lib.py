@@ -46,7 +46,8 @@ class Options(C.Structure):
     _fields_ = [("coeffs", C.POINTER(C.c_double)), ("q", C.c_int), ("variant", C.c_int),
                 ("weighting", C.c_int), ("precision", C.c_int), ("flexible", C.c_int),
                 ("stream", C.c_void_p), ("profile", C.c_int), ("local_order", C.c_int),
-                ("slabs_local", C.c_int), ("slabs_coarse", C.c_int), ("tensor_cores", C.c_int)]
+                ("slabs_local", C.c_int), ("slabs_coarse", C.c_int), ("tensor_cores", C.c_int),
+                ("coarse_block", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -763,7 +763,10 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   // rows are known
   h->auto_local = o.slabs_local == 0;
   h->nsub_local = o.slabs_local == 0 ? 1 : (o.slabs_local == -1 ? 0 : o.slabs_local);
-  h->nsub_coarse = o.slabs_coarse == 0 ? 4 : o.slabs_coarse;
+  h->nsub_coarse = o.slabs_coarse == 0 ? 2 : o.slabs_coarse;
+  h->cb_coarse = o.coarse_block == 0 ? 4 : o.coarse_block;
+  if (h->cb_coarse != 1 && h->cb_coarse != 2 && h->cb_coarse != 4 && h->cb_coarse != 8)
+    return SFCDD_ERR_INVALID_ARG;
   if (!valid_slabs(h->precision, h->nsub_local, h->nsub_coarse)) return SFCDD_ERR_INVALID_ARG;
   if (o.tensor_cores < -1 || o.tensor_cores > 1) return SFCDD_ERR_INVALID_ARG;
   h->tensor_cores = o.tensor_cores != 0;

@@ -447,6 +447,18 @@ __device__ __forceinline__ A sum8(A v) {
   return v;
 }
 
+// Both sums of (a0, a1) over the 8-lane group at once: the first exchange halves
+// the work (lanes with bit 2 clear keep a0, the others a1), three adds instead
+// of six.  Returns a0's total in lanes g < 4 and a1's in lanes g >= 4.
+template <class A>
+__device__ __forceinline__ A sum8_pair(A a0, A a1) {
+  const bool hi = (threadIdx.x & 4) != 0;
+  A v = (hi ? a1 : a0) + __shfl_xor_sync(0xffffffffu, hi ? a0 : a1, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
 template <class T, class A, bool FWD, int RING>
 __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const T* __restrict__ ut,
                              int m, const RowSmem& sm, double* __restrict__ zv) {
@@ -563,8 +575,13 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
           give();
         }
       }
-      acc0 = sum8(acc0);
-      acc1 = sum8(acc1);
+      if (nz > PR) {  // rows of both pieces: lane 0 gets acc0's total, lane 4 acc1's
+        const A tot = sum8_pair(acc0, acc1);
+        acc0 = __shfl_sync(0xffffffffu, tot, lane & ~7);
+        acc1 = __shfl_sync(0xffffffffu, tot, (lane & ~7) | 4);
+      } else {        // uniform over the CTA: the second piece is empty
+        acc0 = sum8(acc0);
+      }
       if (g == 0) {
         const double z0 = double(A(zv[r0]) - acc0), z1 = double(A(zv[r1]) - acc1);
         zv[r0] = z0;
@@ -619,18 +636,15 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
           give();
         }
       }
-      acc0 = sum8(acc0);
-      acc1 = sum8(acc1);
+      // lane g = 0 of the group writes row j (acc0's total), lane g = 4 row j + 32
+      const A tot = sum8_pair(acc0, acc1);
       consumers_sync();  // every read of z_I is done
-      if (g == 0) {
-        const int r0 = I * TILE + j, r1 = r0 + PR;
-        zv[r0] = double(acc0);
-        zv[r1] = double(acc1);
-        a.dout[vb + r0] = double(acc0);
-        a.dout[vb + r1] = double(acc1);
-        // the forward slots, polled by row-slab items of other launches
-        a.y[vb + r0] = __longlong_as_double((long long)TRSV_PENDING);
-        a.y[vb + r1] = __longlong_as_double((long long)TRSV_PENDING);
+      if ((g & 3) == 0) {
+        const int row = I * TILE + j + (g ? PR : 0);
+        zv[row] = double(tot);
+        a.dout[vb + row] = double(tot);
+        // the forward slot, polled by row-slab items of other launches
+        a.y[vb + row] = __longlong_as_double((long long)TRSV_PENDING);
       }
       consumers_sync();  // x_I visible to the next rows
     }

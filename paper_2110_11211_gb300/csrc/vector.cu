@@ -6,16 +6,29 @@
 // Reductions are deterministic: a fixed grid (a function of N only) assigns
 // every element to one block, each block writes its partial, and the last
 // block to arrive sums the partials in block order and updates the scalars.
+// FP64 adds issue at 1/64 of the FP32 rate on this GPU, so the shuffle trees of
+// the reductions cost as much as the element arithmetic unless every thread
+// first accumulates several elements: kernels that reduce run on at most two
+// blocks per SM (about four elements per thread).
 #include "device_common.cuh"
 
 namespace sfcdd {
 
 constexpr int VB = 256;                 // threads per block of vector kernels
 constexpr int VMAXBLOCKS = 152 * 8;     // grid cap (8 blocks per SM)
+constexpr int RMAXBLOCKS = 152 * 2;     // grid cap of kernels that reduce
+constexpr int RPER = 4;                 // elements per thread they aim for
 
 int vec_blocks(int n) {
   int b = (n + VB - 1) / VB;
   if (b > VMAXBLOCKS) b = VMAXBLOCKS;
+  if (b < 1) b = 1;
+  return b;
+}
+
+int red_blocks(int n) {
+  int b = (n + VB * RPER - 1) / (VB * RPER);
+  if (b > RMAXBLOCKS) b = RMAXBLOCKS;
   if (b < 1) b = 1;
   return b;
 }
@@ -28,23 +41,53 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Block-reduce K values, store the block partial, and let the last block call
 // fin(totals).  Must be reached by every thread of every block of the grid.
+// K <= 2 (the PCG reductions): with two values the first warp exchange halves
+// the work (lanes 0-15 keep value 0, lanes 16-31 value 1), so a warp pays five
+// FP64 adds instead of ten; the eight warp partials of both values then go
+// through one three-level tree (value k of warp u in lane 8 k + u).
 template <int K, class Fin>
 __device__ __forceinline__ void reduce_finalize(double (&v)[K], ReduceWs ws, Fin fin) {
-  __shared__ double sh[K][VB / 32];
+  constexpr int NW = VB / 32;
+  static_assert(NW == 8, "eight warps per block");
+  __shared__ double sh[K][NW];
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if constexpr (K <= 2) {
+    double t;
+    int o = 16;
+    if constexpr (K == 2) {
+      const bool hi = (lane & 16) != 0;
+      const double keep = hi ? v[1] : v[0], send = hi ? v[0] : v[1];
+      t = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      o = 8;
+    } else {
+      t = v[0];
+    }
+    for (; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((lane & 15) == 0 && (lane >> 4) < K) sh[lane >> 4][w] = t;
+  } else {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double s = warp_sum(v[k]);
-    if (lane == 0) sh[k][w] = s;
+    for (int k = 0; k < K; ++k) {
+      const double s = warp_sum(v[k]);
+      if (lane == 0) sh[k][w] = s;
+    }
   }
   __syncthreads();
   if (w == 0) {
+    if constexpr (K <= 2) {
+      const int k = lane >> 3, u = lane & 7;
+      double s = k < K ? sh[k][u] : 0.0;
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (u == 0 && k < K) ws.partial[blockIdx.x * K + k] = s;
+    } else {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = lane < VB / 32 ? sh[k][lane] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0) ws.partial[blockIdx.x * K + k] = s;
+      for (int k = 0; k < K; ++k) {
+        double s = lane < NW ? sh[k][lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) ws.partial[blockIdx.x * K + k] = s;
+      }
     }
     if (lane == 0) {
       __threadfence();
@@ -86,6 +129,7 @@ __global__ void __launch_bounds__(VB) k_stencil(GridDev g, const unsigned* __res
   if ((MODE == 1 || ((MODE == 0 || MODE == 3) && sc)) && sc->done) return;
   double acc = 0.0;
   const int stride = gridDim.x * VB;
+#pragma unroll 4
   for (int p = blockIdx.x * VB + threadIdx.x; p < g.N; p += stride) {
     double xc;
     double v = stencil_point<D>(g, code, invpad, x, p, xc);
@@ -118,7 +162,7 @@ template <int MODE>
 static void stencil_dispatch(const GridDev& g, const unsigned* code, const int* invpad,
                              const double* x, double* y, const double* b, PcgScalars* sc,
                              ReduceWs ws, cudaStream_t s) {
-  const int nb = vec_blocks(g.N);
+  const int nb = (MODE == 1 || MODE == 2) ? red_blocks(g.N) : vec_blocks(g.N);
   switch (g.d) {
     case 1: k_stencil<1, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
     case 2: k_stencil<2, MODE><<<nb, VB, 0, s>>>(g, code, invpad, x, y, b, sc, ws); break;
@@ -161,6 +205,7 @@ __global__ void __launch_bounds__(VB) k_update_xr(int n, double* __restrict__ x,
   const double alpha = sc->alpha;
   double acc[2] = {0.0, 0.0};
   const int stride = gridDim.x * VB;
+#pragma unroll 4
   for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) {
     const double xi = x[i] + alpha * p[i];
     x[i] = xi;
@@ -186,7 +231,7 @@ __global__ void __launch_bounds__(VB) k_update_xr(int n, double* __restrict__ x,
 
 void launch_update_xr(int n, double* x, double* r, const double* p, const double* q,
                       PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
-  k_update_xr<<<vec_blocks(n), VB, 0, s>>>(n, x, r, p, q, sc, ws);
+  k_update_xr<<<red_blocks(n), VB, 0, s>>>(n, x, r, p, q, sc, ws);
 }
 
 // Energy-norm protocol (f = 0): r = -A x is given; init = 1 resets the PCG
@@ -196,6 +241,7 @@ __global__ void __launch_bounds__(VB) k_energy(int n, const double* __restrict__
                                                ReduceWs ws, double rtol, int flexible, int init) {
   double acc = 0.0;
   const int stride = gridDim.x * VB;
+#pragma unroll 4
   for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) acc += x[i] * r[i];
   double vv[1] = {acc};
   reduce_finalize<1>(vv, ws, [&](double* t) {
@@ -229,32 +275,39 @@ __global__ void __launch_bounds__(VB) k_energy(int n, const double* __restrict__
 
 void launch_energy(int n, const double* x, const double* r, PcgScalars* sc, ReduceWs ws,
                    double rtol, int flexible, int init, cudaStream_t s) {
-  k_energy<<<vec_blocks(n), VB, 0, s>>>(n, x, r, sc, ws, rtol, flexible, init);
+  k_energy<<<red_blocks(n), VB, 0, s>>>(n, x, r, sc, ws, rtol, flexible, init);
 }
 
 // ---------------------------------------------------------------------------
-// Coarse right-hand side g0 = R_0 r (eq. restr): one warp per coarse block.
+// Coarse right-hand side g0 = R_0 r (eq. restr): eight lanes per coarse block
+// (blocks hold N / (q P) points, a few dozen at the paper's q), summed by a
+// fixed three-level tree.
+constexpr int RL = 8;
 __global__ void k_restrict(PartDev pd, const double* __restrict__ r, double* __restrict__ g0,
                            const PcgScalars* sc) {
   if (sc && sc->done) return;
-  const int lane = threadIdx.x & 31;
-  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int l = threadIdx.x & (RL - 1);
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) / RL;
   const int N0 = pd.q * pd.P;
-  if (a >= N0) return;
-  const int t = a / pd.q, m = a % pd.q;
-  const int n = tilde_size(pd, t);
-  const int bf = n / pd.q, br = n % pd.q;
-  const int start = tilde_off(pd, t) + (m < br ? m * (bf + 1) : br * (bf + 1) + (m - br) * bf);
-  const int size = m < br ? bf + 1 : bf;
+  const bool valid = a < N0;  // partial warps stay for the shuffles
   double s = 0.0;
-  for (int k = lane; k < size; k += 32) s += r[start + k];
-  s = warp_sum(s);
-  if (lane == 0) g0[a] = s;
+  if (valid) {
+    const int t = a / pd.q, m = a % pd.q;
+    const int n = tilde_size(pd, t);
+    const int bf = n / pd.q, br = n % pd.q;
+    const int start = tilde_off(pd, t) + (m < br ? m * (bf + 1) : br * (bf + 1) + (m - br) * bf);
+    const int size = m < br ? bf + 1 : bf;
+    for (int k = l; k < size; k += RL) s += r[start + k];
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (valid && l == 0) g0[a] = s;
 }
 
 void launch_restrict(const PartDev& pd, const double* r, double* g0, const PcgScalars* sc,
                      cudaStream_t s) {
-  const long long threads = (long long)pd.q * pd.P * 32;
+  const long long threads = (long long)pd.q * pd.P * RL;
   k_restrict<<<(unsigned)((threads + VB - 1) / VB), VB, 0, s>>>(pd, r, g0, sc);
 }
 
@@ -309,6 +362,8 @@ void launch_prolong(const PartDev& pd, const TileSetDev& ts, int mode, const dou
                     const double* r, double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s,
                     bool dot) {
   if (sc && dot)
+    // one point per thread: its gathers are dependent loads, which more points per
+    // thread would serialize
     k_prolong<true><<<vec_blocks(pd.N), VB, 0, s>>>(pd, ts, mode, dvec, r, z, sc, ws);
   else
     k_prolong<false><<<vec_blocks(pd.N), VB, 0, s>>>(pd, ts, mode, dvec, r, z, sc, ws);
@@ -327,6 +382,7 @@ __global__ void __launch_bounds__(VB) k_combine_bal(int n, const double* __restr
   if (DOT && sc->done) return;
   double acc[2] = {0.0, 0.0};
   const int stride = gridDim.x * VB;
+#pragma unroll 4
   for (int p = blockIdx.x * VB + threadIdx.x; p < n; p += stride) {
     const double zp = (t[p] - v[p]) + w[p];
     if (DOT) {
@@ -342,7 +398,7 @@ __global__ void __launch_bounds__(VB) k_combine_bal(int n, const double* __restr
 void launch_combine_bal(int n, const double* t, const double* v, const double* w, const double* r,
                         double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s) {
   if (sc)
-    k_combine_bal<true><<<vec_blocks(n), VB, 0, s>>>(n, t, v, w, r, z, sc, ws);
+    k_combine_bal<true><<<red_blocks(n), VB, 0, s>>>(n, t, v, w, r, z, sc, ws);
   else
     k_combine_bal<false><<<vec_blocks(n), VB, 0, s>>>(n, t, v, w, r, z, sc, ws);
 }
@@ -367,6 +423,7 @@ __global__ void __launch_bounds__(VB) k_init_pcg(int n, const double* __restrict
                                                  int flexible) {
   double acc = 0.0;
   const int stride = gridDim.x * VB;
+#pragma unroll 4
   for (int i = blockIdx.x * VB + threadIdx.x; i < n; i += stride) {
     const double bi = b[i];
     x[i] = 0.0;
@@ -398,7 +455,7 @@ __global__ void __launch_bounds__(VB) k_init_pcg(int n, const double* __restrict
 
 void launch_init_pcg(int n, const double* b, double* x, double* r, PcgScalars* sc, ReduceWs ws,
                      double rtol, int flexible, cudaStream_t s) {
-  k_init_pcg<<<vec_blocks(n), VB, 0, s>>>(n, b, x, r, sc, ws, rtol, flexible);
+  k_init_pcg<<<red_blocks(n), VB, 0, s>>>(n, b, x, r, sc, ws, rtol, flexible);
 }
 
 __global__ void k_axpby(int n, double a, const double* __restrict__ x, double b,

@@ -24,7 +24,7 @@ class Solver:
     def __init__(self, levels, P, overlap, *, precision="fp64", variant="additive",
                  weighting="omega", q=0, coeffs=None, flexible=-1, stream=None,
                  profile=False, local_order="lex", slabs_local=0, slabs_coarse=0,
-                 tensor_cores=-1):
+                 tensor_cores=-1, coarse_block=0):
         L = _lib.lib()
         self.levels = tuple(int(l) for l in levels)
         self.d = len(self.levels)
@@ -48,6 +48,7 @@ class Solver:
         opt.slabs_local = int(slabs_local)
         opt.slabs_coarse = int(slabs_coarse)
         opt.tensor_cores = int(tensor_cores)
+        opt.coarse_block = int(coarse_block)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

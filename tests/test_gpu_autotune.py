@@ -145,3 +145,22 @@ def test_whole_matrix_batch():
     for variant in ("additive", "balanced"):
         a, w = sol[1, variant], sol[-1, variant]
         assert float(torch.linalg.norm(w - a) / torch.linalg.norm(a)) <= 1e-8
+
+
+def test_coarse_block_sizes_vs_oracle():
+    """The coarse substitution form L = Lh blockdiag(D_J) with 1-, 2-, 4- and
+    8-tile diagonal blocks: the same A_0^{-1}, so the apply meets the FP64 bar."""
+    from oracle import schwarz
+    from paper_2110_11211_gb300._lib import SfcddError
+    from paper_2110_11211_gb300.solver import Solver
+    levels, P, gamma = (9, 5, 3), 64, 1.0   # N_0 = 4096: 64 coarse tile rows
+    S = schwarz.Schwarz(levels, P, gamma)
+    g = inputs.uniform(67, S.N)
+    ref = S.coarse_correction(g)
+    for cb in (1, 2, 4, 8):
+        with Solver(levels, P, gamma, variant="coarse_only", coarse_block=cb) as s:
+            z = s.apply_precond(torch.tensor(g, device="cuda")).cpu().numpy()
+        assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref), cb
+    for cb in (3, 16, -1):
+        with pytest.raises(SfcddError):
+            Solver((6, 4), 8, 0.5, coarse_block=cb)
