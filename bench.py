@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4, help="local subdomains the oracle factors")
     ap.add_argument("--levels", default=None, help="custom grid levels, e.g. 8,5,3 (profiling runs)")
+    ap.add_argument("--shapes", default=None,
+                    help="substitution shapes slabs_local,slabs_coarse instead of autotuning "
+                         "(profiling runs: the timings under a profiler mislead the tuner)")
     ap.add_argument("--P", type=int, default=None, help="custom subdomain count")
     ap.add_argument("--gamma", type=float, default=None, help="custom overlap")
     ap.add_argument("--stencil-levels", default=None,
@@ -247,19 +250,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def recorded_traffic(kernel, workload, precision):
-    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
-    record, or None when there is none for this workload or the kernel source
-    changed since the counters were taken."""
+# source files whose kernels make up each class with a committed DRAM record
+TRAFFIC_SOURCES = {
+    "trsv_fwd": ["trsv.cu"],
+    "trsv_bwd": ["trsv.cu"],
+    "coarse_factor": ["factor.cu", "oz_tile.cuh"],
+}
+
+
+def traffic_sources_sha(kernel):
     import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2110_11211_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, workload, precision, shapes=None):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    record, or None when there is none for this workload, precision and
+    substitution shapes, or the kernels' source changed since the counters were
+    taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh).get(kernel)
-        with open(os.path.join(ROOT, "paper_2110_11211_gb300", "csrc", "trsv.cu"), "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
+        sha = traffic_sources_sha(kernel) if kernel in TRAFFIC_SOURCES else None
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("workload") != workload or rec.get("precision") != precision:
+    if not rec or sha is None or rec.get("workload") != workload or rec.get("precision") != precision:
+        return None
+    if "substitution_slabs" in rec and shapes is not None and rec["substitution_slabs"] != shapes:
         return None
     if rec.get("kernel_source_sha256") != sha:
         return None
@@ -281,9 +302,13 @@ def run_ours(args):
 
     # substitution tile shapes: tuned once (sfcdd_autotune) before the warm-up,
     # then passed to every step's setup like any other option
-    with Solver(levels, P, gamma, precision=prec, coeffs=coeffs) as s:
-        tuning = s.autotune(reps=5)
-    shapes = dict(slabs_local=tuning["slabs_local"], slabs_coarse=tuning["slabs_coarse"])
+    if args.shapes:
+        sl, sc = (int(v) for v in args.shapes.split(","))
+        shapes = dict(slabs_local=sl, slabs_coarse=sc)
+    else:
+        with Solver(levels, P, gamma, precision=prec, coeffs=coeffs) as s:
+            tuning = s.autotune(reps=5)
+        shapes = dict(slabs_local=tuning["slabs_local"], slabs_coarse=tuning["slabs_coarse"])
 
     def step(profile):
         s = Solver(levels, P, gamma, precision=prec, coeffs=coeffs, profile=profile, **shapes)
@@ -433,7 +458,8 @@ def run_ours(args):
                 "unit": "TFLOP/s"}
     roof.update({"kernel": dom, "achieved": round(achieved, 3),
                  "frac": round(achieved / roof["peak"], 4),
-                 "traffic": recorded_traffic(dom, args.workload if not args.levels else "custom", prec),
+                 "traffic": recorded_traffic(dom, args.workload if not args.levels else "custom", prec,
+                                             shapes),
                  "work_per_launch": per_launch, "avg_launch_ms": round(dom_ms / dom_n, 4),
                  "peak_source": peak_src if roof["bound"] == "hbm" else "nominal (unit counts x clock)",
                  "timing": f"CUDA events around every launch over {prof_steps} profiled steps"})
@@ -444,7 +470,9 @@ def run_ours(args):
             ms, n = timed[k]
             gbs = work[k] / (ms / n * 1e-3) / 1e9
             trsv[k] = {"GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
-                       "bytes_per_launch": work[k], "avg_launch_ms": round(ms / n, 4)}
+                       "bytes_per_launch": work[k], "avg_launch_ms": round(ms / n, 4),
+                       "traffic": recorded_traffic(k, args.workload if not args.levels else "custom",
+                                                   prec, shapes)}
             if prec == "fp64":
                 tf = 2.0 * work[k] / 8.0 / (ms / n * 1e-3) / 1e12
                 trsv[k].update({"fp64_TFLOPs": round(tf, 3), "frac_fp64": round(tf / FP64_PEAK_TFLOPS, 4)})
