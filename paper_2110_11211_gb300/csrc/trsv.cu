@@ -26,10 +26,12 @@
 // a sentinel NaN bit pattern, every slot is written exactly once per launch
 // with a relaxed store, and a consumer polls the slots it needs with relaxed
 // loads until none holds the sentinel (bounded spin; a timeout sets the error
-// word and the CTA still drains its copies before it returns).  Only consumer
-// warp 0 polls; it hands the 64 values of each dependency to the other warps
-// through shared memory and a per-stage mbarrier, so one straggling lane
-// cannot hold up eight warps and the L2 sees one poller per CTA.  The forward
+// word and the CTA still drains its copies before it returns).  One polling
+// warp, which does no arithmetic, waits for the 64 values of each dependency
+// and hands them to the eight consumer warps through shared memory and a
+// per-stage mbarrier: one straggling lane cannot hold up eight warps, the L2
+// sees one poller per CTA, and the poller runs ahead of the consumers, so its
+// round trips to L2 overlap their GEMVs on the previous tiles.  The forward
 // launch resets the backward slots of its slab and also writes its results to
 // a plain buffer zc; the backward launch reads z from zc and resets the forward
 // slots of its slab (nothing reads them during the backward launch).
@@ -46,7 +48,8 @@
 namespace sfcdd {
 
 constexpr int NCONS = 256;                 // consumer threads: 8 warps
-constexpr int NTHR = NCONS + 32;           // + one producer warp
+constexpr int PROD0 = NCONS + 32;          // + one polling warp, then the producer warp
+constexpr int NTHR = PROD0 + 32;
 constexpr int MAXST = 8;
 constexpr long long SPIN_LIMIT = 1ll << 22;
 constexpr long long MBAR_LIMIT = 1ll << 26;
@@ -251,10 +254,17 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
   auto half_tile = [&](int t) {
     return !FWD && t >= nE && a.ts.nzr != nullptr && a.ts.nzr[fb + cl[ncl - 1 - (t - nE)]] <= TILE / 2;
   };
-  if (threadIdx.x >= NCONS) {
+  // dependency vector of tile tt: z of the block comes from the forward launch
+  // (a previous kernel, never the sentinel), the other vectors from this launch
+  auto dep = [&](int tt) -> const double* {
+    return FWD       ? a.y + vb + (k0 + tt) * TILE
+           : tt < nE ? a.zc + vb + (blk0 + tt) * TILE
+                     : a.dout + vb + cl[ncl - 1 - (tt - nE)] * TILE;
+  };
+  if (threadIdx.x >= PROD0) {
     // producer warp: every lane waits for the stage; lane 0 (or, for half
     // tiles, the lanes row by row) issues the copies
-    const int pl = threadIdx.x - NCONS;
+    const int pl = threadIdx.x - PROD0;
     for (int t = 0; t < ntile; ++t) {
       const int s = t % NS, k = t / NS;
       if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 10);
@@ -286,6 +296,25 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
         for (int j = pl; j < R; j += 32)
           bulk_copy(dst + (size_t)j * TILE * sizeof(T), src + (long long)j * TILE, HB, &sm.full[s]);
       }
+    }
+    return;
+  }
+  if (threadIdx.x >= NCONS) {
+    // polling warp: waits for each tile's dependency values and hands them to
+    // the consumers through shared memory, running ahead of them by up to NS
+    // tiles, so that its round trips to L2 overlap their GEMVs
+    const int pln = threadIdx.x & 31;
+    for (int t = 0; t < ntile; ++t) {
+      const int s = t % NS;
+      double* zs = sm.zbuf + s * TILE;
+      // the consumers are done with the previous use of zs (stage s)
+      if (t >= NS) mbar_wait(&sm.empty[s], ((t / NS) & 1) ^ 1, a.err, 13);
+      if (!half_tile(t) || pln < TILE / 4) {
+        const double2 v = wait_pair(dep(t) + 2 * pln, a.err, FWD ? 1 : 2);
+        *reinterpret_cast<double2*>(zs + 2 * pln) = v;
+      }
+      __syncwarp();
+      if (pln == 0) mbar_arrive(&sm.zbar[s]);
     }
     return;
   }
@@ -324,32 +353,14 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
     if (threadIdx.x < R)
       a.y[vb + rbase + threadIdx.x] = __longlong_as_double((long long)TRSV_PENDING);
   }
-  // dependency vector of tile tt: z of the block comes from the forward launch
-  // (a previous kernel, never the sentinel), the other vectors from this launch
-  auto dep = [&](int tt) -> const double* {
-    return FWD       ? a.y + vb + (k0 + tt) * TILE
-           : tt < nE ? a.zc + vb + (blk0 + tt) * TILE
-                     : a.dout + vb + cl[ncl - 1 - (tt - nE)] * TILE;
-  };
   for (int t = 0; t < ntile; ++t) {
     const int s = t % NS;
     const unsigned ph = (t / NS) & 1;
     double* zs = sm.zbuf + s * TILE;
     const bool half = half_tile(t);
     double2 v = make_double2(0.0, 0.0);
-    if (w == 0) {
-      // every warp is done with the previous use of stage s (and of zs)
-      if (t >= NS) mbar_wait(&sm.empty[s], ph ^ 1, a.err, 13);
-      if (!half || lane < TILE / 4) {
-        v = wait_pair(dep(t) + 2 * lane, a.err, FWD ? 1 : 2);
-        *reinterpret_cast<double2*>(zs + 2 * lane) = v;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.zbar[s]);
-    } else {
-      mbar_wait(&sm.zbar[s], ph, a.err, 14);
-      if (!half) v = *reinterpret_cast<const double2*>(zs + 2 * lane);
-    }
+    mbar_wait(&sm.zbar[s], ph, a.err, 14);
+    if (!half) v = *reinterpret_cast<const double2*>(zs + 2 * lane);
     mbar_wait(&sm.full[s], ph, a.err, 11);
     const T* st = reinterpret_cast<const T*>(sm.ring + (size_t)s * SB);
     if (half) {
@@ -475,9 +486,10 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
   const int nt = a.ts.nt[m];
   auto half_piece = [&](int K) { return sizeof(T) == 8 && a.ts.nzr[fb + K] <= TILE / 2; };
 
-  if (threadIdx.x >= NCONS) {
+  if (threadIdx.x >= NCONS && threadIdx.x < PROD0) return;  // no polling: the chain is in the CTA
+  if (threadIdx.x >= PROD0) {
     // producer warp: the pieces in consumption order
-    const int pl = threadIdx.x - NCONS;
+    const int pl = threadIdx.x - PROD0;
     int t = 0;
     auto put = [&](const T* src, unsigned bytes, bool half) {
       const int s = t % NS, k = t / NS;
