@@ -374,17 +374,24 @@ def run_ours(args):
 
     # mixed-precision variants of the same workload, and the balanced operator
     variants = {}
+    bal_shapes = {}
     if not args.no_variants and rank == 0:
         for vp, var in (("fp32", "additive"), ("bf16", "additive"), (prec, "balanced")):
             if vp == prec and var == "additive":
                 continue
+            # each variant with its own tuned substitution shapes, like the main arm
+            with Solver(levels, P, gamma, precision=vp, coeffs=coeffs, variant=var) as s:
+                vt = s.autotune(reps=3)
+            vshapes = dict(slabs_local=vt["slabs_local"], slabs_coarse=vt["slabs_coarse"])
+            if var == "balanced":
+                bal_shapes = vshapes
             times = []
             for k in range(3):
                 torch.cuda.synchronize()
                 a0 = torch.cuda.Event(enable_timing=True)
                 a1 = torch.cuda.Event(enable_timing=True)
                 a0.record(stream)
-                s = Solver(levels, P, gamma, precision=vp, coeffs=coeffs, variant=var)
+                s = Solver(levels, P, gamma, precision=vp, coeffs=coeffs, variant=var, **vshapes)
                 uv, stv = s.solve(f, rtol=args.rtol)
                 s.close()
                 a1.record(stream)
@@ -396,11 +403,12 @@ def run_ours(args):
             variants[key] = {"ms": round(statistics.mean(times), 2), "iters": stv.iters,
                             "setup_ms": round(stv.setup_ms, 2), "solve_ms": round(stv.solve_ms, 2),
                             "applies_per_s": round(stv.iters / (stv.solve_ms / 1e3), 1),
-                            "rel_diff_vs_fp64_solution": err, "true_rel_res": stv.true_rel_res}
+                            "rel_diff_vs_fp64_solution": err, "true_rel_res": stv.true_rel_res,
+                            "substitution_slabs": vshapes}
 
     # Algorithm 3 with the balanced operator, damping from the Lanczos estimate
     if not args.no_variants and rank == 0:
-        s = Solver(levels, P, gamma, precision=prec, coeffs=coeffs, variant="balanced")
+        s = Solver(levels, P, gamma, precision=prec, coeffs=coeffs, variant="balanced", **bal_shapes)
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
