@@ -73,8 +73,10 @@ typedef struct {
                            64-row tile row (rows of 64, 32, 16), one CTA each, chained through
                            result slots in L2; splitting shortens the GEMV on the dependency
                            chain from one tile row to the next.  -1: one CTA per local matrix
-                           sweeping all its tile rows, chained through shared memory (local
-                           matrices of at most 192 tile rows, INVALID_ARG otherwise).
+                           sweeping all its tile rows, chained through shared memory (the
+                           matrix vector must fit beside the stream ring: local matrices of
+                           at most 189 tile rows with FP64 factors, 317 with FP32, 380 with
+                           BF16; INVALID_ARG otherwise).
                            0 (default): -1 where the local matrices allow it, else 1.
                            sfcdd_autotune picks it by measurement. */
   int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 2.

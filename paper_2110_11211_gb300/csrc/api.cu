@@ -317,9 +317,6 @@ void build_skyline(const std::vector<int>& nt, const std::vector<int>& vbase,
   }
 }
 
-// Whole-matrix sweeps keep a local matrix's vector in shared memory.
-bool whole_fits(int max_nt) { return max_nt > 0 && max_nt * TILE * (int)sizeof(double) <= WHOLE_ZV_BYTES; }
-
 }  // namespace sfcdd
 
 struct sfcdd_handle {
@@ -644,7 +641,7 @@ void enqueue_iteration(sfcdd_handle* h, Prof& pf) {
 int configure_substitution(sfcdd_handle* h, int nsub_local, int nsub_coarse) {
   const int P = h->P;
   cudaStream_t s = h->stream;
-  if (nsub_local == 0 && (!whole_fits(h->max_nt) || !h->d_nzr)) return SFCDD_ERR_INVALID_ARG;
+  if (nsub_local == 0 && (!whole_fits(h->st, h->max_nt) || !h->d_nzr)) return SFCDD_ERR_INVALID_ARG;
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
   if (h->iter_graph) {
     cudaGraphExecDestroy(h->iter_graph);
@@ -1099,7 +1096,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   cudaEventDestroy(ev_coarse);
   SFCDD_CUDA_OK(cudaGetLastError());
 
-  if (h->auto_local && h->variant != SFCDD_COARSE_ONLY && whole_fits(h->max_nt)) h->nsub_local = 0;
+  if (h->auto_local && h->variant != SFCDD_COARSE_ONLY && whole_fits(h->st, h->max_nt))
+    h->nsub_local = 0;
   TRY(configure_substitution(h, h->nsub_local, h->nsub_coarse));
   if (h->variant == SFCDD_BALANCED)
     for (int k = 0; k < 4; ++k) TRY(dalloc(h, &h->bal[k], N));
@@ -1627,7 +1625,7 @@ int sfcdd_autotune(sfcdd_handle* h, int reps, sfcdd_tuning* out) {
     for (int ic = 0; ic < 3 && rc == SFCDD_OK; ++ic) {
       const int sl = opts[il], sc = opts[ic];
       if (!valid_slabs(h->precision, sl, sc)) continue;
-      if (sl == 0 && (!whole_fits(h->max_nt) || h->variant == SFCDD_COARSE_ONLY)) continue;
+      if (sl == 0 && (!whole_fits(h->st, h->max_nt) || h->variant == SFCDD_COARSE_ONLY)) continue;
       rc = configure_substitution(h, sl, sc);
       if (rc != SFCDD_OK) break;
       Prof pf(h, s);

@@ -125,7 +125,7 @@ void bfree(sfcdd_batch* b, void* p) {
 // slab) items for the given slab counts; drops the captured solve graph.
 int batch_configure(sfcdd_batch* b, int nsub_local, int nsub_coarse) {
   cudaStream_t s = b->stream;
-  if (nsub_local == 0 && !whole_fits(b->max_nt_local)) return SFCDD_ERR_INVALID_ARG;
+  if (nsub_local == 0 && !whole_fits(b->st, b->max_nt_local)) return SFCDD_ERR_INVALID_ARG;
   SFCDD_CUDA_OK(cudaStreamSynchronize(s));
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
@@ -1277,7 +1277,7 @@ int sfcdd_batch_autotune(sfcdd_batch* b, int reps, sfcdd_tuning* out) {
     for (int ic = 0; ic < 3 && rc == SFCDD_OK; ++ic) {
       const int sl = opts[il], sc = opts[ic];
       if (b->st != Store::F64 && sc == 1) continue;  // 64-row FP64 stage: FP64 launches only
-      if (sl == 0 && !whole_fits(b->max_nt_local)) continue;
+      if (sl == 0 && !whole_fits(b->st, b->max_nt_local)) continue;
       rc = batch_configure(b, sl, sc);
       if (rc != SFCDD_OK) break;
       for (int k = 0; k < 2; ++k) pair();

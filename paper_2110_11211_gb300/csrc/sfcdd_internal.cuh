@@ -414,10 +414,10 @@ struct MatDesc {
 // written in the current launch.
 constexpr unsigned long long TRSV_PENDING = 0x7FF4DEADBEEF0000ull;
 void launch_fill_pending(double* p, long long n, cudaStream_t s);
-// Largest shared-memory vector of a whole-matrix substitution item (a local
-// matrix of up to 192 tile rows).
-constexpr int WHOLE_ZV_BYTES = 96 * 1024;
-bool whole_fits(int max_nt);
+// Whether whole-matrix substitution items fit local matrices of up to max_nt
+// tile rows with factors stored as st: the matrix vector beside the launch's
+// ring must stay within a CTA's shared memory (227 KB).
+bool whole_fits(Store st, int max_nt);
 struct TrsvArgs {
   TileSetDev ts;
   const MatDesc* md;           // per matrix

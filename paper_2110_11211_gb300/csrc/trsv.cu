@@ -724,6 +724,22 @@ __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
   }
 }
 
+// Shared memory of a launch with whole-matrix items (largest local tile count
+// max_nt), and whether it fits a CTA.
+constexpr long long CTA_SMEM_MAX = 227 * 1024;
+template <int ES>
+static long long whole_bytes(int max_nt) {
+  return Plan<ES, true>::BYTES + (long long)max_nt * TILE * (long long)sizeof(double);
+}
+
+bool whole_fits(Store st, int max_nt) {
+  if (max_nt <= 0) return false;
+  const long long b = st == Store::F64 ? whole_bytes<8>(max_nt)
+                      : st == Store::F32 ? whole_bytes<4>(max_nt)
+                                         : whole_bytes<2>(max_nt);
+  return b <= CTA_SMEM_MAX;
+}
+
 __global__ void k_fill_pending(double* p, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)

@@ -164,3 +164,26 @@ def test_coarse_block_sizes_vs_oracle():
     for cb in (3, 16, -1):
         with pytest.raises(SfcddError):
             Solver((6, 4), 8, 0.5, coarse_block=cb)
+
+
+def test_whole_matrix_size_limit():
+    """Local matrices of about 217 tile rows (1023 x 31 x 7, P = 48, gamma = 1): the
+    FP64 matrix vector does not fit beside the ring (at most 189 tile rows), so
+    slabs_local = -1 is rejected and the default falls back to row slabs; FP32
+    factors (at most 317 tile rows) run whole-matrix items."""
+    from paper_2110_11211_gb300._lib import SfcddError
+    from paper_2110_11211_gb300.solver import Solver
+    levels, P, gamma = (10, 5, 3), 48, 1.0
+    g = torch.tensor(inputs.uniform(68, inputs.grid_size(levels)), device="cuda")
+    with pytest.raises(SfcddError):
+        Solver(levels, P, gamma, slabs_local=-1)
+    with Solver(levels, P, gamma) as s:
+        z_def = s.apply_precond(g)
+    with Solver(levels, P, gamma, slabs_local=1) as s:
+        z_one = s.apply_precond(g)
+    assert float(torch.linalg.norm(z_def - z_one) / torch.linalg.norm(z_one)) == 0.0
+    z = {}
+    for sl in (-1, 1):
+        with Solver(levels, P, gamma, precision="fp32", slabs_local=sl) as s:
+            z[sl] = s.apply_precond(g)
+    assert float(torch.linalg.norm(z[-1] - z[1]) / torch.linalg.norm(z[1])) <= 1e-4
