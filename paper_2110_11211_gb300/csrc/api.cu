@@ -777,7 +777,13 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->st = (Store)h->precision;
 
   SFCDD_CUDA_OK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  SFCDD_CUDA_OK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+  {
+    // the coarse factorization is a chain of 128 small steps that shares the GPU
+    // with the local factorization: its CTAs go first whenever an SM frees up
+    int lo = 0, hi = 0;
+    SFCDD_CUDA_OK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    SFCDD_CUDA_OK(cudaStreamCreateWithPriority(&h->side_stream, cudaStreamNonBlocking, hi));
+  }
   cudaEvent_t e0, e1;
   SFCDD_CUDA_OK(cudaEventCreate(&e0));
   SFCDD_CUDA_OK(cudaEventCreate(&e1));
