@@ -1098,10 +1098,11 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
     pf.run(SFCDD_K_TRSM, [&] {
       launch_offblock_rows(h->ts, 0, P, h->max_nt, h->ltiles, h->st, h->d_nzr, s);
     });
-  SFCDD_CUDA_OK(cudaStreamWaitEvent(s, ev_coarse, 0));
-  cudaEventDestroy(ev_coarse);
   SFCDD_CUDA_OK(cudaGetLastError());
 
+  // The host bookkeeping below (work lists, solve buffers) waits for the local
+  // work on s only; the coarse factorization, usually the longer of the two,
+  // keeps running on the side stream and is joined just before the end event.
   if (h->auto_local && h->variant != SFCDD_COARSE_ONLY && whole_fits(h->st, h->max_nt))
     h->nsub_local = 0;
   TRY(configure_substitution(h, h->nsub_local, h->nsub_coarse));
@@ -1132,6 +1133,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   TRY(dalloc(h, &h->ws.counter, 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->ws.counter, 0, sizeof(unsigned), s));
 
+  SFCDD_CUDA_OK(cudaStreamWaitEvent(s, ev_coarse, 0));
+  cudaEventDestroy(ev_coarse);
   SFCDD_CUDA_OK(cudaEventRecord(e1, s));
   SFCDD_CUDA_OK(cudaEventSynchronize(e1));
   pf.collect();
