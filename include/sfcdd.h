@@ -255,16 +255,18 @@ int sfcdd_apply_operator(sfcdd_handle* h, const double* x_dev, double* y_dev, in
  * curve_order as in sfcdd_apply_operator. */
 int sfcdd_apply_precond(sfcdd_handle* h, const double* g_dev, double* z_dev, int curve_order);
 
-/* Autotuner of the substitution tile shapes (the row slab a work item of the
- * batched triangular solves covers: 64, 32 or 16 rows, for the local and the
- * coarse factors).  Times `reps` preconditioner applies (device time, CUDA
- * events, after two warm-up applies) for every admissible (slabs_local,
+/* Autotuner of the substitution shapes (what a work item of the batched
+ * triangular solves covers: for the local factors a whole matrix, where its
+ * vector fits the shared memory, or a row slab of 64, 32 or 16 rows; for the
+ * coarse factor a row slab).  Times `reps` preconditioner applies (device time,
+ * CUDA events, after two warm-up applies) for every admissible (slabs_local,
  * slabs_coarse) pair, keeps the fastest in the handle and reports it.  The
- * preconditioner's values do not depend on the choice.  Drops the captured
- * iteration graph (rebuilt by the next solve).  Synchronises the stream.
+ * preconditioner's values do not depend on the choice beyond rounding (whole-
+ * matrix items sum each row in another order).  Drops the captured iteration
+ * graph (rebuilt by the next solve).  Synchronises the stream.
  * Errors: INVALID_ARG (reps < 1), TIMEOUT, CUDA. */
 typedef struct {
-  int slabs_local;      /* chosen slab count of the local substitutions */
+  int slabs_local;      /* chosen slab count of the local substitutions (-1: whole matrices) */
   int slabs_coarse;     /* chosen slab count of the coarse substitutions */
   double apply_ms;      /* mean device time of one apply with the choice */
   int candidates;       /* configurations timed */

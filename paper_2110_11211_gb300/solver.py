@@ -147,7 +147,8 @@ class Solver:
         return u, st
 
     def autotune(self, reps=5):
-        """Pick the substitution slab shapes by timing preconditioner applies."""
+        """Pick the substitution shapes (whole-matrix local items, slabs_local = -1,
+        or row slabs) by timing preconditioner applies."""
         t = Tuning()
         check("sfcdd_autotune", self._L.sfcdd_autotune(self._h, int(reps), C.byref(t)))
         return {"slabs_local": t.slabs_local, "slabs_coarse": t.slabs_coarse,
