@@ -15,10 +15,17 @@
 // array, where Lh is the identity).  Both sweeps stream contiguous row slabs;
 // all rows of a block depend only on earlier blocks, so the row-to-row chain
 // has nt / cb steps, each carrying the GEMVs with the previous block's tiles.
+// Zero rows: rows nzr[I].. of tile row I are zero in all its off-block Lh
+// tiles (the factor keeps the narrow local bands), so the forward neither
+// streams nor applies them, and the backward reads only the left halves of
+// transposed tiles whose source bound is at most 32.
 //
-// Parallel layout: one CTA per work item (matrix, tile row, slab), a slab
-// being R = 64 / S consecutive rows of the tile row (S = 1, 2 or 4 per matrix:
-// splitting the rows of a long chain spreads its FP64 GEMVs over S SMs).  CTAs
+// Parallel layout: one CTA per work item.  A local matrix is either one item
+// (the whole matrix, its tile rows chained through shared memory: see
+// sweep_matrix) or one item per (tile row, slab); coarse rows are always slab
+// items, in the same launch.  A slab is R = 64 / S consecutive rows of the tile
+// row (S = 1, 2 or 4 per matrix: splitting the rows of a long chain spreads its
+// FP64 GEMVs over S SMs).  CTAs
 // take tickets from a monotone counter and map them through a work list in
 // which every item comes after the items it depends on, so a CTA only ever
 // waits for CTAs that already started (no deadlock, whatever the residency).
@@ -39,10 +46,11 @@
 // Data movement: a producer warp streams the item's tile slabs (E tiles first
 // in the backward) from HBM into a shared-memory ring with bulk asynchronous
 // copies (cp.async.bulk, completion on mbarriers); eight consumer warps wait on
-// the ring's mbarriers, apply the slabs, and free the stages.  The ring holds
-// two tiles of the launch's local precision (FP64 64 KB, FP32 32 KB, BF16
-// 16 KB), so low-precision launches keep more CTAs resident; coarse items of
-// such launches run in 16-row slabs (8 KB stages).
+// the ring's mbarriers, apply the slabs, and free the stages.  In launches of
+// slab items only, the ring holds 32 KB (one FP64 tile, two FP32 tiles, two
+// BF16 tiles in 16 KB), so that four or more CTAs fit an SM; coarse items of
+// low-precision launches run in 16- or 32-row slabs.  Launches with whole-matrix
+// items use eight 32-row pieces (FP64 128 KB) and the matrix vector instead.
 #include "sfcdd_internal.cuh"
 
 namespace sfcdd {
