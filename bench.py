@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--levels", default=None, help="custom grid levels, e.g. 8,5,3 (profiling runs)")
     ap.add_argument("--shapes", default=None,
                     help="substitution shapes slabs_local,slabs_coarse instead of autotuning "
-                         "(profiling runs: the timings under a profiler mislead the tuner)")
+                         "(profiling runs: the timings under a profiler mislead the tuner); "
+                         "write --shapes=-1,2 for whole-matrix local items")
     ap.add_argument("--P", type=int, default=None, help="custom subdomain count")
     ap.add_argument("--gamma", type=float, default=None, help="custom overlap")
     ap.add_argument("--stencil-levels", default=None,
