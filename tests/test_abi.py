@@ -43,3 +43,32 @@ def test_library_loads_and_reports_status_strings(libpath):
     opt = _lib.Options()
     L.sfcdd_default_options(ctypes.byref(opt))
     assert opt.precision == 0 and opt.weighting == 1 and opt.variant == 0 and opt.flexible == -1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every option, statistics, info and tuning struct of include/sfcdd.h has
+    the size and field offsets of its ctypes mirror (a plain C program built
+    against the header prints them)."""
+    mirrors = {"sfcdd_options": _lib.Options, "sfcdd_stats": _lib.Stats,
+               "sfcdd_info": _lib.Info, "sfcdd_tuning": _lib.Tuning}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sfcdd.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, key, val = line.split()
+            got[(cname, key)] = int(val)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
