@@ -54,6 +54,7 @@ struct sfcdd_batch {
   std::vector<int> h_start;   // first curve position of every local matrix
   int nsub_local = 1, nsub_coarse = 1;
   TileSetDev ts{};
+  int* d_nzr = nullptr;  // zero-row bounds (ts.nzr), written by the setup's scans
   MatDesc* d_md = nullptr;
   void* ltiles = nullptr;  // Lh tiles (unit diagonal blocks implied)
   void* lut = nullptr;     // Lh^T tiles, E_K on the diagonal
@@ -997,12 +998,11 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   b->ts.colidx = d_colidx;
   // zero-row bounds of the off-block tiles: whole tiles until the factors are scanned
   {
-    int* d_nzr = nullptr;
-    BTRY(balloc(b, &d_nzr, nrows));
+    BTRY(balloc(b, &b->d_nzr, nrows));
     const std::vector<int> whole(nrows, TILE);
-    SFCDD_CUDA_OK(cudaMemcpyAsync(d_nzr, whole.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(b->d_nzr, whole.data(), nrows * sizeof(int), cudaMemcpyHostToDevice, s));
     SFCDD_CUDA_OK(cudaStreamSynchronize(s));
-    b->ts.nzr = d_nzr;
+    b->ts.nzr = b->d_nzr;
   }
 
   // local matrices and factors (Sec. 3.1), coarse matrices and FP64 factors (eq. csm)
@@ -1050,7 +1050,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
     b->lut = work_ut;
   }
   launch_offblock_rows(b->ts, 0, b->nlocal, b->max_nt_local, b->ltiles, b->st,
-                       const_cast<int*>(b->ts.nzr), s);
+                       b->d_nzr, s);
   BTRY(balloc(b, &b->ctiles, b->sky.ctiles * TILE2));
   {
     const int smem = TILE2 * (int)(sizeof(double) + sizeof(int));
@@ -1063,7 +1063,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   BTRY(balloc(b, &b->cut, b->sky.ctiles * TILE2));
   unitize_tiles(b->ts, b->nlocal, nsub, b->sky.max_ctiles, b->ctiles, b->cut, Store::F64, s);
   launch_offblock_rows(b->ts, b->nlocal, nsub, b->max_nt_coarse, b->ctiles, Store::F64,
-                       const_cast<int*>(b->ts.nzr), s);
+                       b->d_nzr, s);
   SFCDD_CUDA_OK(cudaGetLastError());
   b->factor_bytes = b->sky.ltiles * TILE2 * (b->precision == 0 ? 8 : b->precision == 1 ? 4 : 2) +
                     b->sky.ctiles * TILE2 * 8;
