@@ -7,6 +7,8 @@ scaled by 1/h_j^2 (the operator of Sec. 4), so
     dL/df   = lambda
     dL/dc_j = -lambda^T B_j u.
 The loss is the plain sum over the interior points (no h^d weight).
+`method="sine"` takes both solves by the sine-mode expansion (exact to
+rounding at any size); the default uses the dense / sparse direct solve.
 """
 from __future__ import annotations
 
@@ -15,16 +17,21 @@ import numpy as np
 from . import exact, grid
 
 
-def loss(levels, f, u_t, coeffs=None) -> float:
-    u = exact.solve(levels, f, coeffs)
+def _solver(method):
+    return exact.solve_sine if method == "sine" else exact.solve
+
+
+def loss(levels, f, u_t, coeffs=None, method="direct") -> float:
+    u = _solver(method)(levels, f, coeffs)
     return float(np.sum((u - u_t) ** 2))
 
 
-def gradients(levels, f, u_t, coeffs=None):
+def gradients(levels, f, u_t, coeffs=None, method="direct"):
     """Returns (u, dL/df, dL/dc)."""
     d = len(levels)
-    u = exact.solve(levels, f, coeffs)
-    lam = exact.solve(levels, 2.0 * (u - u_t), coeffs)
+    solve = _solver(method)
+    u = solve(levels, f, coeffs)
+    lam = solve(levels, 2.0 * (u - u_t), coeffs)
     gc = np.array([-float(lam @ (grid.partial_operator(levels, j) @ u)) for j in range(d)])
     return u, lam, gc
 

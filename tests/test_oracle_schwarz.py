@@ -149,3 +149,40 @@ def test_richardson_rate_bound():
     for k in range(1, 11):
         x = x + xi * S.apply(-(A @ x))      # f = 0: the iterate is the error
         assert enorm(x) <= rho ** k * enorm(x0) * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("levels,P,gamma,q,weighting", [((3, 3), 4, 0.5, 3, "omega"),
+                                                        ((2, 2, 3), 6, 1.0, 2, "omega"),
+                                                        ((4, 3), 5, 0.25, 4, "omega"),
+                                                        ((3, 3), 5, 0.5, 2, "none")])
+def test_balanced_operator_against_dense_definition(levels, P, gamma, q, weighting):
+    """eq. (balan) / (balSW) built from dense matrices: F = R_0^T A_0^{-1} R_0
+    with R_0 from the blocks of eq. (restr), C_(1),D^{-1} = sum_i omega_i R_i^T
+    A_i^{-1} R_i from the literal sets of eq. (enlarge), G = I - A F and
+    M = G^T C_(1),D^{-1} G + F with G^T formed by an explicit transpose.  A
+    swap of G and G^T gives G C G^T + F, also symmetric positive definite, but
+    another matrix: it is checked to differ."""
+    S = schwarz.Schwarz(levels, P=P, gamma=gamma, q=q, weighting=weighting)
+    A = S.A.toarray()
+    N = S.N
+    sets = partition.overlap_sets_literal(N, P, gamma)
+    cnt = np.zeros(N)
+    for s in sets:
+        cnt[list(s)] += 1
+    R0 = np.zeros((S.N0, N))
+    for a, (s, n) in enumerate(zip(S.bstart, S.bsize)):
+        R0[a, S.perm[s:s + n]] = 1.0
+    F = R0.T @ np.linalg.inv(R0 @ A @ R0.T) @ R0
+    C1 = np.zeros((N, N))
+    for s in sets:
+        pos = sorted(s)
+        omega = max(1.0 / cnt[p] for p in pos) if weighting == "omega" else 1.0
+        R = np.zeros((len(pos), N))
+        R[np.arange(len(pos)), S.perm[pos]] = 1.0
+        C1 += omega * R.T @ np.linalg.inv(R @ A @ R.T) @ R
+    G = np.eye(N) - A @ F
+    M = G.T @ C1 @ G + F
+    Mo = dense_M(S, S.apply_balanced)
+    assert np.allclose(Mo, M, rtol=1e-10, atol=1e-11 * np.abs(M).max())
+    swapped = G @ C1 @ G.T + F
+    assert np.abs(swapped - M).max() > 1e-3 * np.abs(M).max()
