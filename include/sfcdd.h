@@ -35,7 +35,7 @@ typedef struct sfcdd_handle sfcdd_handle;
 
 enum sfcdd_status {
   SFCDD_OK = 0,
-  SFCDD_ERR_INVALID_ARG = -1,  /* d < 1, d > 8, l_j < 1, P < 3, gamma <= 0, 2 floor(gamma)+1 >= P,
+  SFCDD_ERR_INVALID_ARG = -1,  /* d < 1, d > 8, l_j < 1, P < 2, gamma <= 0, 2 floor(gamma)+1 >= P,
                                   q outside 1..floor(N/P), a subdomain longer than N, NULL pointer */
   SFCDD_ERR_KEY_OVERFLOW = -2, /* d * max_j l_j > 64: the Hilbert key does not fit 64 bits (Sec. 4.3) */
   SFCDD_ERR_NOMEM = -3,        /* device allocation failed (dense local factors larger than free HBM) */
@@ -337,9 +337,20 @@ double sfcdd_kernel_work(const sfcdd_handle* h, int kernel_class);
 int sfcdd_destroy(sfcdd_handle* h);
 const char* sfcdd_status_string(int status);
 
-/* Curve order without any device allocation (the paper has no counterpart: it
- * is a deployment variant of the key generation and sort of Algorithm 1,
- * step 3).  For callers that cannot call cudaMalloc: code running while a
+/* Measured FP64 FMA rate of the current device (no counterpart in the paper: a
+ * measurement for reporting).  The FP64 kernels of this library (substitutions
+ * with FP64 factors, the stencil, the diagonal tile factorizations) are bound
+ * by the FP64 pipe, not by HBM, on this GPU; this is their measured ceiling.
+ * Runs `reps` launches of an in-register FMA loop over every SM on `stream`
+ * (cudaStream_t, NULL = legacy default stream), synchronises it, and writes the
+ * rate in TFLOP/s (2 flops per FMA) to *tflops (host) and the mean launch time
+ * in ms to *ms_per_launch (host, may be NULL).  Allocates and frees a small
+ * device buffer.  Errors: INVALID_ARG (tflops NULL or reps < 1), CUDA. */
+int sfcdd_measure_fp64_rate(int reps, double* tflops, double* ms_per_launch, void* stream);
+
+/* Curve order without any device allocation.  The paper has no counterpart:
+ * this is a deployment variant of the keys and sort that sfcdd_setup_ex
+ * computes.  For callers that cannot call cudaMalloc: code running while a
  * stream is being captured into a CUDA graph, hosts that hand out all device
  * memory from their own pool, and latency-critical code that must not hit the
  * device synchronisation of cudaMalloc/cudaFree.

@@ -33,7 +33,7 @@ EXPORTS = [
     "sfcdd_batch_offsets", "sfcdd_batch_solve", "sfcdd_batch_info", "sfcdd_batch_destroy",
     "sfcdd_estimate_spectrum", "sfcdd_richardson", "sfcdd_solve_homogeneous",
     "sfcdd_batch_setup_each", "sfcdd_batch_combine", "sfcdd_autotune", "sfcdd_batch_autotune",
-    "sfcdd_selftest",
+    "sfcdd_selftest", "sfcdd_measure_fp64_rate",
 ]
 
 
@@ -129,6 +129,8 @@ def lib() -> C.CDLL:
     L.sfcdd_richardson.argtypes = [H, P, P, C.c_double, C.c_double, C.c_int, C.POINTER(Stats)]
     L.sfcdd_solve_homogeneous.argtypes = [H, P, P, C.c_int, C.c_double, C.c_double, C.c_int,
                                           C.POINTER(Stats)]
+    L.sfcdd_measure_fp64_rate.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.c_void_p]
     for name in EXPORTS:
         if name not in ("sfcdd_default_options", "sfcdd_kernel_work", "sfcdd_status_string"):
             getattr(L, name).restype = C.c_int

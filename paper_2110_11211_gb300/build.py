@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsfcdd.so")
-SOURCES = ["api.cu", "keys_sort.cu", "vector.cu", "trsv.cu", "factor.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "keys_sort.cu", "vector.cu", "trsv.cu", "factor.cu", "noalloc.cu", "batch.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-diag-suppress", "550", "-I", os.path.join(ROOT, "include")]

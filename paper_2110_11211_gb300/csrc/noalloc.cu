@@ -57,16 +57,17 @@ using namespace sfcdd;
 extern "C" int sfcdd_curve_order_noalloc(const int* levels, int d, unsigned long long* keys_dev,
                                          int* perm_dev, void* stream) {
   if (!levels || !keys_dev || !perm_dev || d < 1 || d > MAXD) return SFCDD_ERR_INVALID_ARG;
-  long long N = 1;
+  // the bit counts first: with B <= 31 the point count below stays under 2^31
   int nbits = 0, B = 0;
   for (int j = 0; j < d; ++j) {
     if (levels[j] < 1 || levels[j] > 30) return SFCDD_ERR_INVALID_ARG;
-    N *= (1ll << levels[j]) - 1;
     nbits = levels[j] > nbits ? levels[j] : nbits;
     B += levels[j];
   }
   if (d * nbits > 64) return SFCDD_ERR_KEY_OVERFLOW;
   if (B > 31) return SFCDD_ERR_UNSUPPORTED;
+  long long N = 1;
+  for (int j = 0; j < d; ++j) N *= (1ll << levels[j]) - 1;
   if (N > NOALLOC_MAX_POINTS) {
     fprintf(stderr,
             "sfcdd_curve_order_noalloc: %lld grid points exceed the static scratch limit of %d "

@@ -112,6 +112,7 @@ def test_whole_matrix_apply_vs_oracle(variant):
         with Solver(levels, P, gamma, variant=variant, slabs_local=-1) as s:
             z = s.apply_precond(torch.tensor(g, device="cuda")).cpu().numpy()
         assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref), (levels, variant)
+        assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max(), (levels, variant)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
@@ -161,6 +162,7 @@ def test_coarse_block_sizes_vs_oracle():
         with Solver(levels, P, gamma, variant="coarse_only", coarse_block=cb) as s:
             z = s.apply_precond(torch.tensor(g, device="cuda")).cpu().numpy()
         assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref), cb
+        assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max(), cb
     for cb in (3, 16, -1):
         with pytest.raises(SfcddError):
             Solver((6, 4), 8, 0.5, coarse_block=cb)

@@ -6,7 +6,8 @@ FP64 floating point within the bounds derived in the design notes:
   stencil / assembled matrices: same terms summed in another order -> elementwise
   |delta| <= 8 u sum_k |A_ik x_k| (u = 2^-53);
   preconditioner apply (FP64): two triangular solves per subdomain, backward
-  stable, relative norm difference <= 1e-12;
+  stable, relative norm difference <= 1e-12 and every entry within
+  1e-12 max_i |z_i| (so one wrong entry of a small subdomain cannot hide);
   solve: ||u - u*|| / ||u*|| <= 1e-8 at relative residual 1e-10 and PCG
   iteration counts within +-1 of the oracle's.
 """
@@ -109,6 +110,8 @@ def test_preconditioner_apply_fp64(levels, P, gamma, variant):
     else:
         ref = S.coarse_correction(g)
     assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+    # element by element: a wrong entry of one small subdomain cannot hide in the norm
+    assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("levels,P,gamma", [((6, 6), 8, 0.5), ((3, 3, 3), 5, 1.0),
@@ -170,6 +173,7 @@ def test_preconditioner_apply_low_precision(precision, tol):
         z = s.apply_precond(torch.tensor(g, device="cuda")).cpu().numpy()
     ref = S.apply(g)
     assert np.linalg.norm(z - ref) <= tol * np.linalg.norm(ref)
+    assert np.abs(z - ref).max() <= tol * np.abs(ref).max()
 
 
 def test_deterministic_repeat():
@@ -225,6 +229,7 @@ def test_full_size_aniso3d_sampled():
         ids = S.local_ids(i)
         ref[ids] += S.omega[i] * S.local_solve(i, g[ids])
     assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("levels,P,gamma", [((6, 6), 8, 0.5), ((4, 3, 3), 6, 1.0),

@@ -124,6 +124,7 @@ def test_fp64_apply_sliced_vs_oracle():
             z = s.apply_precond(torch.tensor(g, device="cuda")).cpu().numpy()
         ref = S.apply(g)
         assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+        assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("levels,P,gamma", GRIDS[:3])

@@ -54,3 +54,21 @@ def test_two_calls_in_a_row_match_the_allocating_path():
 def test_rejects_grids_beyond_the_scratch_limit():
     rc, _, _ = noalloc_curve((10, 10))      # 1,046,529 points > 262,144
     assert rc == -1
+
+
+def test_rejects_oversized_levels_before_counting_points():
+    # d * max l > 64 -> KEY_OVERFLOW; sum l > 31 -> UNSUPPORTED; both before the
+    # point count is formed (no overflow for levels up to 30 on every axis)
+    for levels, code in [((30,) * 6, -2), ((30, 30), -9), ((16, 16), -9)]:
+        rc, _, _ = noalloc_curve_args(levels)
+        assert rc == code, (levels, rc)
+
+
+def noalloc_curve_args(levels):
+    L = _lib.lib()
+    keys = torch.empty(1, dtype=torch.int64, device="cuda")
+    perm = torch.empty(1, dtype=torch.int32, device="cuda")
+    lv = (C.c_int * len(levels))(*levels)
+    rc = L.sfcdd_curve_order_noalloc(lv, len(levels), keys.data_ptr(), perm.data_ptr(),
+                                     C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return rc, keys, perm
