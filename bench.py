@@ -381,14 +381,16 @@ def gpu_small_solve(name, stream, reps=5):
 
 
 def single_variant(levels, P, gamma, prec, coeffs, f, u_ref, rtol, stream, steps=3, variant="additive",
-                   hbm_peak=None):
+                   hbm_peak=None, tensor_cores=-1):
     """Tuned shapes, then `steps` timed setup + solve passes (CUDA events, after one
     warm-up) and one profiled pass for the substitution rates."""
     import torch
     from paper_2110_11211_gb300.solver import Solver
-    with Solver(levels, P, gamma, precision=prec, coeffs=coeffs, variant=variant) as s:
+    with Solver(levels, P, gamma, precision=prec, coeffs=coeffs, variant=variant,
+                tensor_cores=tensor_cores) as s:
         vt = s.autotune(reps=3)
-    shapes = dict(slabs_local=vt["slabs_local"], slabs_coarse=vt["slabs_coarse"])
+    shapes = dict(slabs_local=vt["slabs_local"], slabs_coarse=vt["slabs_coarse"],
+                  tensor_cores=tensor_cores)
     times = []
     for k in range(steps + 1):
         torch.cuda.synchronize()
@@ -438,6 +440,11 @@ def aniso6d_variants(stream, hbm_peak, rtol=1e-10):
     for prec in ("fp64", "fp32", "bf16"):
         _, out[prec] = single_variant(w["levels"], w["P"], w["gamma"], prec, None, f, u_ref, rtol,
                                       stream, hbm_peak=hbm_peak)
+    # the FP32-accurate factorization rounded to bf16 afterwards, for comparison
+    # with the BF16 factorization (bf16 tensor-core operands) above
+    _, out["bf16_fp32_factorization"] = single_variant(
+        w["levels"], w["P"], w["gamma"], "bf16", None, f, u_ref, rtol, stream, hbm_peak=hbm_peak,
+        tensor_cores=2)
     out["iteration_penalty"] = {p: out[p]["iters"] - out["fp64"]["iters"] for p in ("fp32", "bf16")}
     out["speedup_vs_fp64"] = {p: round(out["fp64"]["ms"] / out[p]["ms"], 3) for p in ("fp32", "bf16")}
     return out

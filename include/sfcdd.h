@@ -82,12 +82,16 @@ typedef struct {
   int slabs_coarse;     /* the same for the coarse substitutions: 1, 2 or 4; 0 (default) = 2.
                            FP32 / BF16 local factors require 2 or 4 (INVALID_ARG otherwise). */
   int tensor_cores;     /* the panel and trailing-update tile products of the local and coarse
-                           factorizations on the tensor cores (tcgen05) when 1 or -1 (default),
-                           on CUDA cores when 0.  FP32 / BF16 local factors: TF32 operands
-                           with the hi/lo split, FP32 accumulation (FP32-accurate).  FP64
-                           factors: exact 8-bit digit slices of each row (Ozaki, Ogita, Oishi
-                           and Rump's error-free splitting) multiplied as bf16 with exact FP32
-                           accumulation, combined in integers and rounded once to FP64. */
+                           factorizations on the tensor cores (tcgen05) when 1, 2 or -1
+                           (default), on CUDA cores when 0.  FP32 local factors: TF32 operands
+                           with the hi/lo split, FP32 accumulation (FP32-accurate).  BF16 local
+                           factors: bf16 operands with FP32 accumulation (kind::f16; FP32
+                           working tiles and diagonal tiles; the BF16 factorization) when 1 or
+                           -1; with 2 the FP32-accurate TF32 split, the factor rounded to bf16
+                           afterwards.  FP64 factors: exact 8-bit digit slices of each row
+                           (Ozaki, Ogita, Oishi and Rump's error-free splitting) multiplied as
+                           bf16 with exact FP32 accumulation, combined in integers and rounded
+                           once to FP64. */
   int coarse_block;     /* tiles per unit diagonal block of the coarse substitution form
                            (L = Lh blockdiag(D_J), Sec. 3.1 solves): 1, 2, 4 or 8; 0 (default)
                            = 4.  Larger blocks shorten the coarse substitutions' dependency
@@ -320,6 +324,8 @@ enum sfcdd_kernel_class {
   SFCDD_K_KEYGEN = 0, SFCDD_K_SORT, SFCDD_K_ASSEMBLE, SFCDD_K_POTRF, SFCDD_K_TRSM, SFCDD_K_SYRK,
   SFCDD_K_COARSE_ASSEMBLE, SFCDD_K_STENCIL, SFCDD_K_UPDATE, SFCDD_K_RESTRICT, SFCDD_K_TRSV_FWD,
   SFCDD_K_TRSV_BWD, SFCDD_K_PROLONG, SFCDD_K_VECTOR, SFCDD_K_GRAD, SFCDD_K_COARSE_FACTOR,
+  SFCDD_K_PCG_VECTOR, /* the fused vector phase of a PCG iteration (prolongation, p, stencil,
+                         x / r update, restriction) in one cooperative launch */
   SFCDD_K_COUNT
 };
 int sfcdd_set_profiling(sfcdd_handle* h, int enable);

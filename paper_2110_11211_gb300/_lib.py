@@ -21,7 +21,7 @@ VARIANT = {"additive": 0, "balanced": 1, "one_level": 2, "coarse_only": 3}
 WEIGHTING = {"none": 0, "omega": 1}
 KERNEL_CLASSES = ["keygen", "sort", "assemble", "potrf", "trsm", "syrk", "coarse_assemble",
                   "stencil", "update", "restrict", "trsv_fwd", "trsv_bwd", "prolong", "vector",
-                  "grad", "coarse_factor"]
+                  "grad", "coarse_factor", "pcg_vector"]
 
 # Every exported function the header declares (checked by a CPU test).
 EXPORTS = [

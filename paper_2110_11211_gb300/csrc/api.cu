@@ -363,6 +363,7 @@ struct sfcdd_handle {
   int max_nt = 0, nt0 = 0, max_ltiles = 0, max_ctiles = 0;
   int nsub_local = 1, nsub_coarse = 4;
   bool tensor_cores = false;  // factorization tile products on tcgen05 (FP32 split / FP64 sliced)
+  bool bf16_operands = false; // BF16 local factors: bf16 operands (kind::f16), else the TF32 split
   int cb_coarse = 4;  // tiles per unit diagonal block of the coarse substitution form
   long long fwd_tiles_l = 0, bwd_tiles_l = 0, fwd_tiles_c = 0, bwd_tiles_c = 0;
   // local factor elements the substitutions need (nonzero rows of the off-block
@@ -387,6 +388,12 @@ struct sfcdd_handle {
   PcgScalars* sc = nullptr;
   PcgScalars* sc_host = nullptr;
   ReduceWs ws{};
+  // the vector phase of an iteration as one cooperative launch (every variant
+  // but the balanced one): CTA ranges, barrier, partials, the second p buffer
+  bool fused = false;
+  int fused_rc = 0;
+  FusedPcg fz{};
+  double* p2 = nullptr;
   ErrWord* err = nullptr;
   cudaGraphExec_t iter_graph = nullptr;
   int graph_kernels[SFCDD_K_COUNT] = {0};
@@ -627,6 +634,13 @@ void enqueue_apply(sfcdd_handle* h, Prof& pf, const double* g, double* z, PcgSca
 
 void enqueue_iteration(sfcdd_handle* h, Prof& pf) {
   cudaStream_t s = pf.s;
+  if (h->fused) {
+    // z = C^{-1} r through the substitutions (g0 = R_0 r was formed by the
+    // previous vector phase), then the whole vector phase in one launch
+    enqueue_solves(h, pf, h->r, h->sc, LIST_MAIN);
+    pf.run(SFCDD_K_PCG_VECTOR, [&] { h->fused_rc = launch_fused_pcg(h->fz, s); });
+    return;
+  }
   pf.run(SFCDD_K_STENCIL,
          [&] { launch_stencil(h->g, h->curve_code, h->invpad, h->p, h->qv, 1, h->sc, h->ws, s); });
   pf.run(SFCDD_K_UPDATE, [&] { launch_update_xr(h->N, h->x, h->r, h->p, h->qv, h->sc, h->ws, s); });
@@ -695,9 +709,15 @@ int build_graph(sfcdd_handle* h) {
   h->profiling = false;
   SFCDD_CUDA_OK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   Prof pf(h, h->cap_stream);
+  h->fused_rc = 0;
   enqueue_iteration(h, pf);
   cudaGraph_t graph;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (h->fused_rc) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    h->profiling = prof;
+    return h->fused_rc;
+  }
   h->profiling = prof;
   for (int k = 0; k < SFCDD_K_COUNT; ++k) {
     h->graph_kernels[k] = (int)(h->launches[k] - before[k]);
@@ -716,6 +736,63 @@ int check_err(sfcdd_handle* h, int* fail_index) {
   SFCDD_CUDA_OK(cudaStreamSynchronize(h->stream));
   if (fail_index) *fail_index = e.index;
   return e.code;
+}
+
+// The fused vector phase: CTA count (resident in one cooperative launch, at
+// most one CTA per 256 points and, with a coarse space, per coarse block) and
+// the CTA ranges of curve positions (whole coarse blocks when there is a
+// coarse space, so the restriction stays inside a CTA).
+int setup_fused(sfcdd_handle* h) {
+  const int mode = prolong_mode(h);
+  int nb = fused_pcg_blocks(h->d);
+  if (nb <= 0) return SFCDD_ERR_CUDA;
+  nb = std::min(nb, std::max(1, (h->N + 255) / 256));
+  if (mode != 1) nb = std::min(nb, h->N0);
+  std::vector<int> range(nb + 1);
+  for (int c = 0; c <= nb; ++c) {
+    if (mode == 1) {
+      range[c] = (int)((long long)h->N * c / nb);
+    } else {
+      const int b = (int)((long long)h->N0 * c / nb);
+      int st = h->N, sz = 0;
+      if (b < h->N0) coarse_block_range(h->pd, b, st, sz);
+      range[c] = st;
+    }
+  }
+  FusedPcg& f = h->fz;
+  f.nblocks = nb;
+  f.mode = mode;
+  int* d_range = nullptr;
+  TRY(dalloc(h, &d_range, nb + 1));
+  TRY(dalloc(h, &f.bar, 2));
+  TRY(dalloc(h, &f.part, (size_t)4 * nb));
+  TRY(dalloc(h, &f.ws.partial, (size_t)2 * nb));
+  TRY(dalloc(h, &f.ws.counter, 1));
+  TRY(dalloc(h, &h->p2, h->N));
+  cudaStream_t s = h->stream;
+  SFCDD_CUDA_OK(cudaMemcpyAsync(d_range, range.data(), (nb + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(f.bar, 0, 2 * sizeof(unsigned), s));
+  SFCDD_CUDA_OK(cudaMemsetAsync(f.ws.counter, 0, sizeof(unsigned), s));
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // the host range vector goes out of scope
+  f.ws.nblocks = nb;
+  f.range = d_range;
+  f.g = h->g;
+  f.pd = h->pd;
+  f.ts = h->ts;
+  f.code = h->curve_code;
+  f.invpad = h->invpad;
+  f.dvec = h->dbuf;
+  f.x = h->x;
+  f.r = h->r;
+  f.z = h->z;
+  f.p[0] = h->p;
+  f.p[1] = h->p2;
+  f.q = h->qv;
+  f.g0 = h->g0;
+  f.sc = h->sc;
+  f.err = h->err;
+  h->fused = true;
+  return SFCDD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -765,8 +842,9 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   if (h->cb_coarse != 1 && h->cb_coarse != 2 && h->cb_coarse != 4 && h->cb_coarse != 8)
     return SFCDD_ERR_INVALID_ARG;
   if (!valid_slabs(h->precision, h->nsub_local, h->nsub_coarse)) return SFCDD_ERR_INVALID_ARG;
-  if (o.tensor_cores < -1 || o.tensor_cores > 1) return SFCDD_ERR_INVALID_ARG;
+  if (o.tensor_cores < -1 || o.tensor_cores > 2) return SFCDD_ERR_INVALID_ARG;
   h->tensor_cores = o.tensor_cores != 0;
+  h->bf16_operands = h->precision == SFCDD_BF16 && h->tensor_cores && o.tensor_cores != 2;
   h->flexible = o.flexible < 0 ? (h->precision != SFCDD_FP64 ? 1 : 0) : (o.flexible ? 1 : 0);
   h->stream = (cudaStream_t)o.stream;
   h->profiling = o.profile != 0;
@@ -1070,7 +1148,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
                             work_tiles, compute_st, s);
     });
     factor_tiles(h->ts, 0, P, h->max_nt, h->col_max_local.data(), work_tiles, compute_st, diag_cnt,
-                 h->err, s, &pf, compute_st == Store::F64 ? 4 : 1, h->tensor_cores);
+                 h->err, s, &pf, compute_st == Store::F64 ? 4 : 1, h->tensor_cores,
+                 h->bf16_operands);
   }
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
   NvtxRange nvtx_unit("sfcdd setup: substitution form");
@@ -1132,6 +1211,7 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   TRY(dalloc(h, &h->ws.partial, (size_t)h->ws.nblocks * MAXD));
   TRY(dalloc(h, &h->ws.counter, 1));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->ws.counter, 0, sizeof(unsigned), s));
+  if (h->variant != SFCDD_BALANCED) TRY(setup_fused(h));
 
   SFCDD_CUDA_OK(cudaStreamWaitEvent(s, ev_coarse, 0));
   cudaEventDestroy(ev_coarse);
@@ -1199,8 +1279,15 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats,
   }
   SFCDD_CUDA_OK(cudaMemsetAsync(h->p, 0, (size_t)h->N * sizeof(double), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->z, 0, (size_t)h->N * sizeof(double), s));
-  enqueue_apply(h, pf, h->r, h->z, h->sc);   // z_0 = C^{-1} r_0, rz, beta = 0
-  pf.run(SFCDD_K_VECTOR, [&] { launch_update_p(h->N, h->z, h->p, h->sc, s); });
+  if (h->fused) {
+    // every iteration is {substitutions, vector phase}: the first needs R_0 r_0
+    SFCDD_CUDA_OK(cudaMemsetAsync(h->p2, 0, (size_t)h->N * sizeof(double), s));
+    if (h->variant != SFCDD_ONE_LEVEL)
+      pf.run(SFCDD_K_RESTRICT, [&] { launch_restrict(h->pd, h->r, h->g0, h->sc, s); });
+  } else {
+    enqueue_apply(h, pf, h->r, h->z, h->sc);   // z_0 = C^{-1} r_0, rz, beta = 0
+    pf.run(SFCDD_K_VECTOR, [&] { launch_update_p(h->N, h->z, h->p, h->sc, s); });
+  }
   int launched = 0;
   int chunk = 2;
   int rc = SFCDD_OK;
@@ -1212,6 +1299,7 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats,
     for (int k = 0; k < n; ++k) {
       if (h->profiling) {
         enqueue_iteration(h, pf);
+        if (h->fused_rc) return h->fused_rc;
       } else {
         SFCDD_CUDA_OK(cudaGraphLaunch(h->iter_graph, s));
         for (int c = 0; c < SFCDD_K_COUNT; ++c) h->launches[c] += h->graph_kernels[c];

@@ -775,7 +775,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   if (opt) o = *opt;
   const bool variant_ok = o.variant == SFCDD_ADDITIVE || o.variant == SFCDD_BALANCED;
   if (!variant_ok || o.precision < 0 || o.precision > 2 || o.weighting < 0 || o.weighting > 1 ||
-      o.tensor_cores < -1 || o.tensor_cores > 1)
+      o.tensor_cores < -1 || o.tensor_cores > 2)
     return !variant_ok ? SFCDD_ERR_UNSUPPORTED : SFCDD_ERR_INVALID_ARG;
   b->variant = o.variant;
   b->nsub = nsub;
@@ -1030,7 +1030,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
     void after(int) override {}
   } nohook;
   factor_tiles(b->ts, 0, b->nlocal, b->max_nt_local, b->sky.col_max_local.data(), work_tiles, cst,
-               diag_cnt, b->err, s, &nohook, 1, o.tensor_cores != 0);
+               diag_cnt, b->err, s, &nohook, 1, o.tensor_cores != 0,
+               o.precision == SFCDD_BF16 && o.tensor_cores != 0 && o.tensor_cores != 2);
   // substitution form: Lh in place, Lh^T and E_K into a second tile array
   void* work_ut = nullptr;
   BTRY(balloc(b, (unsigned char**)&work_ut, b->sky.ltiles * TILE2 * esz));

@@ -491,39 +491,88 @@ __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int nmat, 
 }
 
 // ---------------------------------------------------------------------------
-// FP32 panel and trailing update on the tensor cores (tcgen05, TF32 operands
-// with the error-compensated hi/lo split, FP32 accumulation in tensor memory;
-// see tc_tile.cuh).  One CTA computes two tile products that share their right
+// FP32 panel and trailing update on the tensor cores (tcgen05, FP32 accumulation
+// in tensor memory).  One CTA computes two tile products that share their right
 // operand as one M = 128 MMA chain: rows 0-63 of A are the first tile, rows
 // 64-127 the second (or the first again when there is no second).
+// BF = false: TF32 operands with the error-compensated hi/lo split (see
+// tc_tile.cuh), FP32-accurate products.  BF = true: the operands rounded to
+// bf16 (one kind::f16 MMA per K = 16 step), the BF16 factorization: bf16
+// operands, FP32 accumulation, FP32 working tiles and diagonal factorizations.
+
+// Stage rows [row0, row0 + 64) of a bf16 operand from a row-major 64 x 64 FP32
+// tile, rounded to nearest: 8 consecutive columns form one 16-byte core row
+// (the K-major layout of oz_tile.cuh: LBO 128, SBO 1024).
+__device__ __forceinline__ void stage_tile_bf16(unsigned char* dst, const float* __restrict__ src,
+                                                int row0) {
+  for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) {
+    const int r = e >> 3, c8 = e & 7;
+    const float4 v0 = *reinterpret_cast<const float4*>(src + r * 64 + 8 * c8);
+    const float4 v1 = *reinterpret_cast<const float4*>(src + r * 64 + 8 * c8 + 4);
+    auto pack = [](float lo, float hi) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);  // lo in the low half
+      return *reinterpret_cast<const uint32_t*>(&b);
+    };
+    const uint4 w = make_uint4(pack(v0.x, v0.y), pack(v0.z, v0.w), pack(v1.x, v1.y),
+                               pack(v1.z, v1.w));
+    *reinterpret_cast<uint4*>(dst + oz::core_offset(row0 + r, c8)) = w;
+  }
+}
+
+// Shared memory of one product: TF32 split A_hi | A_lo | B_hi | B_lo, bf16 A | B;
+// then the mbarrier and the tensor-memory address.
+template <bool BF>
+__host__ __device__ constexpr uint32_t tc_operand_bytes() {
+  return BF ? oz::A_SLICE + oz::B_SLICE : 2 * tc::A_BYTES + 2 * tc::B_BYTES;
+}
+template <bool BF>
+__host__ __device__ constexpr int tc_smem_bytes() {
+  return (int)tc_operand_bytes<BF>() + 16;
+}
 
 // Stage, multiply, and hand each thread its 32 accumulator columns; returns
 // false (error word set) when the MMA completion wait ran out.
+template <bool BF>
 __device__ __forceinline__ bool tc_product(unsigned char* dsm, const float* a0, const float* a1,
                                            const float* b, float (&v)[32], int& row, int& col0,
                                            uint32_t& tmem, ErrWord* err, int m) {
   using namespace tc;
-  unsigned char* ahi = dsm;
-  unsigned char* alo = dsm + A_BYTES;
-  unsigned char* bhi = dsm + 2 * A_BYTES;
-  unsigned char* blo = bhi + B_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(blo + B_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + tc_operand_bytes<BF>());
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   if (threadIdx.x < 32) tmem_alloc(tslot);
   if (threadIdx.x == 0) {
     mbar_init1(bar);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  stage_tile(ahi, alo, a0, 0);
-  stage_tile(ahi, alo, a1, 64);
-  stage_tile(bhi, blo, b, 0);
+  if constexpr (BF) {
+    stage_tile_bf16(dsm, a0, 0);
+    stage_tile_bf16(dsm, a1, 64);
+    stage_tile_bf16(dsm + oz::A_SLICE, b, 0);
+  } else {
+    unsigned char* ahi = dsm;
+    unsigned char* alo = dsm + A_BYTES;
+    unsigned char* bhi = dsm + 2 * A_BYTES;
+    unsigned char* blo = bhi + B_BYTES;
+    stage_tile(ahi, alo, a0, 0);
+    stage_tile(ahi, alo, a1, 64);
+    stage_tile(bhi, blo, b, 0);
+  }
   fence_proxy_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   tmem = *tslot;
   if (threadIdx.x == 0) {
-    issue_product(tmem, ahi, alo, bhi, blo);
+    if constexpr (BF) {
+      const uint32_t a = smem_addr(dsm), bb = smem_addr(dsm + oz::A_SLICE);
+#pragma unroll
+      for (int kk = 0; kk < TC_K / 16; ++kk) {
+        const uint32_t o = (uint32_t)kk * 2 * oz::LBO;
+        oz::mma_bf16(tmem, oz::make_desc(a + o), oz::make_desc(bb + o), kk > 0 ? 1u : 0u);
+      }
+    } else {
+      issue_product(tmem, dsm, dsm + A_BYTES, dsm + 2 * A_BYTES, dsm + 2 * A_BYTES + B_BYTES);
+    }
     mma_commit(bar);
   }
   const bool ok = mbar_wait_bounded(bar, 0, 1ll << 24);
@@ -548,6 +597,7 @@ __device__ __forceinline__ void tc_release(uint32_t tmem) {
 
 // Panel L_ik = A_ik Linv_kk^T, two stored tiles of column k per CTA.
 // grid = (ceil(max panel rows / 2), nmat)
+template <bool BF>
 __global__ void __launch_bounds__(FB) k_trsm_tc(TileSetDev ts, int mat0, int nmat, int k,
                                                 float* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_tc[];
@@ -568,7 +618,7 @@ __global__ void __launch_bounds__(FB) k_trsm_tc(TileSetDev ts, int mat0, int nma
   float v[32];
   int row, col0;
   uint32_t tmem;
-  const bool ok = tc_product(dsm_tc, a0, a1, lkk, v, row, col0, tmem, err, m);
+  const bool ok = tc_product<BF>(dsm_tc, a0, a1, lkk, v, row, col0, tmem, err, m);
   // every A tile is staged (the barrier inside tc_product) before any is overwritten
   if (ok && (row < 64 || two)) {
     float* out = (row < 64 ? a0 : a1) + (row & 63) * TILE + col0;
@@ -585,6 +635,7 @@ __global__ void __launch_bounds__(FB) k_trsm_tc(TileSetDev ts, int mat0, int nma
 // CTA whose first target is tile (k+1, k+1) then factors it (step k+1's
 // potrf); the launch's last CTA does so when column k does not reach row k+1.
 // grid = (max panel rows * pmax + 1, nmat), pmax = ceil(max panel rows / 2)
+template <bool BF>
 __global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int nmat, int k, int pmax,
                                                 float* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_tc[];
@@ -615,7 +666,7 @@ __global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int nma
   float v[32];
   int row, col0;
   uint32_t tmem;
-  const bool ok = tc_product(dsm_tc, l0, l1, ljk, v, row, col0, tmem, err, m);
+  const bool ok = tc_product<BF>(dsm_tc, l0, l1, ljk, v, row, col0, tmem, err, m);
   if (ok && (row < 64 || two)) {
     float* out = (row < 64 ? d0 : d1) + (row & 63) * TILE + col0;
 #pragma unroll
@@ -814,15 +865,18 @@ static void factor_tiles_oz(const TileSetDev& ts, int mat0, int nmat, int max_nt
   }
 }
 
-// The FP32 factorization with its panel and trailing updates on the tensor cores.
+// The FP32 factorization with its panel and trailing updates on the tensor cores
+// (BF: bf16 operands, the BF16 factorization; else the FP32-accurate TF32 split).
+template <bool BF>
 static void factor_tiles_tc(const TileSetDev& ts, int mat0, int nmat, int max_nt,
                             const int* col_max, float* tiles, ErrWord* err, cudaStream_t s,
                             LaunchHook* hook) {
   const int sm_potrf = (2 * TILE + 1) * (TILE + 1) * (int)sizeof(float);
-  const int sm_tc = (int)tc::SMEM_BYTES;
+  // the syrk launch's last CTA factors the next diagonal tile in the same shared memory
+  const int sm_tc = std::max(tc_smem_bytes<BF>(), sm_potrf);
   cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_potrf);
-  cudaFuncSetAttribute(k_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_tc);
-  cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_tc);
+  cudaFuncSetAttribute(k_trsm_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_tc);
+  cudaFuncSetAttribute(k_syrk_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_tc);
   hook->before(SFCDD_K_POTRF);
   k_potrf<float><<<nmat, FB, sm_potrf, s>>>(ts, mat0, 0, tiles, err);
   hook->after(SFCDD_K_POTRF);
@@ -831,11 +885,11 @@ static void factor_tiles_tc(const TileSetDev& ts, int mat0, int nmat, int max_nt
     if (rows > 0) {
       const int pmax = (rows + 1) / 2;
       hook->before(SFCDD_K_TRSM);
-      k_trsm_tc<<<mat_grid(pmax, nmat), FB, sm_tc, s>>>(ts, mat0, nmat, k, tiles, err);
+      k_trsm_tc<BF><<<mat_grid(pmax, nmat), FB, sm_tc, s>>>(ts, mat0, nmat, k, tiles, err);
       hook->after(SFCDD_K_TRSM);
       hook->before(SFCDD_K_SYRK);
-      k_syrk_tc<<<mat_grid(rows * pmax + 1, nmat), FB, sm_tc, s>>>(ts, mat0, nmat, k, pmax, tiles,
-                                                                    err);
+      k_syrk_tc<BF><<<mat_grid(rows * pmax + 1, nmat), FB, sm_tc, s>>>(ts, mat0, nmat, k, pmax,
+                                                                        tiles, err);
       hook->after(SFCDD_K_SYRK);
     } else if (k + 1 < max_nt) {
       hook->before(SFCDD_K_POTRF);
@@ -878,7 +932,7 @@ static void factor_tiles_t(const TileSetDev& ts, int mat0, int nmat, int max_nt,
 
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                   void* tiles, Store st, int* diag_cnt, ErrWord* err, cudaStream_t s,
-                  LaunchHook* hook, int split, bool tensor_cores) {
+                  LaunchHook* hook, int split, bool tensor_cores, bool bf16_operands) {
   if (st == Store::F64 && tensor_cores) {
     factor_tiles_oz(ts, mat0, nmat, max_nt, col_max, (double*)tiles, err, s, hook);
   } else if (st == Store::F64) {
@@ -888,8 +942,10 @@ void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const in
     else
       factor_tiles_t<double, 1>(ts, mat0, nmat, max_nt, col_max, (double*)tiles, diag_cnt, err, s,
                                 hook);
+  } else if (tensor_cores && bf16_operands) {
+    factor_tiles_tc<true>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, err, s, hook);
   } else if (tensor_cores) {
-    factor_tiles_tc(ts, mat0, nmat, max_nt, col_max, (float*)tiles, err, s, hook);
+    factor_tiles_tc<false>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, err, s, hook);
   } else {
     factor_tiles_t<float, 1>(ts, mat0, nmat, max_nt, col_max, (float*)tiles, diag_cnt, err, s, hook);
   }

@@ -313,6 +313,38 @@ void launch_residual(const GridDev& g, const unsigned* code, const int* invpad, 
 void launch_combine_bal(int n, const double* t, const double* v, const double* w, const double* r,
                         double* z, PcgScalars* sc, ReduceWs ws, cudaStream_t s);
 void launch_update_p(int n, const double* z, double* p, const PcgScalars* sc, cudaStream_t s);
+
+// The vector phase of one PCG iteration in one cooperative launch (every CTA
+// resident; two grid barriers): prolongation z = C^{-1} r with r^T z -> beta;
+// p_new = z + beta p_old (double-buffered by iteration parity), q = A p_new and
+// p^T q -> alpha; x += alpha p, r -= alpha q, ||r|| -> convergence; the coarse
+// restriction g0 = R_0 r for the next iteration.  Each CTA owns the curve
+// positions [range[c], range[c + 1]), whole coarse blocks when mode != 1.
+struct FusedPcg {
+  GridDev g;
+  PartDev pd;
+  TileSetDev ts;
+  const unsigned* code;
+  const int* invpad;
+  const double* dvec;        // substitution results (local slices, coarse at vbase[P])
+  double* x;
+  double* r;
+  double* z;
+  double* p[2];              // p of even / odd iterations
+  double* q;
+  double* g0;
+  PcgScalars* sc;
+  double* part;              // [2 phases][nblocks][2] block partials
+  ReduceWs ws;               // last-block reduction of the third phase
+  unsigned* bar;             // grid barrier: arrival count, generation
+  const int* range;          // [nblocks + 1]
+  ErrWord* err;
+  int mode;                  // 0 two-level, 1 one level, 2 coarse only
+  int nblocks;
+};
+// CTAs one cooperative launch of the fused kernel can keep resident (0 on error).
+int fused_pcg_blocks(int d);
+int launch_fused_pcg(const FusedPcg& a, cudaStream_t s);
 void launch_init_pcg(int n, const double* b, double* x, double* r, PcgScalars* sc, ReduceWs ws,
                      double rtol, int flexible, cudaStream_t s);
 void launch_energy(int n, const double* x, const double* r, PcgScalars* sc, ReduceWs ws,
@@ -359,7 +391,8 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 // trailing update of step k factors diagonal tile k+1 once its last update is in.
 void factor_tiles(const TileSetDev& ts, int mat0, int nmat, int max_nt, const int* col_max,
                   void* tiles, Store st, int* diag_cnt, ErrWord* err, cudaStream_t s,
-                  LaunchHook* hook, int split = 1, bool tensor_cores = false);
+                  LaunchHook* hook, int split = 1, bool tensor_cores = false,
+                  bool bf16_operands = false);
 // Substitution form of the factors of matrices [mat0, mat0+nmat) (after
 // factor_tiles, same precision): every stored off-diagonal tile L_IK becomes
 // Lh_IK = L_IK L_KK^{-1} in place, ut receives Lh_IK^T in the same slot and

@@ -10,6 +10,8 @@
 // the reductions cost as much as the element arithmetic unless every thread
 // first accumulates several elements: kernels that reduce run on at most two
 // blocks per SM (about four elements per thread).
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace sfcdd {
@@ -547,6 +549,290 @@ void launch_grad(const GridDev& g, const unsigned* code, const int* invpad, cons
     case 7: k_grad<7><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
     default: k_grad<8><<<nb, VB, 0, s>>>(g, code, invpad, lam, u, sc, ws); break;
   }
+}
+
+// ---------------------------------------------------------------------------
+// The vector phase of one PCG iteration as one cooperative launch.  Between
+// the backward substitution of iteration k and the forward substitution of
+// iteration k + 1 the iteration needs, in order: the prolongation z (eq. addSW)
+// with r^T z (beta), p = z + beta p with q = A p (alpha), the x / r update with
+// ||r|| (convergence), and the coarse restriction R_0 r (eq. restr) of the next
+// preconditioner apply.  As separate launches these are five kernels whose
+// time goes to latency (dependent gathers, reductions through the last CTA),
+// not to bytes or FP64 work; here every CTA owns a fixed range of curve
+// positions through all three phases and the two scalars a later phase needs
+// (beta, alpha) are exchanged through two grid barriers.  Every CTA sums the
+// block partials itself, in the same fixed order, so all of them obtain
+// bit-identical scalars without a second barrier; CTA 0 publishes them.
+// The stencil reads p_new = z + beta p_old at the neighbours on the fly (z is
+// complete after the first barrier), so p needs no barrier of its own: p of
+// the previous iteration stays in one buffer and the new p goes to the other.
+namespace {
+
+constexpr int FB_THREADS = 256;
+constexpr long long BAR_SPIN_LIMIT = 1ll << 24;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident): arrival count
+// and a generation word; the generation is read before arriving, so a waiter
+// cannot miss the release.  Bounded: a timeout records TIMEOUT (site 30) and
+// lets the CTA go on, so the launch always ends.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, ErrWord* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acquire_u32(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (ld_acquire_u32(bar + 1) == gen) {
+        if (++it > 64) __nanosleep(32);
+        if (it > BAR_SPIN_LIMIT) {
+          if (atomicCAS(&err->code, 0, (int)SFCDD_ERR_TIMEOUT) == 0) err->index = 30;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Block sum of two values (every thread passes its pair; thread 0 gets totals).
+__device__ __forceinline__ void block_sum2(double& a, double& b, double (*sh)[FB_THREADS / 32]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool hi = (lane & 16) != 0;
+  double t = (hi ? b : a) + __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+  for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((lane & 15) == 0) sh[lane >> 4][w] = t;
+  __syncthreads();
+  if (w == 0) {
+    const int k = lane >> 3, u = lane & 7;
+    double v = k < 2 ? sh[k][u] : 0.0;
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    a = __shfl_sync(0xffffffffu, v, 0);
+    b = __shfl_sync(0xffffffffu, v, 8);
+  }
+}
+
+// Totals of the two block partials of a phase over all CTAs, summed by warp 0
+// of every CTA in the same order (bit-identical in every CTA); broadcast to
+// the CTA through shared memory.
+__device__ __forceinline__ void grid_totals(const double* part, int nblocks, double* out2) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
+      s0 += __ldcg(&part[2 * b]);
+      s1 += __ldcg(&part[2 * b + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+      out2[0] = s0;
+      out2[1] = s1;
+    }
+  }
+  __syncthreads();
+}
+
+template <int D>
+__global__ void __launch_bounds__(FB_THREADS) k_pcg_fused(FusedPcg a) {
+  __shared__ double sh[2][FB_THREADS / 32];
+  __shared__ double tot[2];
+  PcgScalars* sc = a.sc;
+  // scalars of the previous iteration, read before anything is published
+  if (sc->done) return;  // uniform: nothing writes done before the last phase
+  const int iter = sc->iter;
+  const double rz_prev = sc->rz;
+  const int flexible = sc->flexible;
+  const int c = blockIdx.x;
+  const int lo = a.range[c], hi = a.range[c + 1];
+  const double* pold = a.p[iter & 1];
+  double* pnew = a.p[(iter + 1) & 1];
+
+  // phase 1: z = C^{-1} r from the substitution results, r^T z and r^T z_old
+  double acc0 = 0.0, acc1 = 0.0;
+  {
+    const int coarse_base = a.mode != 1 ? __ldg(&a.ts.vbase[a.pd.P]) : 0;
+    auto lvbase = [&](int i) { return __ldg(&a.ts.vbase[i]); };
+    for (int p = lo + threadIdx.x; p < hi; p += FB_THREADS) {
+      const double v = prolong_point(a.pd, a.mode, a.dvec, coarse_base, lvbase, a.ts.linv, p);
+      const double rp = a.r[p];
+      acc0 += rp * v;
+      acc1 += rp * a.z[p];
+      a.z[p] = v;
+    }
+  }
+  block_sum2(acc0, acc1, sh);
+  if (threadIdx.x == 0) {
+    a.part[2 * c] = acc0;
+    a.part[2 * c + 1] = acc1;
+  }
+  grid_barrier(a.bar, (unsigned)a.nblocks, a.err);
+  grid_totals(a.part, a.nblocks, tot);
+  const double rz = tot[0], rz_oldz = tot[1];
+  const double beta = iter == 0 ? 0.0 : (flexible ? (rz - rz_oldz) / rz_prev : rz / rz_prev);
+  if (c == 0 && threadIdx.x == 0) {
+    sc->beta = beta;
+    sc->rz_old = rz_oldz;
+    sc->rz = rz;
+    if (sc->hist_beta && iter >= 1 && iter - 1 < sc->hist_cap) sc->hist_beta[iter - 1] = beta;
+  }
+
+  // phase 2: p_new = z + beta p_old (neighbours on the fly), q = A p_new, p^T q
+  double pq = 0.0;
+  for (int p = lo + threadIdx.x; p < hi; p += FB_THREADS) {
+    const unsigned cd = __ldg(&a.code[p]);
+    // z was written by other CTAs of this launch: read it through L2 (__ldcg)
+    const double pc = __ldcg(&a.z[p]) + beta * pold[p];
+    double v = a.g.diag * pc;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const unsigned kj = (cd >> a.g.off[j]) & ((1u << a.g.lev[j]) - 1u);
+      const unsigned unit = 1u << a.g.off[j];
+      if (kj > 1u) {
+        const int n = __ldg(&a.invpad[cd - unit]);
+        v -= a.g.w[j] * (__ldcg(&a.z[n]) + beta * pold[n]);
+      }
+      if (kj < (unsigned)a.g.size[j]) {
+        const int n = __ldg(&a.invpad[cd + unit]);
+        v -= a.g.w[j] * (__ldcg(&a.z[n]) + beta * pold[n]);
+      }
+    }
+    pnew[p] = pc;
+    a.q[p] = v;
+    pq += pc * v;
+  }
+  double dummy = 0.0;
+  block_sum2(pq, dummy, sh);
+  if (threadIdx.x == 0) {
+    a.part[2 * (a.nblocks + c)] = pq;
+    a.part[2 * (a.nblocks + c) + 1] = 0.0;
+  }
+  grid_barrier(a.bar, (unsigned)a.nblocks, a.err);
+  grid_totals(a.part + 2 * a.nblocks, a.nblocks, tot);
+  const double pq_tot = tot[0];
+  const double alpha = rz / pq_tot;
+  if (c == 0 && threadIdx.x == 0) {
+    sc->pq = pq_tot;
+    sc->alpha = alpha;
+    if (sc->hist_alpha && iter < sc->hist_cap) sc->hist_alpha[iter] = alpha;
+  }
+
+  // phase 3: x += alpha p, r -= alpha q, ||r||^2 and x^T r (energy); then the
+  // coarse restriction of the new r over this CTA's whole coarse blocks
+  double rr = 0.0, xr = 0.0;
+  for (int p = lo + threadIdx.x; p < hi; p += FB_THREADS) {
+    const double xi = a.x[p] + alpha * pnew[p];
+    a.x[p] = xi;
+    const double ri = a.r[p] - alpha * a.q[p];
+    a.r[p] = ri;
+    rr += ri * ri;
+    xr += xi * ri;
+  }
+  if (a.mode != 1) {
+    __syncthreads();  // r of the CTA's range written
+    const int N0 = a.pd.q * a.pd.P;
+    const int b0 = coarse_block_of(a.pd, lo);
+    const int b1 = hi >= a.pd.N ? N0 : coarse_block_of(a.pd, hi);
+    const int l = threadIdx.x & (RL - 1);
+    for (int bb = b0 + (int)threadIdx.x / RL; bb - (int)threadIdx.x / RL < b1;
+         bb += FB_THREADS / RL) {
+      double s = 0.0;
+      const bool valid = bb < b1;
+      if (valid) {
+        int st, sz;
+        coarse_block_range(a.pd, bb, st, sz);
+        for (int k = l; k < sz; k += RL) s += a.r[st + k];
+      }
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (valid && l == 0) a.g0[bb] = s;
+    }
+  }
+  double vv[2] = {rr, xr};
+  reduce_finalize<2>(vv, a.ws, [&](double* t) {
+    sc->rr = t[0];
+    const double rel = sc->energy ? sqrt(fmax(-t[1], 0.0) / sc->esq0) : sqrt(t[0] / sc->bb);
+    sc->rel = rel;
+    sc->iter = iter + 1;
+    if (!(rel == rel) || isinf(rel) || !(alpha == alpha) || isinf(alpha)) {
+      sc->status = SFCDD_ERR_NAN;
+      sc->done = 1;
+    } else if (rel <= sc->rtol) {
+      sc->done = 1;
+    }
+  });
+}
+
+template <int D>
+int fused_blocks_d() {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_fused<D>, FB_THREADS, 0) !=
+      cudaSuccess)
+    return 0;
+  return sms * std::min(occ, 2);
+}
+
+template <int D>
+cudaError_t launch_fused_d(const FusedPcg& a, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)a.nblocks);
+  cfg.blockDim = dim3(FB_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg_fused<D>, a);
+}
+
+}  // namespace
+
+int fused_pcg_blocks(int d) {
+  switch (d) {
+    case 1: return fused_blocks_d<1>();
+    case 2: return fused_blocks_d<2>();
+    case 3: return fused_blocks_d<3>();
+    case 4: return fused_blocks_d<4>();
+    case 5: return fused_blocks_d<5>();
+    case 6: return fused_blocks_d<6>();
+    case 7: return fused_blocks_d<7>();
+    default: return fused_blocks_d<8>();
+  }
+}
+
+int launch_fused_pcg(const FusedPcg& a, cudaStream_t s) {
+  cudaError_t e;
+  switch (a.g.d) {
+    case 1: e = launch_fused_d<1>(a, s); break;
+    case 2: e = launch_fused_d<2>(a, s); break;
+    case 3: e = launch_fused_d<3>(a, s); break;
+    case 4: e = launch_fused_d<4>(a, s); break;
+    case 5: e = launch_fused_d<5>(a, s); break;
+    case 6: e = launch_fused_d<6>(a, s); break;
+    case 7: e = launch_fused_d<7>(a, s); break;
+    default: e = launch_fused_d<8>(a, s); break;
+  }
+  return e == cudaSuccess ? 0 : cuda_fail(e, "cooperative launch of k_pcg_fused", __FILE__, __LINE__);
 }
 
 }  // namespace sfcdd
