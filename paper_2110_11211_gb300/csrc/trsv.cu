@@ -111,6 +111,23 @@ __device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned pari
     }
   }
 }
+// Factor tiles are read once per substitution and stream through L2: their
+// bulk copies carry an evict-first policy, so that they do not push the PCG
+// vectors, the result slots and the index maps (tens of MB, reused every
+// iteration) out of L2.
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void factor_copy(void* dst, const void* src, unsigned bytes,
+                                            unsigned long long* bar, unsigned long long pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes,
                                           unsigned long long* bar) {
   asm volatile(
@@ -273,6 +290,7 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
     // producer warp: every lane waits for the stage; lane 0 (or, for half
     // tiles, the lanes row by row) issues the copies
     const int pl = threadIdx.x - PROD0;
+    const unsigned long long pol = evict_first_policy();
     for (int t = 0; t < ntile; ++t) {
       const int s = t % NS, k = t / NS;
       if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 10);
@@ -295,14 +313,15 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
       if (sizeof(T) < 8 || !half_tile(t)) {
         if (pl == 0) {
           mbar_expect_tx(&sm.full[s], bytes);
-          bulk_copy(dst, src, bytes, &sm.full[s]);
+          factor_copy(dst, src, bytes, &sm.full[s], pol);
         }
       } else {
         constexpr unsigned HB = TILE / 2 * sizeof(T);  // 16-byte multiple for every T
         if (pl == 0) mbar_expect_tx(&sm.full[s], R * HB);
         __syncwarp();
         for (int j = pl; j < R; j += 32)
-          bulk_copy(dst + (size_t)j * TILE * sizeof(T), src + (long long)j * TILE, HB, &sm.full[s]);
+          factor_copy(dst + (size_t)j * TILE * sizeof(T), src + (long long)j * TILE, HB, &sm.full[s],
+                      pol);
       }
     }
     return;
@@ -498,6 +517,7 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
   if (threadIdx.x >= PROD0) {
     // producer warp: the pieces in consumption order
     const int pl = threadIdx.x - PROD0;
+    const unsigned long long pol = evict_first_policy();
     int t = 0;
     auto put = [&](const T* src, unsigned bytes, bool half) {
       const int s = t % NS, k = t / NS;
@@ -506,13 +526,13 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
       if (!half) {
         if (pl == 0) {
           mbar_expect_tx(&sm.full[s], bytes);
-          bulk_copy(dst, src, bytes, &sm.full[s]);
+          factor_copy(dst, src, bytes, &sm.full[s], pol);
         }
       } else {
         if (pl == 0) mbar_expect_tx(&sm.full[s], TILE * HB);
         __syncwarp();
         for (int j = pl; j < TILE; j += 32)
-          bulk_copy(dst + (size_t)j * HB, src + (long long)j * TILE, HB, &sm.full[s]);
+          factor_copy(dst + (size_t)j * HB, src + (long long)j * TILE, HB, &sm.full[s], pol);
       }
       ++t;
     };
