@@ -1280,8 +1280,10 @@ int pcg_impl(sfcdd_handle* h, double rtol, int maxit, sfcdd_stats* stats,
   SFCDD_CUDA_OK(cudaMemsetAsync(h->p, 0, (size_t)h->N * sizeof(double), s));
   SFCDD_CUDA_OK(cudaMemsetAsync(h->z, 0, (size_t)h->N * sizeof(double), s));
   if (h->fused) {
-    // every iteration is {substitutions, vector phase}: the first needs R_0 r_0
+    // every iteration is {substitutions, vector phase}: the first needs R_0 r_0;
+    // the vector phase's barrier counts arrivals from the start of the solve
     SFCDD_CUDA_OK(cudaMemsetAsync(h->p2, 0, (size_t)h->N * sizeof(double), s));
+    SFCDD_CUDA_OK(cudaMemsetAsync(h->fz.bar, 0, 2 * sizeof(unsigned), s));
     if (h->variant != SFCDD_ONE_LEVEL)
       pf.run(SFCDD_K_RESTRICT, [&] { launch_restrict(h->pd, h->r, h->g0, h->sc, s); });
   } else {

@@ -336,7 +336,7 @@ struct FusedPcg {
   PcgScalars* sc;
   double* part;              // [2 phases][nblocks][2] block partials
   ReduceWs ws;               // last-block reduction of the third phase
-  unsigned* bar;             // grid barrier: arrival count, generation
+  unsigned* bar;             // grid barrier: arrivals since the solve started
   const int* range;          // [nblocks + 1]
   ErrWord* err;
   int mode;                  // 0 two-level, 1 one level, 2 coarse only

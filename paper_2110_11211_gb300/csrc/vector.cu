@@ -578,30 +578,25 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs resident): arrival count
-// and a generation word; the generation is read before arriving, so a waiter
-// cannot miss the release.  Bounded: a timeout records TIMEOUT (site 30) and
-// lets the CTA go on, so the launch always ends.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, ErrWord* err) {
+// Grid-wide barrier of a cooperative launch (all CTAs resident).  One arrival
+// counter that only grows during a solve (reset when the solve starts): the
+// b-th barrier of iteration `iter` releases once the counter reaches
+// (2 iter + b + 1) nblocks, so arriving is one fire-and-forget release add and
+// waiting one acquire poll, with no reset on the critical path.  Bounded: a
+// timeout records TIMEOUT (site 30) and lets the CTA go on, so the launch
+// always ends.
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned target, ErrWord* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned gen = ld_acquire_u32(bar + 1);
-    __threadfence();
-    if (atomicAdd(bar, 1u) == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long it = 0;
-      while (ld_acquire_u32(bar + 1) == gen) {
-        if (++it > 64) __nanosleep(32);
-        if (it > BAR_SPIN_LIMIT) {
-          if (atomicCAS(&err->code, 0, (int)SFCDD_ERR_TIMEOUT) == 0) err->index = 30;
-          break;
-        }
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    long long it = 0;
+    while ((int)(ld_acquire_u32(count) - target) < 0) {
+      if (++it > 256) __nanosleep(20);
+      if (it > BAR_SPIN_LIMIT) {
+        if (atomicCAS(&err->code, 0, (int)SFCDD_ERR_TIMEOUT) == 0) err->index = 30;
+        break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
@@ -681,7 +676,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_pcg_fused(FusedPcg a) {
     a.part[2 * c] = acc0;
     a.part[2 * c + 1] = acc1;
   }
-  grid_barrier(a.bar, (unsigned)a.nblocks, a.err);
+  grid_barrier(a.bar, (unsigned)(2 * iter + 1) * (unsigned)a.nblocks, a.err);
   grid_totals(a.part, a.nblocks, tot);
   const double rz = tot[0], rz_oldz = tot[1];
   const double beta = iter == 0 ? 0.0 : (flexible ? (rz - rz_oldz) / rz_prev : rz / rz_prev);
@@ -722,7 +717,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_pcg_fused(FusedPcg a) {
     a.part[2 * (a.nblocks + c)] = pq;
     a.part[2 * (a.nblocks + c) + 1] = 0.0;
   }
-  grid_barrier(a.bar, (unsigned)a.nblocks, a.err);
+  grid_barrier(a.bar, (unsigned)(2 * iter + 2) * (unsigned)a.nblocks, a.err);
   grid_totals(a.part + 2 * a.nblocks, a.nblocks, tot);
   const double pq_tot = tot[0];
   const double alpha = rz / pq_tot;
