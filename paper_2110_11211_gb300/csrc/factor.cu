@@ -192,8 +192,22 @@ __device__ __forceinline__ void tri_rc(int e, int& i, int& l) {
 // The whole factorization + inversion of the tile at tp by one CTA (FB threads),
 // in dsm (2 (TILE + 1)^2 elements of T).  The tile is read through L2, so it
 // may have been written by other CTAs of the same launch (after a fence).
+// rows: the tile's rows inside the matrix (the last tile of a matrix whose
+// size is not a multiple of TILE); the rows beyond are identity padding with
+// zero couplings, so their 16-column blocks are the identity in L and in
+// L^{-1}, and only the blocks holding matrix rows are factored.
 template <class T>
-__device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m) {
+__device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m,
+                           int rows = TILE);
+
+// Rows of matrix m inside its diagonal tile k.
+__device__ __forceinline__ int tile_rows(const TileSetDev& ts, int m, int k) {
+  return min(TILE, ts.n[m] - k * TILE);
+}
+
+template <class T>
+__device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m,
+                           int rows) {
   T (*L)[TILE + 1] = reinterpret_cast<T (*)[TILE + 1]>(dsm);
   T (*X)[TILE + 1] = L + TILE;
   T* rinv = &X[TILE][0];  // TILE reciprocal pivots (row TILE of X, TILE + 1 entries)
@@ -207,7 +221,9 @@ __device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err,
     if (tid + 128 < PB * (PB + 1) / 2) tri_rc(tid + 128, di1, dl1);
   }
   __syncthreads();
-  for (int b = 0; b < PNB; ++b) {
+  const int nbr = rows >= TILE ? PNB : (rows + PB - 1) / PB;  // blocks with matrix rows
+  const int rtop = PB * nbr;
+  for (int b = 0; b < nbr; ++b) {
     const int o = PB * b;
     if (tid < 128) {
       // factor D_b in place (column scaling deferred): d_c -> rinv, trailing update
@@ -242,7 +258,7 @@ __device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err,
       }
     }
     __syncthreads();
-    const int o2 = o + PB, rest = TILE - o2;  // rows below the block
+    const int o2 = o + PB, rest = rtop - o2;  // matrix rows below the block
     if (rest > 0) {
       // panel L_pc = sum_{k <= c} A_pk X_ck  (D^{-T} is X^T), written after all reads
       T pv[3];
@@ -272,8 +288,8 @@ __device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err,
   }
   // off-diagonal blocks of X by diagonals d = a - b; S_ab is staged in the
   // (zero) upper block (b, a) of X
-  for (int d = 1; d < PNB; ++d) {
-    const int nblk = PNB - d;
+  for (int d = 1; d < nbr; ++d) {
+    const int nblk = nbr - d;
     for (int e = tid; e < nblk * PB * PB; e += FB) {
       const int bb = e / (PB * PB), a = bb + d;
       const int i = (e / PB) % PB, j = e % PB;
@@ -294,7 +310,7 @@ __device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err,
   }
   for (int e = tid; e < TILE2; e += FB) {
     const int r = e / TILE, c = e % TILE;
-    tp[e] = c > r ? T(0) : X[r][c];
+    tp[e] = c > r ? T(0) : (r >= rtop ? (r == c ? T(1) : T(0)) : X[r][c]);
   }
 }
 
@@ -316,7 +332,7 @@ __global__ void __launch_bounds__(FB) k_potrf(TileSetDev ts, int mat0, int k, T*
   const int m = mat0 + blockIdx.x;
   if (ts.nt[m] <= k) return;
   const int fb = ts.vbase[m] / TILE;
-  potrf_tile<T>(tiles + tile_at(ts, ts.tbase[m], fb, k, k), dsm_potrf, err, m);
+  potrf_tile<T>(tiles + tile_at(ts, ts.tbase[m], fb, k, k), dsm_potrf, err, m, tile_rows(ts, m, k));
 }
 
 // C = X * Y^T on 64x64 tiles (X, Y row-major in global), each thread a 4x4 block.
@@ -452,7 +468,8 @@ __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int nmat, 
   if ((int)blockIdx.x == (int)gridDim.x - 1) {
     // column k does not reach row k+1: tile (k+1, k+1) is final already
     if (k + 1 < nt && ts.kmin[fb + k + 1] > k)
-      potrf_tile<T>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_syrk, err, m);
+      potrf_tile<T>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_syrk, err, m,
+                    tile_rows(ts, m, k + 1));
     return;
   }
   const int tix = blockIdx.x / SPLIT, slab = blockIdx.x % SPLIT;
@@ -485,7 +502,7 @@ __global__ void __launch_bounds__(FB) k_syrk(TileSetDev ts, int mat0, int nmat, 
     __syncthreads();
     if (s_last) {
       __threadfence();
-      potrf_tile<T>(aij, dsm_syrk, err, m);
+      potrf_tile<T>(aij, dsm_syrk, err, m, tile_rows(ts, m, k + 1));
     }
   }
 }
@@ -649,7 +666,8 @@ __global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int nma
   const long long tb = ts.tbase[m];
   if ((int)blockIdx.x == (int)gridDim.x - 1) {
     if (k + 1 < nt && ts.kmin[fb + k + 1] > k)
-      potrf_tile<float>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_tc, err, m);
+      potrf_tile<float>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_tc, err, m,
+                        tile_rows(ts, m, k + 1));
     return;
   }
   const int jj = (int)blockIdx.x / pmax, p = (int)blockIdx.x % pmax;
@@ -683,7 +701,7 @@ __global__ void __launch_bounds__(FB) k_syrk_tc(TileSetDev ts, int mat0, int nma
   if (ok && i0 == k + 1 && j == k + 1) {
     __threadfence();
     __syncthreads();  // the whole tile is written
-    potrf_tile<float>(d0, dsm_tc, err, m);
+    potrf_tile<float>(d0, dsm_tc, err, m, tile_rows(ts, m, k + 1));
   }
 }
 
@@ -809,7 +827,8 @@ __global__ void __launch_bounds__(FB) k_syrk_oz(TileSetDev ts, int mat0, int nma
   const long long tb = ts.tbase[m];
   if ((int)blockIdx.x == (int)gridDim.x - 1) {
     if (k + 1 < nt && ts.kmin[fb + k + 1] > k)
-      potrf_tile<double>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_oz, err, m);
+      potrf_tile<double>(tiles + tile_at(ts, tb, fb, k + 1, k + 1), dsm_oz, err, m,
+                         tile_rows(ts, m, k + 1));
     return;
   }
   const int jj = (int)blockIdx.x / pmax, p = (int)blockIdx.x % pmax;
@@ -830,7 +849,7 @@ __global__ void __launch_bounds__(FB) k_syrk_oz(TileSetDev ts, int mat0, int nma
   if (ok && i0 == k + 1 && j == k + 1) {
     __threadfence();
     __syncthreads();  // the whole tile is written
-    potrf_tile<double>(d0, dsm_oz, err, m);
+    potrf_tile<double>(d0, dsm_oz, err, m, tile_rows(ts, m, k + 1));
   }
 }
 
