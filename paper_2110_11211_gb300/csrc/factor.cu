@@ -979,9 +979,10 @@ __device__ __forceinline__ void load_plain(T (*dst)[TILE + 4], const T* __restri
 // acc[i][j] = sum_{s >= s0} Xt[s][r0 + i] Yt[s][c0 + j]
 template <class T>
 __device__ __forceinline__ void mma_4x4_from(T (&acc)[4][4], T (*Xt)[TILE + 4],
-                                             T (*Yt)[TILE + 4], int r0, int c0, int s0) {
+                                             T (*Yt)[TILE + 4], int r0, int c0, int s0,
+                                             int s1 = TILE) {
 #pragma unroll 4
-  for (int s = s0; s < TILE; ++s) {
+  for (int s = s0; s < s1; ++s) {
     T xv[4], yv[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -1032,7 +1033,17 @@ __global__ void __launch_bounds__(FB) k_unitize(TileSetDev ts, int mat0, int nma
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  mma_4x4_from<T>(acc, Xt, I == K ? Xt : Yt, r0, c0, s0);
+  // a matrix's last tile row / column may hold fewer than TILE rows: the padding
+  // is zero in L_IK and the identity in X_K, so only the inner index s < mK
+  // contributes, and warps whose columns lie in the padding have nothing to do
+  const int mK = tile_rows(ts, m, K);
+  if (s0 < mK) mma_4x4_from<T>(acc, Xt, I == K ? Xt : Yt, r0, c0, s0, mK);
+  if (I == K)  // E_K = X_K^T X_K is the identity on the padding
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (r0 + a == c0 + b && r0 + a >= mK) acc[a][b] = T(1);
   __syncthreads();
   // stage the result (rows in Xt) and its transpose (rows in Yt), then copy out
 #pragma unroll
