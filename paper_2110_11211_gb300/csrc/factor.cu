@@ -162,20 +162,25 @@ void launch_assemble_coarse(const GridDev& g, const PartDev& pd, const unsigned*
 // ---------------------------------------------------------------------------
 // Factorization kernels, compute type T (double or float), storage T.
 
-// Diagonal tile k of every matrix with nt > k: Cholesky in shared memory, then
-// the inverse of the lower-triangular factor block replaces the tile.
-// Blocked right-looking Cholesky with 16-column blocks.  FP64 instructions are
-// slow on this part (a warp instruction occupies a sub-partition's FP64 unit
-// for tens of cycles, masked lanes included), so the dependent work is kept
-// small and the bulk runs as dense 16-wide products on all eight warps:
-//   per block b: warps 0-3 factor the 16 x 16 diagonal block D_b (one element
-//   of its triangle per thread, reciprocal pivots, scaling applied once at the
-//   end) and invert it into X (row by row, 8 threads per dot product); then
-//   all warps form the panel L_pb = A_pb D_b^{-T} and update the trailing
-//   triangle with it.
-// The off-diagonal 16 x 16 blocks of X = L^{-1} follow by diagonals:
-// X_ab = -X_aa sum_{k=b}^{a-1} L_ak X_kb.
-constexpr int PB = 16;           // column block
+// Diagonal tile k of every matrix with nt > k: Cholesky of the tile, then the
+// inverse of its lower-triangular factor replaces it.  Two algorithms, one per
+// compute type, chosen by what bounds each on this part:
+//   FP64 (potrf_tile_column): a warp's FP64 instruction occupies its
+//   sub-partition's FP64 unit for about 64 cycles whatever its predicate, so
+//   the work is laid out for few issued FP64 instructions and a short
+//   dependent chain: the factorization and the inverse advance together one
+//   column per iteration, every entry of the lower triangle held in one
+//   thread's registers, and an instruction issues only where some lane of the
+//   warp still has a live entry.
+//   FP32 (potrf_tile_blocked): FP32 issue is cheap and the blocked algorithm's
+//   16-wide products keep all eight warps busy with fewer barriers.
+// Both read the tile through L2 (it may have been written by other CTAs of the
+// same launch, after a fence) and use dsm, 2 (TILE + 1)^2 elements of T.
+// rows: the tile's rows inside the matrix (the last tile of a matrix whose size
+// is not a multiple of TILE); the rows beyond are identity padding with zero
+// couplings, the identity in L and in L^{-1}, so only the matrix rows are
+// factored.
+constexpr int PB = 16;           // column block of the blocked algorithm
 constexpr int PNB = TILE / PB;   // blocks per tile
 
 __device__ __forceinline__ void potrf_bar128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
@@ -189,13 +194,6 @@ __device__ __forceinline__ void tri_rc(int e, int& i, int& l) {
   l = e - t * (t + 1) / 2;
 }
 
-// The whole factorization + inversion of the tile at tp by one CTA (FB threads),
-// in dsm (2 (TILE + 1)^2 elements of T).  The tile is read through L2, so it
-// may have been written by other CTAs of the same launch (after a fence).
-// rows: the tile's rows inside the matrix (the last tile of a matrix whose
-// size is not a multiple of TILE); the rows beyond are identity padding with
-// zero couplings, so their 16-column blocks are the identity in L and in
-// L^{-1}, and only the blocks holding matrix rows are factored.
 template <class T>
 __device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m,
                            int rows = TILE);
@@ -205,9 +203,29 @@ __device__ __forceinline__ int tile_rows(const TileSetDev& ts, int m, int k) {
   return min(TILE, ts.n[m] - k * TILE);
 }
 
+// A non-positive pivot marks matrix m not SPD (first error wins) and continues
+// with 1 so that the kernel finishes; returns 1 / sqrt(pivot).
 template <class T>
-__device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m,
-                           int rows) {
+__device__ __forceinline__ T pivot_rsqrt(T d, ErrWord* err, int m) {
+  if (!(d > T(0))) {
+    if (atomicCAS(&err->code, 0, (int)SFCDD_ERR_NOT_SPD) == 0) err->index = m;
+    d = T(1);
+  }
+  return rsqrt(d);
+}
+
+// Blocked right-looking Cholesky with 16-column blocks:
+//   per block b: warps 0-3 factor the 16 x 16 diagonal block D_b (one element
+//   of its triangle per thread, reciprocal pivots, scaling applied once at the
+//   end) and invert it into X (row by row, 8 threads per dot product); then
+//   all warps form the panel L_pb = A_pb D_b^{-T} and update the trailing
+//   triangle with it.
+// The off-diagonal 16 x 16 blocks of X = L^{-1} follow by diagonals:
+// X_ab = -X_aa sum_{k=b}^{a-1} L_ak X_kb.  Padding rows fill whole 16-column
+// blocks, which are left out.
+template <class T>
+__device__ void potrf_tile_blocked(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m,
+                                   int rows) {
   T (*L)[TILE + 1] = reinterpret_cast<T (*)[TILE + 1]>(dsm);
   T (*X)[TILE + 1] = L + TILE;
   T* rinv = &X[TILE][0];  // TILE reciprocal pivots (row TILE of X, TILE + 1 entries)
@@ -312,6 +330,122 @@ __device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err,
     const int r = e / TILE, c = e % TILE;
     tp[e] = c > r ? T(0) : (r >= rtop ? (r == c ? T(1) : T(0)) : X[r][c]);
   }
+}
+
+// Right-looking Cholesky fused with the row-oriented inverse X = L^{-1}, one
+// column per iteration k.  Warp 0 owns the diagonal, takes the pivots'
+// reciprocal square roots and scales what is published; warps 1-7 own the
+// 2016 entries below the diagonal, 9 each, in registers.  An entry is L(i, j)
+// until column j is final and from then on Y(i, j), the open part of row i of
+// X, which starts at zero (Y starts as the identity).  Iteration k:
+//   A (warp 0): r_k = 1 / sqrt(pivot k); L(i, k) = raw(i, k) r_k for i > k and
+//      X(k, j) = Y(k, j) r_k for j < k, X(k, k) = r_k, into shared memory; row
+//      k of X is final and goes to the tile.
+//   B (all): L(i, j) -= L(i, k) L(j, k) for k < j <= i and
+//      Y(i, j) -= L(i, k) X(k, j) for j <= k < i; the entries that become
+//      column k + 1 or row k + 1 publish their raw values; warp 0 finishes
+//      pivot k + 1 and inverts it.
+// A slot is skipped by the whole warp when none of its lanes holds a live
+// entry (rows above k or in the padding), which saves the FP64 issue of the
+// triangle's shrinking part; the scaling costs one multiplication per
+// published value.
+template <class T>
+__device__ void potrf_tile_column(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m,
+                                  int rows) {
+  constexpr int NE = FB - 32;                                // threads owning entries
+  constexpr int NS = (TILE * (TILE - 1) / 2 + NE - 1) / NE;  // entries per thread
+  T* colbuf = reinterpret_cast<T*>(dsm);  // L(:, k), scaled
+  T* rowbuf = colbuf + TILE;              // X(k, :)
+  T* colraw = rowbuf + TILE;              // L(:, k + 1) before scaling
+  T* rowraw = colraw + TILE;              // Y(k + 1, :) before scaling
+  T* rinv = rowraw + TILE;                // reciprocal pivots
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int n = rows < TILE ? rows : TILE;  // matrix rows; the rest is identity padding
+  T v[NS];
+  int ii[NS], jj[NS];
+  T dg[2] = {T(0), T(0)};
+  if (w == 0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      dg[h] = __ldcg(tp + i * TILE + i);
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int e = tid - 32 + NE * s;
+      if (e < TILE * (TILE - 1) / 2) {
+        int a, b;
+        tri_rc(e, a, b);  // strictly lower entry: row a + 1, column b
+        ii[s] = a + 1;
+        jj[s] = b;
+        v[s] = __ldcg(tp + ii[s] * TILE + jj[s]);
+        if (jj[s] == 0 && ii[s] < n) colraw[ii[s]] = v[s];  // column 0 is final as loaded
+      } else {
+        ii[s] = 0;  // no entry: never live
+        jj[s] = 0;
+        v[s] = T(0);
+      }
+    }
+  }
+  __syncthreads();  // every entry is in registers: the tile may be overwritten
+  if (tid == 0) rinv[0] = pivot_rsqrt(dg[0], err, m);
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (w == 0) {
+      const T r = rinv[k];
+      for (int i = k + 1 + lane; i < n; i += 32) colbuf[i] = colraw[i] * r;
+      for (int j = lane; j < k; j += 32) {
+        const T x = rowraw[j] * r;
+        rowbuf[j] = x;
+        tp[k * TILE + j] = x;
+      }
+      if (lane == 0) {
+        rowbuf[k] = r;
+        tp[k * TILE + k] = r;
+      }
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        const bool live = i > k && i < n;
+        if (__any_sync(0xffffffffu, live) && live) {
+          const T l = colbuf[i];
+          dg[h] -= l * l;
+          if (i == k + 1) rinv[k + 1] = pivot_rsqrt(dg[h], err, m);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const int i = ii[s], j = jj[s];
+        const bool live = i > k && i < n;
+        if (__any_sync(0xffffffffu, live) && live) {
+          // L(i, j) while j > k; at j == k it turns into Y(i, k) = 0 - L(i, k) X(k, k)
+          const T b = j > k ? colbuf[j] : rowbuf[j];
+          const T base = j == k ? T(0) : v[s];
+          v[s] = base - colbuf[i] * b;
+          if (j == k + 1) colraw[i] = v[s];       // column k + 1 is final
+          else if (i == k + 1) rowraw[j] = v[s];  // row k + 1 of Y is final
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // above the diagonal zeros, the padding rows the identity
+  for (int e = tid; e < TILE2; e += FB) {
+    const int rr = e / TILE, c = e % TILE;
+    if (c > rr) tp[e] = T(0);
+    else if (rr >= n) tp[e] = rr == c ? T(1) : T(0);
+  }
+}
+
+template <class T>
+__device__ void potrf_tile(T* __restrict__ tp, unsigned char* dsm, ErrWord* err, int m, int rows) {
+  if constexpr (sizeof(T) == 8) potrf_tile_column<T>(tp, dsm, err, m, rows);
+  else potrf_tile_blocked<T>(tp, dsm, err, m, rows);
 }
 
 __global__ void __launch_bounds__(FB) k_potrf_one(double* tile, ErrWord* err, int m) {
@@ -787,10 +921,14 @@ __device__ __forceinline__ void oz_emit(const unsigned char* dsm, uint32_t tmem,
   }
 }
 
+// The FP64 tile-product kernels hold one CTA per SM (their shared memory and
+// the whole TMEM), so they take the SM's register budget: __launch_bounds__
+// with one block per SM keeps the fused diagonal factorization out of local
+// memory.
 // Panel L_ik = A_ik Linv_kk^T in FP64, two stored tiles of column k per CTA.
 // grid = (ceil(max panel rows / 2), nmat)
-__global__ void __launch_bounds__(FB) k_trsm_oz(TileSetDev ts, int mat0, int nmat, int k,
-                                                double* __restrict__ tiles, ErrWord* err) {
+__global__ void __launch_bounds__(FB, 1) k_trsm_oz(TileSetDev ts, int mat0, int nmat, int k,
+                                                   double* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_oz[];
   if (grid_mat() >= nmat) return;
   const int m = mat0 + grid_mat();
@@ -814,8 +952,8 @@ __global__ void __launch_bounds__(FB) k_trsm_oz(TileSetDev ts, int mat0, int nma
 
 // Trailing update A_ij -= L_ik L_jk^T in FP64; same target map as k_syrk_tc.
 // grid = (max panel rows * pmax + 1, nmat), pmax = ceil(max panel rows / 2)
-__global__ void __launch_bounds__(FB) k_syrk_oz(TileSetDev ts, int mat0, int nmat, int k, int pmax,
-                                                double* __restrict__ tiles, ErrWord* err) {
+__global__ void __launch_bounds__(FB, 1) k_syrk_oz(TileSetDev ts, int mat0, int nmat, int k, int pmax,
+                                                   double* __restrict__ tiles, ErrWord* err) {
   extern __shared__ __align__(1024) unsigned char dsm_oz[];
   if (grid_mat() >= nmat) return;
   const int m = mat0 + grid_mat();
