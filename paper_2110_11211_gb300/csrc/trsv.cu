@@ -432,14 +432,17 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
 // memory and a CTA barrier instead of result slots in L2 polled by other CTAs.
 // With the narrow bands of curve-ordered subdomains the chain carries about one
 // off-block tile per row, which makes the cross-CTA hand-off the bound of the
-// row-slab items; here a step costs the tile's FMAs and two barriers.  The
+// row-slab items; here a forward step costs the tile's FMAs and one barrier,
+// and a backward step only the product with the previous row's x and an
+// mbarrier phase (the rest of the row's work is formed before the wait).  The
 // matrix vector (z, then x) lives in shared memory.
 //   forward   z_I = b_I - sum_{K < I} Lh_IK z_K   (rows below nzr[I]: z = b)
 //   backward  x_I = E_I z_I - sum_{K > I} Lh_KI^T x_K  (columns below nzr[K])
 // The producer warp streams the factor in pieces of 32 tile rows (forward: the
 // nonzero rows of each off-block tile; backward: the two halves of E_I, then
 // per Lh^T tile its left halves (FP64, nzr[K] <= TILE / 2: 64 rows of 32
-// columns, packed) or its two halves) through an eight-stage ring.  Consumer
+// columns, packed) or its two halves, the nearest row's tile last) through an
+// eight-stage ring.  Consumer
 // thread (j, g) = (tid / 8, tid % 8) owns tile rows j and j + 32 and the
 // 16-byte chunks g + 8 k of a piece row, so each quarter-warp phase of a
 // shared load reads one contiguous 128-byte row segment.
@@ -556,8 +559,8 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
         put(e + PR * TILE, PB, false);
         const int* cl = a.ts.colidx + a.ts.colptr[fb + I];
         const int ncl = a.ts.colptr[fb + I + 1] - a.ts.colptr[fb + I];
-        for (int q = 0; q < ncl; ++q) {
-          const int K = cl[q];
+        for (int q = 1; q <= ncl; ++q) {
+          const int K = cl[q < ncl ? q : 0];  // the nearest row last (it waits for the chain)
           const T* src = ut + tile_at(a.ts, tb, fb, K, I);
           if (half_piece(K)) {
             put(src, 0, true);
@@ -637,12 +640,30 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
       consumers_sync();  // z_I visible to the next rows
     }
   } else {
+    // E_I z_I and the products with the x_K of rows K >= I + 2 do not wait for
+    // the chain: every warp forms them first and waits only before the product
+    // with x_{I+1}, on an mbarrier (zbar[1], NCONS / 32 arrivals, set up by
+    // k_trsv) at which each warp arrives once it has written its rows of
+    // x_{I+1}.  A warp reads z_I into registers before it arrives for x_{I+1};
+    // x_I replaces z_I in zv only after every warp has arrived, so those reads
+    // never race with the writes.
+    unsigned long long* xbar = &sm.zbar[1];
     mbar_wait(&sm.zbar[0], 0, a.err, 22);  // z in zv
-    for (int I = nt - 1; I >= 0; --I) {
-      A acc0 = A(0), acc1 = A(0);
-      {
+    auto apply_lt = [&](int K, A& acc0, A& acc1) {
+      if (half_piece(K)) {
+        // 64 rows of 32 columns: chunks g and g + 8 of rows j and j + 32
+        A xs[2 * EPC];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) xs[k * EPC + e] = A(-zv[K * TILE + (g + 8 * k) * EPC + e]);
+        const T* st = take();
+        piece_row_dot<T, A, 2>(st + j * (TILE / 2), g, xs, acc0);
+        piece_row_dot<T, A, 2>(st + (j + PR) * (TILE / 2), g, xs, acc1);
+        give();
+      } else {
         A xs[CH * EPC];
-        slice(I, xs, false);
+        slice(K, xs, true);
         const T* st = take();
         piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc0);
         give();
@@ -650,35 +671,26 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
         piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc1);
         give();
       }
+    };
+    A zs[CH * EPC];
+    slice(nt - 1, zs, false);
+    consumers_sync();  // every warp holds z_{nt-1} before x_{nt-1} replaces it
+    for (int I = nt - 1; I >= 0; --I) {
+      A acc0 = A(0), acc1 = A(0);
+      const T* st = take();
+      piece_row_dot<T, A, CH>(st + j * TILE, g, zs, acc0);
+      give();
+      st = take();
+      piece_row_dot<T, A, CH>(st + j * TILE, g, zs, acc1);
+      give();
       const int* cl = a.ts.colidx + a.ts.colptr[fb + I];
       const int ncl = a.ts.colptr[fb + I + 1] - a.ts.colptr[fb + I];
-      for (int q = 0; q < ncl; ++q) {
-        const int K = cl[q];
-        if (half_piece(K)) {
-          // 64 rows of 32 columns: chunks g and g + 8 of rows j and j + 32
-          A xs[2 * EPC];
-#pragma unroll
-          for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int e = 0; e < EPC; ++e) xs[k * EPC + e] = A(-zv[K * TILE + (g + 8 * k) * EPC + e]);
-          const T* st = take();
-          piece_row_dot<T, A, 2>(st + j * (TILE / 2), g, xs, acc0);
-          piece_row_dot<T, A, 2>(st + (j + PR) * (TILE / 2), g, xs, acc1);
-          give();
-        } else {
-          A xs[CH * EPC];
-          slice(K, xs, true);
-          const T* st = take();
-          piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc0);
-          give();
-          st = take();
-          piece_row_dot<T, A, CH>(st + j * TILE, g, xs, acc1);
-          give();
-        }
-      }
+      for (int q = 1; q < ncl; ++q) apply_lt(cl[q], acc0, acc1);  // rows >= I + 2
+      if (I < nt - 1) mbar_wait(xbar, (unsigned)(nt - 2 - I) & 1u, a.err, 23);  // x_{I+1}
+      if (ncl > 0) apply_lt(cl[0], acc0, acc1);
       // lane g = 0 of the group writes row j (acc0's total), lane g = 4 row j + 32
       const A tot = sum8_pair(acc0, acc1);
-      consumers_sync();  // every read of z_I is done
+      if (I > 0) slice(I - 1, zs, false);
       if ((g & 3) == 0) {
         const int row = I * TILE + j + (g ? PR : 0);
         zv[row] = double(tot);
@@ -686,7 +698,8 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
         // the forward slot, polled by row-slab items of other launches
         a.y[vb + row] = __longlong_as_double((long long)TRSV_PENDING);
       }
-      consumers_sync();  // x_I visible to the next rows
+      __syncwarp();
+      if (lane == 0) mbar_arrive(xbar);  // this warp's rows of x_I are in zv
     }
   }
 }
@@ -703,11 +716,15 @@ __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
   sm.zbar = sm.empty + MAXST;
   __shared__ unsigned long long s_ticket;
   if (threadIdx.x == 0) {
-    s_ticket = atomicAdd(a.ticket, 1ull);
+    const unsigned long long tk = atomicAdd(a.ticket, 1ull);
+    s_ticket = tk;
+    // the backward sweep of a whole-matrix item takes zbar[1] as the phase
+    // barrier of its rows of x, one arrival per consumer warp
+    const bool whole_item = WHOLE && a.work[(int)(tk % (unsigned long long)a.nwork)].row < 0;
     for (int k = 0; k < MAXST; ++k) {
       mbar_init(&sm.full[k], 1);
       mbar_init(&sm.empty[k], NCONS / 32);
-      mbar_init(&sm.zbar[k], 1);
+      mbar_init(&sm.zbar[k], whole_item && k == 1 ? NCONS / 32 : 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
