@@ -172,36 +172,43 @@ void build_worklists(const std::vector<int>& nt, const std::vector<char>& includ
 // order[r] = node numbered r.  Deterministic.
 void rcm_order(int n, const std::vector<int>& deg, const std::vector<int>& adj, int stride,
                std::vector<int>& order) {
-  std::vector<std::vector<int>> nb(n);
+  // neighbour lists in one flat array, each sorted by (degree, index)
+  std::vector<int> off(n + 1, 0);
+  for (int v = 0; v < n; ++v) off[v + 1] = off[v] + deg[v];
+  std::vector<int> nb(off[n]);
   for (int v = 0; v < n; ++v) {
-    nb[v].assign(adj.begin() + (size_t)v * stride, adj.begin() + (size_t)v * stride + deg[v]);
-    std::sort(nb[v].begin(), nb[v].end(), [&](int a, int b) {
-      return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
-    });
+    int* l = nb.data() + off[v];
+    std::copy(adj.begin() + (size_t)v * stride, adj.begin() + (size_t)v * stride + deg[v], l);
+    std::sort(l, l + deg[v], [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
   }
-  std::vector<int> stamp(n, -1);
+  std::vector<int> stamp(n, -1), queue(n);
   int stampv = 0;
   // number of breadth-first levels from root; last = min-degree node of the last level
   auto sweep = [&](int root, int& last) {
     ++stampv;
-    std::vector<int> cur{root}, next;
+    int head = 0, tail = 0, lev_begin = 0, nlev = 0;
+    queue[tail++] = root;
     stamp[root] = stampv;
-    int nlev = 1;
-    for (;;) {
-      next.clear();
-      for (int v : cur)
-        for (int u : nb[v])
+    while (head < tail) {
+      lev_begin = head;
+      const int lev_end = tail;
+      ++nlev;
+      for (; head < lev_end; ++head) {
+        const int v = queue[head];
+        for (int k = off[v]; k < off[v + 1]; ++k) {
+          const int u = nb[k];
           if (stamp[u] != stampv) {
             stamp[u] = stampv;
-            next.push_back(u);
+            queue[tail++] = u;
           }
-      if (next.empty()) break;
-      cur.swap(next);
-      ++nlev;
+        }
+      }
     }
-    last = cur[0];
-    for (int v : cur)
+    last = queue[lev_begin];
+    for (int k = lev_begin; k < tail; ++k) {
+      const int v = queue[k];
       if (deg[v] < deg[last] || (deg[v] == deg[last] && v < last)) last = v;
+    }
     return nlev;
   };
   std::vector<char> seen(n, 0);
@@ -222,11 +229,13 @@ void rcm_order(int n, const std::vector<int>& deg, const std::vector<int>& adj, 
     seen[root] = 1;
     while (head < order.size()) {
       const int v = order[head++];
-      for (int u : nb[v])
+      for (int k = off[v]; k < off[v + 1]; ++k) {
+        const int u = nb[k];
         if (!seen[u]) {
           seen[u] = 1;
           order.push_back(u);
         }
+      }
     }
   }
   std::reverse(order.begin(), order.end());
@@ -948,11 +957,53 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   h->ts.tbase = h->d_tbase;
   h->ts.vbase = h->d_vbase;
 
+  // Numbering of the coarse unknowns in the coarse factor: reverse
+  // Cuthill-McKee on the graph of adjacent coarse blocks, a profile-reducing
+  // order (A_0^{-1}, and so the coarse correction, is unchanged by it).  The
+  // adjacency lists come from the device; the ordering is host bookkeeping on
+  // N0 nodes, done while the device runs the local numbering below.
+  int* d_adj = nullptr;
+  int* d_deg = nullptr;
+  std::vector<int> cdeg, cadj;
+  int cdmax = 0;
+  if (h->variant != SFCDD_ONE_LEVEL && h->N0 > 1) {
+    const int N0 = h->N0;
+    const int bmax = (pd.f + (pd.r > 0 ? 1 : 0) + h->q - 1) / h->q;
+    const int maxdeg = std::min(N0 - 1, std::min(2048, std::max(32, bmax * 2 * d)));
+    TRY(dalloc(h, &d_adj, (size_t)N0 * maxdeg));
+    TRY(dalloc(h, &d_deg, N0));
+    pf.run(SFCDD_K_COARSE_ASSEMBLE, [&] {
+      launch_coarse_adjacency(g, pd, h->curve_code, h->invpad, maxdeg, d_adj, d_deg, s);
+    });
+    cdeg.resize(N0);
+    SFCDD_CUDA_OK(cudaMemcpyAsync(cdeg.data(), d_deg, N0 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    bool ok = true;
+    for (int v : cdeg) {
+      if (v < 0) ok = false;
+      cdmax = std::max(cdmax, v);
+    }
+    if (ok && cdmax > 0) {  // otherwise the coarse blocks keep the eq. restr order
+      cadj.resize((size_t)N0 * cdmax);
+      SFCDD_CUDA_OK(cudaMemcpy2DAsync(cadj.data(), cdmax * sizeof(int), d_adj, maxdeg * sizeof(int),
+                                      cdmax * sizeof(int), N0, cudaMemcpyDeviceToHost, s));
+      SFCDD_CUDA_OK(cudaStreamSynchronize(s));
+    } else {
+      cdmax = 0;
+    }
+  }
+
   // numbering inside each subdomain: lexicographic grid order by default (a
-  // fill-reducing order; A_i^{-1} does not depend on it)
+  // fill-reducing order; A_i^{-1} does not depend on it); queued here, waited
+  // for after the coarse ordering
   h->local_order = o.local_order;
+  std::vector<void*> order_tmp;
+  std::vector<int> mstart, mN, mcb, lb;
   if (h->local_order == 0 && h->variant != SFCDD_COARSE_ONLY) {
-    std::vector<int> mstart(P), mN(P, h->N), mcb(P, 0), lb(P);
+    mstart.assign(P, 0);
+    mN.assign(P, h->N);
+    mcb.assign(P, 0);
+    lb.assign(P, 0);
     long long tot = 0;
     for (int m = 0; m < P; ++m) {
       mstart[m] = h->h_start[m];
@@ -980,57 +1031,29 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
       local_order_lex(h->ts, P, max_nlocal, d_ms, d_mN, d_mcb, d_lb, tot, h->curve_code, okeys,
                       ovals, otemp, h->d_lperm, h->d_linv, s);
     });
-    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
-    for (void* t : {(void*)okeys, (void*)ovals, (void*)otemp, (void*)d_ms, (void*)d_mN,
-                    (void*)d_mcb, (void*)d_lb})
-      dfree(h, t);
+    order_tmp = {(void*)okeys, (void*)ovals, (void*)otemp, (void*)d_ms,
+                 (void*)d_mN,  (void*)d_mcb, (void*)d_lb};
     h->ts.lperm = h->d_lperm;
     h->ts.linv = h->d_linv;
   }
 
-  // Numbering of the coarse unknowns in the coarse factor: reverse
-  // Cuthill-McKee on the graph of adjacent coarse blocks, a profile-reducing
-  // order (A_0^{-1}, and so the coarse correction, is unchanged by it).  The
-  // adjacency lists come from the device; the ordering is host bookkeeping on
-  // N0 nodes.
-  if (h->variant != SFCDD_ONE_LEVEL && h->N0 > 1) {
+  std::vector<int> corder, crow;
+  if (cdmax > 0) {
     const int N0 = h->N0;
-    const int bmax = (pd.f + (pd.r > 0 ? 1 : 0) + h->q - 1) / h->q;
-    const int maxdeg = std::min(N0 - 1, std::min(2048, std::max(32, bmax * 2 * d)));
-    int *d_adj = nullptr, *d_deg = nullptr;
-    TRY(dalloc(h, &d_adj, (size_t)N0 * maxdeg));
-    TRY(dalloc(h, &d_deg, N0));
-    pf.run(SFCDD_K_COARSE_ASSEMBLE, [&] {
-      launch_coarse_adjacency(g, pd, h->curve_code, h->invpad, maxdeg, d_adj, d_deg, s);
-    });
-    std::vector<int> deg(N0);
-    SFCDD_CUDA_OK(cudaMemcpyAsync(deg.data(), d_deg, N0 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    SFCDD_CUDA_OK(cudaStreamSynchronize(s));
-    int dmax = 0;
-    bool ok = true;
-    for (int v : deg) {
-      if (v < 0) ok = false;
-      dmax = std::max(dmax, v);
-    }
-    if (ok && dmax > 0) {  // otherwise the coarse blocks keep the eq. restr order
-      std::vector<int> adj((size_t)N0 * dmax);
-      SFCDD_CUDA_OK(cudaMemcpy2DAsync(adj.data(), dmax * sizeof(int), d_adj, maxdeg * sizeof(int),
-                                      dmax * sizeof(int), N0, cudaMemcpyDeviceToHost, s));
-      SFCDD_CUDA_OK(cudaStreamSynchronize(s));
-      std::vector<int> order, crow(N0);
-      rcm_order(N0, deg, adj, dmax, order);
-      for (int r = 0; r < N0; ++r) crow[order[r]] = r;
-      TRY(dalloc(h, &h->d_crow, N0));
-      TRY(dalloc(h, &h->d_cblock, N0));
-      SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_crow, crow.data(), N0 * sizeof(int), cudaMemcpyHostToDevice, s));
-      SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_cblock, order.data(), N0 * sizeof(int), cudaMemcpyHostToDevice, s));
-      SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
-      pd.crow = h->d_crow;
-      pd.cblock = h->d_cblock;
-    }
-    dfree(h, d_adj);
-    dfree(h, d_deg);
+    rcm_order(N0, cdeg, cadj, cdmax, corder);
+    crow.resize(N0);
+    for (int r = 0; r < N0; ++r) crow[corder[r]] = r;
+    TRY(dalloc(h, &h->d_crow, N0));
+    TRY(dalloc(h, &h->d_cblock, N0));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_crow, crow.data(), N0 * sizeof(int), cudaMemcpyHostToDevice, s));
+    SFCDD_CUDA_OK(cudaMemcpyAsync(h->d_cblock, corder.data(), N0 * sizeof(int), cudaMemcpyHostToDevice, s));
+    pd.crow = h->d_crow;
+    pd.cblock = h->d_cblock;
   }
+  SFCDD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors above go out of scope
+  for (void* t : order_tmp) dfree(h, t);
+  dfree(h, d_adj);
+  dfree(h, d_deg);
 
   // Cholesky envelopes of every local matrix and of the coarse matrix: the
   // first column with a nonzero in each tile row (the factor keeps that profile)
