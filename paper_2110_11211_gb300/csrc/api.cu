@@ -1199,6 +1199,8 @@ int setup_impl(sfcdd_handle* h, const int* levels, int d, int P, double overlap,
   if (h->variant != SFCDD_COARSE_ONLY)
     pf.run(SFCDD_K_TRSM, [&] {
       launch_offblock_rows(h->ts, 0, P, h->max_nt, h->ltiles, h->st, h->d_nzr, s);
+      if (h->st == Store::F64)
+        launch_pack_half_tiles(h->ts, 0, P, h->max_ltiles, (double*)h->lut, h->d_nzr, s);
     });
   SFCDD_CUDA_OK(cudaGetLastError());
 

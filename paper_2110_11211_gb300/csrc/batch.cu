@@ -1052,6 +1052,8 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   }
   launch_offblock_rows(b->ts, 0, b->nlocal, b->max_nt_local, b->ltiles, b->st,
                        b->d_nzr, s);
+  if (b->st == Store::F64)
+    launch_pack_half_tiles(b->ts, 0, b->nlocal, b->sky.max_ltiles, (double*)b->lut, b->d_nzr, s);
   BTRY(balloc(b, &b->ctiles, b->sky.ctiles * TILE2));
   {
     const int smem = TILE2 * (int)(sizeof(double) + sizeof(int));
@@ -1065,6 +1067,7 @@ int batch_setup_impl(sfcdd_batch* b, const int* levels, int nsub, int d, const i
   unitize_tiles(b->ts, b->nlocal, nsub, b->sky.max_ctiles, b->ctiles, b->cut, Store::F64, s);
   launch_offblock_rows(b->ts, b->nlocal, nsub, b->max_nt_coarse, b->ctiles, Store::F64,
                        b->d_nzr, s);
+  launch_pack_half_tiles(b->ts, b->nlocal, nsub, b->sky.max_ctiles, b->cut, b->d_nzr, s);
   SFCDD_CUDA_OK(cudaGetLastError());
   b->factor_bytes = b->sky.ltiles * TILE2 * (b->precision == 0 ? 8 : b->precision == 1 ? 4 : 2) +
                     b->sky.ctiles * TILE2 * 8;

@@ -1258,6 +1258,33 @@ void launch_offblock_rows(const TileSetDev& ts, int mat0, int nmat, int max_nt, 
   }
 }
 
+// Packs the left halves of the FP64 transposed tiles whose source row bound is
+// at most TILE / 2 (one CTA per stored tile; read all, then write in place).
+__global__ void __launch_bounds__(FB) k_pack_half_tiles(TileSetDev ts, int mat0, int nmat,
+                                                        double* __restrict__ ut,
+                                                        const int* __restrict__ nzr) {
+  __shared__ double half[TILE * (TILE / 2)];
+  if (grid_mat() >= nmat) return;
+  const int m = mat0 + grid_mat();
+  const int nt = ts.nt[m];
+  const int fb = ts.vbase[m] / TILE;
+  if ((int)blockIdx.x >= stored_tiles(ts, fb, nt)) return;
+  int I, K;
+  skyline_decode(ts, fb, nt, blockIdx.x, I, K);
+  if (I == K || nzr[fb + I] > TILE / 2) return;  // uniform over the CTA
+  double* t = ut + tile_at(ts, ts.tbase[m], fb, I, K);
+  for (int e = threadIdx.x; e < TILE * (TILE / 2); e += FB)
+    half[e] = t[(e / (TILE / 2)) * TILE + e % (TILE / 2)];
+  __syncthreads();
+  for (int e = threadIdx.x; e < TILE * (TILE / 2); e += FB) t[e] = half[e];
+}
+
+void launch_pack_half_tiles(const TileSetDev& ts, int mat0, int nmat, int max_stored, double* ut,
+                            const int* nzr, cudaStream_t s) {
+  if (nmat <= 0 || max_stored <= 0) return;
+  k_pack_half_tiles<<<mat_grid(max_stored, nmat), FB, 0, s>>>(ts, mat0, nmat, ut, nzr);
+}
+
 // ---------------------------------------------------------------------------
 // Substitution form with cb-tile diagonal blocks (one matrix, FP64).  D_J is
 // the lower block-triangular cb x cb-tile diagonal block J of the factor and

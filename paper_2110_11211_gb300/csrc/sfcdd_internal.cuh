@@ -480,6 +480,13 @@ void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s, int grid = 0);
 // stored Lh tiles: one past the last row holding a nonzero bit pattern.
 void launch_offblock_rows(const TileSetDev& ts, int mat0, int nmat, int max_nt, const void* tiles,
                           Store st, int* nzr, cudaStream_t s);
+// FP64 transposed off-block tiles Lh_IK^T (slot (I, K) of ut, I > K, matrices
+// [mat0, mat0 + nmat) with cb = 1) whose row bound nzr[I] is at most TILE / 2
+// keep their nonzeros in the left half of every row: packs those halves into
+// the first TILE * TILE / 2 elements of the slot (row stride TILE / 2), the
+// layout the backward substitution streams them in.  After launch_offblock_rows.
+void launch_pack_half_tiles(const TileSetDev& ts, int mat0, int nmat, int max_stored, double* ut,
+                            const int* nzr, cudaStream_t s);
 // Factorization and inversion of one 64 x 64 FP64 tile in place (self-test of the
 // breakdown report: a non-positive pivot sets NOT_SPD with index m).
 void launch_potrf_one(double* tile, ErrWord* err, int m, cudaStream_t s);

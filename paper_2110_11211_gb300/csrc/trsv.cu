@@ -287,8 +287,7 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
                      : a.dout + vb + cl[ncl - 1 - (tt - nE)] * TILE;
   };
   if (threadIdx.x >= PROD0) {
-    // producer warp: every lane waits for the stage; lane 0 (or, for half
-    // tiles, the lanes row by row) issues the copies
+    // producer warp: every lane waits for the stage; lane 0 issues the copy
     const int pl = threadIdx.x - PROD0;
     const unsigned long long pol = evict_first_policy();
     for (int t = 0; t < ntile; ++t) {
@@ -308,20 +307,18 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
       } else {
         src = ut + tile_at(a.ts, tb, fb, cl[ncl - 1 - (t - nE)], r) + soff;
       }
-      // half tiles: FP64 copies the left halves row by row; narrower types keep
-      // one copy of the slab (their rows' halves are too short to copy alone)
-      if (sizeof(T) < 8 || !half_tile(t)) {
-        if (pl == 0) {
-          mbar_expect_tx(&sm.full[s], bytes);
-          factor_copy(dst, src, bytes, &sm.full[s], pol);
-        }
-      } else {
-        constexpr unsigned HB = TILE / 2 * sizeof(T);  // 16-byte multiple for every T
-        if (pl == 0) mbar_expect_tx(&sm.full[s], R * HB);
-        __syncwarp();
-        for (int j = pl; j < R; j += 32)
-          factor_copy(dst + (size_t)j * TILE * sizeof(T), src + (long long)j * TILE, HB, &sm.full[s],
-                      pol);
+      // half tiles: FP64 slots hold the left halves packed (launch_pack_half_tiles),
+      // so the slab's R half rows are one contiguous copy; narrower types keep
+      // the full slab (their rows' halves are too short to pay)
+      if (sizeof(T) == 8 && half_tile(t)) {
+        constexpr unsigned HB = TILE / 2 * sizeof(T);
+        src = ut + tile_at(a.ts, tb, fb, cl[ncl - 1 - (t - nE)], r) +
+              (long long)R * slab * (TILE / 2);
+        bytes = R * HB;
+      }
+      if (pl == 0) {
+        mbar_expect_tx(&sm.full[s], bytes);
+        factor_copy(dst, src, bytes, &sm.full[s], pol);
       }
     }
     return;
@@ -393,8 +390,9 @@ __device__ void sweep_item(const TrsvArgs& a, const T* __restrict__ lt, const T*
     if (half) {
       // - Lh^T x on the left half: column `lane`
       const A vh = A(-zs[lane]);
+      constexpr int HS = sizeof(T) == 8 ? TILE / 2 : TILE;  // row stride of a half tile's stage
 #pragma unroll
-      for (int i = 0; i < RPW; ++i) acc[i] = fma(sm_one(st + (rloc + i) * TILE + lane), vh, acc[i]);
+      for (int i = 0; i < RPW; ++i) acc[i] = fma(sm_one(st + (rloc + i) * HS + lane), vh, acc[i]);
     } else {
       // backward: + E z, - Lh^T x
       const bool neg = !FWD && t >= nE;
@@ -522,20 +520,13 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
     const int pl = threadIdx.x - PROD0;
     const unsigned long long pol = evict_first_policy();
     int t = 0;
-    auto put = [&](const T* src, unsigned bytes, bool half) {
+    auto put = [&](const T* src, unsigned bytes) {
       const int s = t % NS, k = t / NS;
       if (k >= 1) mbar_wait(&sm.empty[s], (k - 1) & 1, a.err, 20);
       unsigned char* dst = sm.ring + (size_t)s * PB;
-      if (!half) {
-        if (pl == 0) {
-          mbar_expect_tx(&sm.full[s], bytes);
-          factor_copy(dst, src, bytes, &sm.full[s], pol);
-        }
-      } else {
-        if (pl == 0) mbar_expect_tx(&sm.full[s], TILE * HB);
-        __syncwarp();
-        for (int j = pl; j < TILE; j += 32)
-          factor_copy(dst + (size_t)j * HB, src + (long long)j * TILE, HB, &sm.full[s], pol);
+      if (pl == 0) {
+        mbar_expect_tx(&sm.full[s], bytes);
+        factor_copy(dst, src, bytes, &sm.full[s], pol);
       }
       ++t;
     };
@@ -545,7 +536,7 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
         for (int K = a.ts.kmin[fb + I]; K < I; ++K)
           for (int p = 0; p * PR < nz; ++p)
             put(lt + tile_at(a.ts, tb, fb, I, K) + (long long)p * PR * TILE,
-                (unsigned)(min(PR, nz - p * PR) * TILE * (int)sizeof(T)), false);
+                (unsigned)(min(PR, nz - p * PR) * TILE * (int)sizeof(T)));
       }
     } else {
       if (pl == 0) {
@@ -555,18 +546,18 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
       }
       for (int I = nt - 1; I >= 0; --I) {
         const T* e = ut + tile_at(a.ts, tb, fb, I, I);
-        put(e, PB, false);
-        put(e + PR * TILE, PB, false);
+        put(e, PB);
+        put(e + PR * TILE, PB);
         const int* cl = a.ts.colidx + a.ts.colptr[fb + I];
         const int ncl = a.ts.colptr[fb + I + 1] - a.ts.colptr[fb + I];
         for (int q = 1; q <= ncl; ++q) {
           const int K = cl[q < ncl ? q : 0];  // the nearest row last (it waits for the chain)
           const T* src = ut + tile_at(a.ts, tb, fb, K, I);
           if (half_piece(K)) {
-            put(src, 0, true);
+            put(src, TILE * HB);  // the left halves, packed in the slot (launch_pack_half_tiles)
           } else {
-            put(src, PB, false);
-            put(src + PR * TILE, PB, false);
+            put(src, PB);
+            put(src + PR * TILE, PB);
           }
         }
       }
