@@ -47,10 +47,10 @@
 // in the backward) from HBM into a shared-memory ring with bulk asynchronous
 // copies (cp.async.bulk, completion on mbarriers); eight consumer warps wait on
 // the ring's mbarriers, apply the slabs, and free the stages.  In launches of
-// slab items only, the ring holds 32 KB (one FP64 tile, two FP32 tiles, two
-// BF16 tiles in 16 KB), so that four or more CTAs fit an SM; coarse items of
-// low-precision launches run in 16- or 32-row slabs.  Launches with whole-matrix
-// items use eight 32-row pieces (FP64 128 KB) and the matrix vector instead.
+// slab items only, the ring holds 64 KB (two FP64 tiles, four FP32, eight
+// BF16), three CTAs per SM; coarse items of low-precision launches run in 16-
+// or 32-row slabs.  Launches with whole-matrix items use eight 32-row pieces
+// (FP64 128 KB) and the matrix vector instead.
 #include "sfcdd_internal.cuh"
 
 namespace sfcdd {
@@ -66,11 +66,13 @@ constexpr long long SPIN_FAST = 1 << 12;   // polls before the poller starts to 
 // Shared-memory plan of a launch whose local factors have element size ES.
 template <int ES, bool WHOLE = false>
 struct Plan {
-  // slab ring: 32 KB (one FP64 or two FP32 tiles, four BF16), so that four or more
-  // CTAs fit an SM; a 64-row FP64 slab then has a single stage.  Launches with
-  // whole-matrix items: eight 32-row pieces (FP64 128 KB: a CTA streams the whole
-  // matrix and needs the bytes in flight of an SM), plus the matrix vector.
-  static constexpr int RING = WHOLE ? 8 * 32 * TILE * ES : (ES == 8 ? 1 : 2) * TILE2 * ES;
+  // slab ring: 64 KB (two FP64 tiles, four FP32, eight BF16), three CTAs per SM;
+  // measured against 32 and 128 KB: 32 KB leaves the coarse slab items of a
+  // launch too few stages in flight (FP32 local factors: 360 -> 339 us per PCG
+  // iteration with 64 KB), 128 KB too few CTAs.  Launches with whole-matrix
+  // items: eight 32-row pieces (FP64 128 KB: a CTA streams the whole matrix and
+  // needs the bytes in flight of an SM), plus the matrix vector.
+  static constexpr int RING = WHOLE ? 8 * 32 * TILE * ES : 64 * 1024;
   static constexpr int ZBUF = MAXST * TILE * 8;
   static constexpr int BYTES = RING + ZBUF + 3 * MAXST * 8;
 };
