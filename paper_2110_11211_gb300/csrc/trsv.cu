@@ -64,15 +64,20 @@ constexpr long long MBAR_LIMIT = 1ll << 26;
 constexpr long long SPIN_FAST = 1 << 12;   // polls before the poller starts to back off
 
 // Shared-memory plan of a launch whose local factors have element size ES.
-template <int ES, bool WHOLE = false>
+template <int ES, bool WHOLE = false, bool BIG = false>
 struct Plan {
   // slab ring: 64 KB (two FP64 tiles, four FP32, eight BF16), three CTAs per SM;
   // measured against 32 and 128 KB: 32 KB leaves the coarse slab items of a
   // launch too few stages in flight (FP32 local factors: 360 -> 339 us per PCG
   // iteration with 64 KB), 128 KB too few CTAs.  Launches with whole-matrix
   // items: eight 32-row pieces (FP64 128 KB: a CTA streams the whole matrix and
-  // needs the bytes in flight of an SM), plus the matrix vector.
-  static constexpr int RING = WHOLE ? 8 * 32 * TILE * ES : 64 * 1024;
+  // needs the bytes in flight of an SM), plus the matrix vector.  BIG: FP32 and
+  // BF16 launches take the FP64 ring size too when the matrix vector still fits,
+  // so that one CTA holds an SM and the coarse row items of the launch get eight
+  // 32-row stages: two whole-matrix sweeps on one SM, or a sweep beside coarse
+  // items with four stages, were measured slower (FP32 local factors: 418 -> 308
+  // us per PCG iteration).
+  static constexpr int RING = WHOLE ? 8 * 32 * TILE * (BIG ? 8 : ES) : 64 * 1024;
   static constexpr int ZBUF = MAXST * TILE * 8;
   static constexpr int BYTES = RING + ZBUF + 3 * MAXST * 8;
 };
@@ -697,9 +702,9 @@ __device__ void sweep_matrix(const TrsvArgs& a, const T* __restrict__ lt, const 
   }
 }
 
-template <class T, class A, bool FWD, bool WHOLE>
+template <class T, class A, bool FWD, bool WHOLE, bool BIG = false>
 __global__ void __launch_bounds__(NTHR) k_trsv(TrsvArgs a) {
-  using PL = Plan<(int)sizeof(T), WHOLE>;
+  using PL = Plan<(int)sizeof(T), WHOLE, BIG>;
   extern __shared__ __align__(128) unsigned char dsm_trsv[];
   RowSmem sm;
   sm.ring = dsm_trsv;
@@ -792,7 +797,15 @@ template <class T, class A, bool FWD>
 static void launch_k(const TrsvArgs& a, cudaStream_t s, int grid = 0) {
   const int nblk = grid > 0 ? grid : a.nwork;
   if (a.zv_doubles > 0) {
-    const int bytes = Plan<(int)sizeof(T), true>::BYTES + a.zv_doubles * (int)sizeof(double);
+    const long long zb = (long long)a.zv_doubles * (long long)sizeof(double);
+    if (sizeof(T) < 8 && Plan<(int)sizeof(T), true, true>::BYTES + zb <= CTA_SMEM_MAX) {
+      const int bytes = (int)(Plan<(int)sizeof(T), true, true>::BYTES + zb);
+      cudaFuncSetAttribute(k_trsv<T, A, FWD, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes);
+      k_trsv<T, A, FWD, true, true><<<nblk, NTHR, bytes, s>>>(a);
+      return;
+    }
+    const int bytes = (int)(Plan<(int)sizeof(T), true>::BYTES + zb);
     cudaFuncSetAttribute(k_trsv<T, A, FWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     k_trsv<T, A, FWD, true><<<nblk, NTHR, bytes, s>>>(a);
   } else {
