@@ -555,6 +555,7 @@ TrsvArgs trsv_args(sfcdd_handle* h, bool fwd, const double* rhs, const PcgScalar
   a.err = h->err;
   a.sc = sc;
   if (h->nsub_local == 0 && list != LIST_COARSE) a.zv_doubles = h->max_nt * TILE;
+  a.wide_ring = 1;
   return a;
 }
 

@@ -473,6 +473,10 @@ struct TrsvArgs {
   // each swept by one CTA through a shared-memory vector of this many doubles
   // (the largest local tile count times TILE); 0: row-slab items only
   int zv_doubles;
+  // row-slab launches: 1 streams through a 64 KB ring (three CTAs per SM; the
+  // single large problems), 0 through 32 KB (FP64 one tile, FP32 two, BF16 four:
+  // more CTAs per SM for the many small matrices of a batch)
+  int wide_ring;
 };
 // grid > 0 launches that many CTAs instead of one per work item (self-test only)
 void launch_trsv_fwd(const TrsvArgs& a, Store st, cudaStream_t s, int grid = 0);

@@ -47,10 +47,11 @@
 // in the backward) from HBM into a shared-memory ring with bulk asynchronous
 // copies (cp.async.bulk, completion on mbarriers); eight consumer warps wait on
 // the ring's mbarriers, apply the slabs, and free the stages.  In launches of
-// slab items only, the ring holds 64 KB (two FP64 tiles, four FP32, eight
-// BF16), three CTAs per SM; coarse items of low-precision launches run in 16-
-// or 32-row slabs.  Launches with whole-matrix items use eight 32-row pieces
-// (FP64 128 KB) and the matrix vector instead.
+// slab items only, the ring holds 64 KB for a single problem (two FP64 tiles,
+// four FP32, eight BF16; three CTAs per SM) and 32 KB for a batch (more CTAs
+// per SM); coarse items of low-precision launches run in 16- or 32-row slabs.
+// Launches with whole-matrix items use eight 32-row pieces (FP64 128 KB) and
+// the matrix vector instead (see Plan).
 #include "sfcdd_internal.cuh"
 
 namespace sfcdd {
@@ -66,18 +67,22 @@ constexpr long long SPIN_FAST = 1 << 12;   // polls before the poller starts to 
 // Shared-memory plan of a launch whose local factors have element size ES.
 template <int ES, bool WHOLE = false, bool BIG = false>
 struct Plan {
-  // slab ring: 64 KB (two FP64 tiles, four FP32, eight BF16), three CTAs per SM;
-  // measured against 32 and 128 KB: 32 KB leaves the coarse slab items of a
-  // launch too few stages in flight (FP32 local factors: 360 -> 339 us per PCG
-  // iteration with 64 KB), 128 KB too few CTAs.  Launches with whole-matrix
-  // items: eight 32-row pieces (FP64 128 KB: a CTA streams the whole matrix and
-  // needs the bytes in flight of an SM), plus the matrix vector.  BIG: FP32 and
-  // BF16 launches take the FP64 ring size too when the matrix vector still fits,
-  // so that one CTA holds an SM and the coarse row items of the launch get eight
-  // 32-row stages: two whole-matrix sweeps on one SM, or a sweep beside coarse
-  // items with four stages, were measured slower (FP32 local factors: 418 -> 308
-  // us per PCG iteration).
-  static constexpr int RING = WHOLE ? 8 * 32 * TILE * (BIG ? 8 : ES) : 64 * 1024;
+  // Slab launches, BIG (TrsvArgs::wide_ring): 64 KB (two FP64 tiles, four FP32,
+  // eight BF16), three CTAs per SM; against 32 KB it gives the coarse slab items
+  // of a single large problem more stages in flight (FP32 local factors: 360 ->
+  // 339 us per PCG iteration); 128 KB leaves too few CTAs.  Otherwise 32 KB
+  // (one FP64 tile, two FP32, four BF16 in 16 KB): more CTAs per SM, which the
+  // many small matrices of a batch need (the 385-subgrid batch: FP32 solve 60
+  // ms against 80 with 64 KB).  Launches with whole-matrix items: eight 32-row
+  // pieces (FP64 128 KB: a CTA streams the whole matrix and needs the bytes in
+  // flight of an SM), plus the matrix vector.  BIG: FP32 and BF16 launches take
+  // the FP64 ring size too when the matrix vector still fits, so that one CTA
+  // holds an SM and the coarse row items of the launch get eight 32-row stages:
+  // two whole-matrix sweeps on one SM, or a sweep beside coarse items with four
+  // stages, were measured slower (FP32 local factors: 418 -> 308 us per PCG
+  // iteration).
+  static constexpr int RING = WHOLE ? 8 * 32 * TILE * (BIG ? 8 : ES)
+                                    : (BIG ? 64 * 1024 : (ES == 8 ? 1 : 2) * TILE2 * ES);
   static constexpr int ZBUF = MAXST * TILE * 8;
   static constexpr int BYTES = RING + ZBUF + 3 * MAXST * 8;
 };
@@ -808,6 +813,11 @@ static void launch_k(const TrsvArgs& a, cudaStream_t s, int grid = 0) {
     const int bytes = (int)(Plan<(int)sizeof(T), true>::BYTES + zb);
     cudaFuncSetAttribute(k_trsv<T, A, FWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     k_trsv<T, A, FWD, true><<<nblk, NTHR, bytes, s>>>(a);
+  } else if (a.wide_ring) {
+    constexpr int bytes = Plan<(int)sizeof(T), false, true>::BYTES;
+    cudaFuncSetAttribute(k_trsv<T, A, FWD, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
+    k_trsv<T, A, FWD, false, true><<<nblk, NTHR, bytes, s>>>(a);
   } else {
     constexpr int bytes = Plan<(int)sizeof(T)>::BYTES;
     cudaFuncSetAttribute(k_trsv<T, A, FWD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
